@@ -1,0 +1,30 @@
+"""Compile the plain C oracle into oracle/liboracle.so with gcc.
+
+TEST INFRASTRUCTURE: the oracle is used by the test suite, the smoke check and the CPU-baseline
+leg of the benchmark only.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "hdarray_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+
+def build(force=False, verbose=False):
+    """Build liboracle.so if it is missing or older than its source. Returns the library path."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))
