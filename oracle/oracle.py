@@ -83,8 +83,19 @@ def _i64(seq):
 
 
 def _dims3(dims):
+    """Extents padded to three dimensions (unused dimensions have extent 1)."""
     d = list(dims) + [1] * (3 - len(dims))
     return _i64(d)
+
+
+def _lo3(lo):
+    """Lower corner padded to three dimensions (coordinate 0)."""
+    return _i64(list(lo) + [0] * (3 - len(lo)))
+
+
+def _hi3(hi):
+    """Upper corner padded to three dimensions (exclusive bound 1)."""
+    return _i64(list(hi) + [1] * (3 - len(hi)))
 
 
 def _off3(offs):
@@ -116,8 +127,7 @@ def bf16_to_f32(h):
 def partition_boxes(ptype, nparts, dims, lo, hi):
     """Work boxes of an even ROW/COL/BLOCK partition (HDArrayPartition, Sec. 3.1)."""
     dim = len(dims)
-    rlo, rhi = _dims3(lo), _i64(list(hi) + [1] * (3 - len(hi)))
-    rlo[dim:] = 0
+    rlo, rhi = _lo3(lo), _hi3(hi)
     boxes = []
     for p in range(nparts):
         blo, bhi = np.zeros(3, np.int64), np.zeros(3, np.int64)
@@ -261,14 +271,14 @@ class OArray:
 
     # section masks over this array's tracked elements ---------------------------------------
     def mask_box(self, lo, hi, out):
-        lo3, hi3 = _dims3(lo), _i64(list(hi) + [1] * (3 - len(hi)))
+        lo3, hi3 = _lo3(lo), _hi3(hi)
         if self.coords is None:
             lib().orc_mask_box(_p(self.n3), _p(lo3), _p(hi3), _p(out))
         else:
             lib().orc_pred_box(_p(lo3), _p(hi3), self.total, _p(self.coords), _p(out))
 
     def mask_offsets(self, wlo, whi, offs, out):
-        wlo3, whi3 = _dims3(wlo), _i64(list(whi) + [1] * (3 - len(whi)))
+        wlo3, whi3 = _lo3(wlo), _hi3(whi)
         o = _off3(offs)
         if self.coords is None:
             lib().orc_mask_offsets(_p(self.n3), _p(wlo3), _p(whi3), len(o), _p(o), _p(out))

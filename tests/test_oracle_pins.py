@@ -526,3 +526,24 @@ def test_sampled_mode_agrees_with_full_mode():
         res.append(out)
     for full, samp in zip(*res):
         assert np.array_equal(full[:, flat], samp)
+
+
+def test_offsets_golden():
+    n = 0
+    for line in _golden_lines("offsets.txt"):
+        work, offs, rows = (x.strip() for x in line.split("|"))
+        lo0, hi0, lo1, hi1 = (int(v) for v in work.split())
+        offsets = []
+        for tok in offs.split():
+            offsets.append(tuple(oracle.ALL if v == "*" else int(v) for v in tok.split(",")))
+        want = set()
+        for item in rows.split():
+            r, span = item.split(":")
+            c0, c1 = span.split("-")
+            want |= {(int(r), c) for c in range(int(c0), int(c1) + 1)}
+        a = oracle.oracle.OArray("t", "double", (6, 8), 1)
+        m = np.zeros(48, np.uint8)
+        a.mask_offsets((lo0, lo1), (hi0, hi1), offsets, m)
+        assert {(int(i) // 8, int(i) % 8) for i in np.nonzero(m)[0]} == want, line
+        n += 1
+    assert n == 6
