@@ -1,0 +1,433 @@
+"""Benchmark of the HDArray hot path on GB300.
+
+Workload (one "step"): 2-D 5-point Jacobi on an 8192 x 8192 binary32 grid split 4 x 4 (BLOCK) over
+16 logical devices, the paper's data/work partition pair (whole grid / interior), 100 Jacobi
+iterations (exchange of the +-1 halo fused into the stencil launch, all 16 devices in one launch
+per iteration, replayed from a CUDA graph of two iterations), then the binary64 residual
+sum((A - B)^2) via HDArrayReduce.  Inputs (2 x 268 MB) exceed the 129 MB L2, so no flush is needed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank runs an independent replica (the
+single-GPU partitions do not span GPUs); the value is the sum over ranks of the work divided by
+the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stencil Gcell-updates/s + exchange GB/s vs HBM peak; batched/mixed vs plain form"
+UNIT = "Gcell-updates/s"
+N, P, ITERS = 8192, 16, 100
+CELLS = (N - 2) * (N - 2)
+WORKLOAD = ("2-D 5-point Jacobi 8192x8192 FP32, 4x4 BLOCK = 16 logical devices, +-1 halo, "
+            "100 iterations per step (exchange fused, one launch per iteration, CUDA graph) "
+            "+ FP64 residual via HDArrayReduce")
+PROFILE = os.path.join(ROOT, "profiles", "jacobi2d_fp32_8192_block16.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1809_05657_gb300", "csrc", "k_stencil2d.cu")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, or None when the
+    kernel source changed since the capture."""
+    try:
+        txt = open(PROFILE).read()
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in txt.splitlines():
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != sha:
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def setup_jacobi(H, x, dtype, pingpong=True):
+    B = H.HDArrayCreate("B", dtype, None, N, N)
+    A = H.HDArrayCreate("A", dtype, None, N, N)
+    R = H.HDArrayCreate("R", "double", None, N, N)
+    D = H.HDArrayPartition(H.BLOCK, (N, N), (0, 0), (N, N), P)
+    W = H.HDArrayPartition(H.BLOCK, (N, N), (1, 1), (N - 1, N - 1), P)
+    return B, A, R, D, W
+
+
+def gpu_arm(args, rank, world):
+    import numpy as np
+    import torch
+    from __graft_entry__ import build_library
+    from paper_1809_05657_gb300 import hdarray as H
+    import synthetic
+
+    build_library()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    H.HDArrayInit(ndev=P)
+    H.HDArraySetStream(stream.cuda_stream)
+    x = synthetic.jacobi_field((N, N), stream=1, dtype="float")
+    xh = torch.from_numpy(x).pin_memory()
+    B, A, R, D, W = setup_jacobi(H, x, "float")
+    H.HDArrayWrite(B, xh, D)
+
+    def warm_iters(b, a):
+        H.HDArrayApplyKernel("jacobi2d", W, b, a)
+        H.HDArrayApplyKernel("jacobi2d", W, a, b)
+
+    for _ in range(2):
+        warm_iters(B, A)
+    H.HDArrayGraphBegin()
+    warm_iters(B, A)
+    gid = H.HDArrayGraphEnd()
+
+    def residual():
+        H.HDArrayApplyKernel("sqdiff", W, B, A, R)
+        return H.HDArrayReduce(R, H.SUM, W)
+
+    # exchange volume of one iteration (the fused kernel's halo traffic)
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    xbytes = sum(int(np.prod(np.subtract(hi, lo))) for _, _, lo, hi in H.HDArrayGetPlan(B)) * 4
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        H.HDArrayGraphLaunch(gid, ITERS // 2)
+        if ev is not None:
+            ev[1].record(stream)
+        return residual()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    c0 = H.HDArrayGetCounters()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = None
+    with ClockSampler(dev) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(args.steps):
+            res = step(kev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    c1 = H.HDArrayGetCounters()
+    ms = t0.elapsed_time(t1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = c1["launches"] - c0["launches"]
+    per_launch_ms = kernel_ms / (args.steps * ITERS)
+    algo_bytes = CELLS * 8 + 2 * xbytes
+    hbm, src = peaks()
+    achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
+    value = world * CELLS * ITERS * args.steps / (ms * 1e-3) / 1e9
+
+    # end to end: inputs from pinned host memory, the residual back to the host
+    e2e = None
+    if rank == 0 and not args.quick:
+        e2e = e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args)
+    H.HDArrayExit()
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = extra_forms(H, torch, stream, args)
+    return dict(ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
+                algo_bytes=algo_bytes, xbytes=xbytes, achieved=achieved, hbm=hbm, src=src,
+                clocks=clk.summary(), residual=res, extra=extra, e2e=e2e)
+
+
+def e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args):
+    """Same step through the public API with the input written from pinned host memory and the
+    residual read back to the host in every step."""
+    def step():
+        H.HDArrayWrite(B, xh, D)                       # host -> device, 268 MB
+        for _ in range(2):                             # back into the periodic state
+            H.HDArrayApplyKernel("jacobi2d", W, B, A)
+            H.HDArrayApplyKernel("jacobi2d", W, A, B)
+        H.HDArrayGraphLaunch(gid, (ITERS - 4) // 2)
+        H.HDArrayApplyKernel("sqdiff", W, B, A, R)
+        return H.HDArrayReduce(R, H.SUM, W)            # device -> host, 8 bytes
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, args.steps // 2)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": CELLS * ITERS / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": N * N * 4, "d2h_bytes_per_step": 8}
+
+
+def extra_forms(H, torch, stream, args):
+    """The comparison forms on the same GPU: BF16 storage (fused, graph) and the plain
+    per-partition binary64 form of the paper's program (two kernels, one copy launch per
+    section, one launch per device, no graph)."""
+    import numpy as np
+    import synthetic
+    out = {}
+    H.HDArrayInit(ndev=P)
+    H.HDArraySetStream(stream.cuda_stream)
+    xb = synthetic.jacobi_field((N, N), stream=1, dtype="bf16")
+    B, A, R, D, W = setup_jacobi(H, xb, "bf16")
+    H.HDArrayWrite(B, torch.from_numpy(xb.view(np.int16)).pin_memory(), D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, 10)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    H.HDArrayGraphLaunch(gid, 50)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / 100
+    out["bf16_fused"] = {"gcells_per_s": CELLS / (ms * 1e-3) / 1e9, "us_per_iter": ms * 1e3,
+                         "hbm_frac": CELLS * 4 / (ms * 1e-3) / 1e9 / peaks()[0]}
+    H.HDArrayExit()
+    # plain binary64 form
+    H.HDArrayInit(ndev=P)
+    H.HDArraySetStream(stream.cuda_stream)
+    H.HDArraySetMode(H.HDARRAY_MODE_PLAIN)
+    x64 = synthetic.jacobi_field((N, N), stream=1, dtype="double")
+    B, A, R, D, W = setup_jacobi(H, x64, "double")
+    H.HDArrayWrite(B, torch.from_numpy(x64).pin_memory(), D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("copy", W, A, B)
+    torch.cuda.synchronize()
+    it = 10
+    c0 = H.HDArrayGetCounters()
+    t0.record(stream)
+    for _ in range(it):
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("copy", W, A, B)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    c1 = H.HDArrayGetCounters()
+    ms = t0.elapsed_time(t1) / it
+    out["plain_fp64"] = {"gcells_per_s": CELLS / (ms * 1e-3) / 1e9, "us_per_iter": ms * 1e3,
+                         "launches_per_iter": (c1["launches"] - c0["launches"]) / it}
+    H.HDArrayExit()
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------------------------
+
+SAMPLE_N = 2048
+
+
+def oracle_sample(iters):
+    """The oracle on a bounded sample of the workload: a 2048 x 2048 binary32 grid with the same
+    4 x 4 BLOCK data/work partition pair over 16 devices, `iters` ping-pong Jacobi iterations
+    with per-element message generation.  Returns (seconds, cell updates)."""
+    import oracle
+    import synthetic
+    n = SAMPLE_N
+    o = oracle.Oracle(P)
+    x = synthetic.jacobi_field((n, n), stream=1, dtype="float")
+    B = o.create("B", "float", (n, n))
+    A = o.create("A", "float", (n, n))
+    D = o.partition(oracle.BLOCK, (n, n), (0, 0), (n, n))
+    W = o.partition(oracle.BLOCK, (n, n), (1, 1), (n - 1, n - 1))
+    o.write(B, x, D)
+    t = time.perf_counter()
+    for _ in range(iters):
+        o.apply("jacobi2d", W, [B, A])
+        A, B = B, A
+    return time.perf_counter() - t, (n - 2) * (n - 2) * iters
+
+
+def cpu_baseline(iters=4):
+    sec, cells = oracle_sample(iters)
+    return {"value": cells / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%dx%d FP32 grid, same 16-device BLOCK data/work partitions, %d iterations, "
+                      "per-element message generation + Jacobi, single thread (%.1f s)"
+                      % (SAMPLE_N, SAMPLE_N, iters, sec)}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    tot_s, tot_c = 0.0, 0
+    for _ in range(args.steps):
+        s, c = oracle_sample(1)
+        tot_s += s
+        tot_c += c
+    value = tot_c / tot_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (reference: the CPU oracle on a %dx%d sample, one "
+                                              "iteration per step)" % (SAMPLE_N, SAMPLE_N)},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": "%dx%d FP32, 16-device BLOCK partitions, 1 Jacobi iteration "
+                                       "per step, single thread" % (SAMPLE_N, SAMPLE_N)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the comparison forms and e2e")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=8192,
+                    help="grid side (default 8192; smaller only for profiling captures)")
+    args = ap.parse_args()
+    global N, CELLS
+    N = args.grid
+    CELLS = (N - 2) * (N - 2)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = gpu_arm(args, rank, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if rank == 0:
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N, N], "logical_devices": P,
+                       "iterations_per_step": ITERS, "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "l2": "inputs 2 x 268 MB > 129 MB L2 (no flush)"},
+            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d<f32> (fused exchange + stencil)",
+                         "achieved": r["achieved"], "peak": r["hbm"], "unit": "GB/s",
+                         "frac": r["achieved"] / r["hbm"], "peak_source": r["src"],
+                         "traffic": traffic, "algo_bytes_per_launch": r["algo_bytes"],
+                         "launch_us": r["per_launch_ms"] * 1e3},
+            "exchange": {"bytes_per_iteration": r["xbytes"] * 2, "note": "halo read+write, fused"},
+            "cpu_baseline": cpu,
+            "e2e": r["e2e"],
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "residual": r["residual"],
+            "forms": r["extra"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

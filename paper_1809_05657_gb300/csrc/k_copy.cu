@@ -1,0 +1,87 @@
+// k_copy.cu -- section copy between logical-device buffers: the message of Eq. 1-2 moved on the
+// GPU.  The paper reads each section out with clEnqueueReadBufferRect, sends it over MPI and
+// writes it with clEnqueueWriteBufferRect (Sec. 3.1, HDArrayApplyKernel); here source and
+// destination are device buffers of the same GPU and one kernel moves every section of a call.
+//
+// Each CTA copies one task (a slice of rows of one box).  Rows are copied with the widest access
+// the task's alignment allows (16-byte vectors for buffers whose rows start on 16-byte
+// boundaries), a warp per row for wide rows and a thread per chunk for narrow rows (the
+// one-element columns of 2-D column faces and 3-D x-faces).
+#include "kernels.h"
+
+namespace hda {
+
+template <int V>
+struct VecOf;
+template <>
+struct VecOf<16> {
+    using T = uint4;
+};
+template <>
+struct VecOf<8> {
+    using T = uint2;
+};
+template <>
+struct VecOf<4> {
+    using T = uint32_t;
+};
+template <>
+struct VecOf<2> {
+    using T = uint16_t;
+};
+
+template <int V>
+__device__ __forceinline__ void copy_task(const CopyTask &t)
+{
+    using T = typename VecOf<V>::T;
+    const int nch = t.inner / V;
+    const int nrows = t.row_end - t.row_begin;
+    if (nch >= 32) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int r = warp; r < nrows; r += nw) {
+            const int row = t.row_begin + r;
+            const int o = row / t.n_mid, m = row - o * t.n_mid;
+            const T *s = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid);
+            T *d = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid);
+            int c = lane;
+            for (; c + 96 < nch; c += 128) {
+                T a = s[c], b = s[c + 32], e = s[c + 64], f = s[c + 96];
+                d[c] = a;
+                d[c + 32] = b;
+                d[c + 64] = e;
+                d[c + 96] = f;
+            }
+            for (; c < nch; c += 32) d[c] = s[c];
+        }
+    } else {
+        const int total = nrows * nch;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int r = i / nch, c = i - r * nch;
+            const int row = t.row_begin + r;
+            const int o = row / t.n_mid, m = row - o * t.n_mid;
+            const T *s = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid);
+            T *d = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid);
+            d[c] = s[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_section_copy(const CopyTask *__restrict__ tasks)
+{
+    const CopyTask t = tasks[blockIdx.x];
+    switch (t.vec) {
+    case 16: copy_task<16>(t); break;
+    case 8: copy_task<8>(t); break;
+    case 4: copy_task<4>(t); break;
+    default: copy_task<2>(t); break;
+    }
+}
+
+cudaError_t launch_copy(const CopyTask *tasks, int ntasks, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    k_section_copy<<<ntasks, 256, 0, s>>>(tasks);
+    return cudaGetLastError();
+}
+
+}  // namespace hda

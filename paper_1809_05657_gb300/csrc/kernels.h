@@ -1,0 +1,129 @@
+// kernels.h -- device-side descriptors and host launchers of the library's CUDA kernels.
+//
+// All tables are built by the host runtime once per plan (a cached exchange + kernel for one
+// HDArrayApplyKernel signature and GDEF state), uploaded to device memory, and then reused by
+// every launch that replays the plan.  Pointers inside the tables are device addresses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hda {
+
+enum DType { DT_F64 = 0, DT_F32 = 1, DT_BF16 = 2 };
+
+// ------------------------------------------------------------------------------------------
+// Section copy: the exchange of Eq. 1-2 moved between two device buffers.  A box is viewed as
+// n_outer x n_mid rows of `inner` contiguous bytes.  One task is a slice of rows of one box.
+// ------------------------------------------------------------------------------------------
+struct CopyTask {
+    const char *src;  // first byte of the box in the source buffer
+    char *dst;        // first byte of the box in the destination buffer
+    int64_t s_outer, s_mid;  // source byte strides
+    int64_t d_outer, d_mid;  // destination byte strides
+    int32_t n_mid;           // rows per outer index
+    int32_t inner;           // contiguous bytes per row
+    int32_t row_begin, row_end;  // rows [row_begin, row_end) of the flattened outer*mid range
+    int32_t vec;             // widest access (16, 8, 4 or 2 bytes) all addresses and `inner` allow
+    int32_t pad;
+};
+cudaError_t launch_copy(const CopyTask *tasks, int ntasks, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// 2-D 4-neighbour Jacobi step (Sec. 5), fused with the exchange.
+// A tile is one warp's job: output rows [r0, r1) x columns [c0, c1) inside one column band of
+// 32 vector chunks starting at cb.  Before computing, the warp copies its receive segments (the
+// parts of the device's incoming sections that only this tile reads) from the sender's buffer
+// into its own buffer.
+// ------------------------------------------------------------------------------------------
+struct StenPart2D {
+    const void *x;  // X buffer (used array) of this device
+    void *y;        // Y buffer (defined array) of this device
+    int64_t xlo0, xlo1, xs;  // X buffer origin (row, col) and row stride in elements
+    int64_t ylo0, ylo1, ys;
+};
+struct StenTile2D {
+    int32_t part;
+    int32_t r0, r1;
+    int32_t c0, c1;
+    int32_t cb;
+    int32_t seg0, nseg;
+};
+struct Seg {  // dst[k * ds] = src[k * ss] for k < n (element strides)
+    const void *src;
+    void *dst;
+    int64_t ss, ds;
+    int32_t n;
+    int32_t pad;
+};
+cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
+                            int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// 3-D 7-point step, fused with the exchange.  A tile is one CTA's job: output z in [z0, z1),
+// y in [y0, y1), x in [x0, x1) within a band of 32 vector chunks starting at xb; the CTA marches
+// along z with one warp per y row.
+// ------------------------------------------------------------------------------------------
+struct StenPart3D {
+    const void *x;
+    void *y;
+    int64_t xlo0, xlo1, xlo2, xs0, xs1;  // origin (z, y, x) and strides of z and y (elements)
+    int64_t ylo0, ylo1, ylo2, ys0, ys1;
+};
+struct StenTile3D {
+    int32_t part;
+    int32_t z0, z1, y0, y1, x0, x1;
+    int32_t xb;
+    int32_t seg0, nseg;
+};
+cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
+                             int ntiles, const Seg *segs, int rows_per_cta, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Element-wise residual R = (X - Y)^2 in double over boxes.
+// ------------------------------------------------------------------------------------------
+struct PwTask {
+    const void *x;
+    const void *y;
+    double *r;
+    int64_t xs_outer, xs_mid, ys_outer, ys_mid, rs_outer, rs_mid;  // element strides
+    int32_t n_mid, n_inner;
+    int32_t row_begin, row_end;
+};
+cudaError_t launch_sqdiff(int dtype, const PwTask *tasks, int ntasks, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Reduction of boxes to one double (HDArrayReduce, Table 2).  Deterministic: the task list and
+// the grid are fixed, every CTA folds a fixed set of rows in a fixed order, and the last CTA to
+// finish folds the per-CTA partials in index order.
+// ------------------------------------------------------------------------------------------
+struct RedTask {
+    const void *x;
+    int64_t s_outer, s_mid;  // element strides
+    int32_t n_mid, n_inner;
+    int32_t row_begin, row_end;
+};
+// scratch: `nblocks` doubles of partials followed by one unsigned counter (zero on entry, left
+// zero on exit); result: one double.
+cudaError_t launch_reduce(int dtype, int op, const RedTask *tasks, int ntasks, int nblocks,
+                          double *partials, unsigned *counter, double *result, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// GEMM of Listing 3 over row blocks: C[i][j] = beta*C[i][j] + alpha * sum_k A[i][k] * B[k][j],
+// for work rows [i0, i1) and all columns, A lower triangular when `lower` (k <= i only).
+// ------------------------------------------------------------------------------------------
+struct GemmPart {
+    const void *a;
+    const void *b;
+    void *c;
+    int64_t alo0, alo1, as;  // buffer origins (row, col) and row strides (elements)
+    int64_t blo0, blo1, bs;
+    int64_t clo0, clo1, cs;
+    int32_t i0, i1, j0, j1;  // work box of C
+    int32_t nk;
+    int32_t lower;
+};
+cudaError_t launch_gemm_f64(const GemmPart *parts, int nparts, int max_rows, int max_cols,
+                            double alpha, double beta, cudaStream_t s);
+
+}  // namespace hda

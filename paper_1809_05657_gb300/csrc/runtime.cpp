@@ -1,0 +1,2072 @@
+// runtime.cpp -- the HDArray runtime on one GB300: arrays split over logical devices, section
+// bookkeeping (Sec. 2), communication generation (Eq. 1-4), the call cache (Sec. 4.2), and the
+// C ABI declared in include/hdarray.h.
+#include "runtime.h"
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "hdarray.h"
+
+using namespace hda;
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------------
+
+struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    struct ArrInfo {
+        HDArray *a;
+        uint64_t generation, epoch;
+        int pre, post;
+    };
+    std::vector<ArrInfo> arrays;
+    std::vector<std::shared_ptr<Plan>> refs;
+    std::vector<std::shared_ptr<DevMem>> mems;
+    int64_t nkernels = 0;
+};
+
+struct Ctx {
+    bool inited = false;
+    bool host_only = false;
+    int ndev = 1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    int mode = HDARRAY_MODE_FUSED;
+    int nsm = 148;
+    std::map<std::string, KernelDef> kernels;
+    std::vector<Part> parts;
+    std::set<HDArray *> arrays;
+    uint64_t next_uid = 1, next_plan = 1;
+    struct AbsSpec {
+        std::map<int, std::vector<Box>> use, def;
+        bool has_use = false, has_def = false;
+        uint64_t version = 0;
+    };
+    std::map<std::tuple<std::string, int, uint64_t>, AbsSpec> abs;
+    uint64_t abs_version = 1;
+    std::unordered_map<std::string, std::shared_ptr<Plan>> memo;
+    // batching
+    bool batching = false;
+    std::vector<std::shared_ptr<Plan>> batch;
+    std::unordered_map<std::string, std::pair<std::shared_ptr<DevMem>, std::vector<LaunchRec>>> batch_cache;
+    // graph recording
+    bool recording = false, rec_invalid = false;
+    std::vector<LaunchRec> rec;
+    std::vector<std::shared_ptr<Plan>> rec_refs;
+    std::vector<std::shared_ptr<DevMem>> rec_mems;
+    std::map<HDArray *, std::pair<int, uint64_t>> rec_pre;  // state id, generation at first touch
+    std::map<int, GraphRec> graphs;
+    int next_graph = 1;
+    // reduction scratch
+    double *red_partials = nullptr;
+    unsigned *red_counter = nullptr;
+    double *red_result = nullptr;
+    double *host_result = nullptr;
+    int red_blocks = 0;
+    // tunables
+    int tile_rows = 64;
+    int warps_per_cta = 4;
+    // counters
+    int64_t counters[5] = {0, 0, 0, 0, 0};
+    int last_error = 0;
+};
+
+Ctx *g = nullptr;
+
+int set_err(int code)
+{
+    if (g) g->last_error = code;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            if (getenv("HDARRAY_TRACE"))                                                     \
+                fprintf(stderr, "hdarray: %s failed: %s\n", #expr, cudaGetErrorString(e_));  \
+            return HDARRAY_ERR_CUDA;                                                         \
+        }                                                                                    \
+    } while (0)
+
+bool trace() { return getenv("HDARRAY_TRACE") != nullptr; }
+
+int dtype_of(const char *t, int *esize)
+{
+    if (!t) return -1;
+    if (!strcmp(t, "double")) { *esize = 8; return DT_F64; }
+    if (!strcmp(t, "float")) { *esize = 4; return DT_F32; }
+    if (!strcmp(t, "bf16") || !strcmp(t, "bfloat16")) { *esize = 2; return DT_BF16; }
+    return -1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Built-in kernel table
+// ------------------------------------------------------------------------------------------
+
+Offset off(int a, int b, int c) { return Offset{{a, b, c}}; }
+
+void register_builtins(Ctx &c)
+{
+    auto add = [&](KernelDef k) { c.kernels[k.name] = k; };
+    const int ALL = OFFSET_ALL;
+    {   // Sec. 5, Jacobi kernel 1: use B at (0,-1) (0,+1) (-1,0) (+1,0), define A at (0,0)
+        KernelDef k;
+        k.name = "jacobi2d"; k.kind = K_JACOBI2D; k.narr = 2; k.space = 1;
+        k.use = {{off(0, -1, 0), off(0, 1, 0), off(-1, 0, 0), off(1, 0, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // Sec. 5, Jacobi kernel 2: B = A with zero offsets
+        KernelDef k;
+        k.name = "copy"; k.kind = K_COPY; k.narr = 2; k.space = 1;
+        k.use = {{off(0, 0, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // 3-D 7-point analogue of Jacobi kernel 1
+        KernelDef k;
+        k.name = "stencil3d"; k.kind = K_STENCIL3D; k.narr = 2; k.space = 1;
+        k.use = {{off(0, 0, -1), off(0, 0, 1), off(0, -1, 0), off(0, 1, 0), off(-1, 0, 0), off(1, 0, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // residual field R = (X - Y)^2
+        KernelDef k;
+        k.name = "sqdiff"; k.kind = K_SQDIFF; k.narr = 3; k.space = 2;
+        k.use = {{off(0, 0, 0)}, {off(0, 0, 0)}, {}};
+        k.def = {{}, {}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // Listing 3: use(A,(0,*)) use(B,(*,0)) def(C,(0,0)); args A, B, C, alpha, beta, ni, nj, nk
+        KernelDef k;
+        k.name = "gemm"; k.kind = K_GEMM; k.narr = 3; k.nscal_f = 2; k.nscal_i = 3; k.space = 2;
+        k.use = {{off(0, ALL, 0)}, {off(ALL, 0, 0)}, {}};
+        k.def = {{}, {}, {off(0, 0, 0)}};
+        add(k);
+        k.name = "trmm"; k.kind = K_TRMM; k.nscal_i = 0;
+        add(k);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Arrays: state interning and device buffers
+// ------------------------------------------------------------------------------------------
+
+uint64_t mix64(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+uint64_t hash_state(const GState &s)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t p = 0; p < s.own.size(); p++) {
+        h = mix64(h, (uint64_t)set_volume(s.own[p]) * 31 + p);
+        h = mix64(h, (uint64_t)set_volume(s.stale[p]) * 37 + p);
+        for (const Box &b : s.own[p])
+            for (int d = 0; d < 3; d++) h = mix64(h, (uint64_t)(b.lo[d] * 131 + b.hi[d]));
+    }
+    return h;
+}
+
+bool state_equal(const GState &a, const GState &b)
+{
+    if (a.hash != b.hash || a.own.size() != b.own.size()) return false;
+    for (size_t p = 0; p < a.own.size(); p++) {
+        if (!set_equal(a.own[p], b.own[p])) return false;
+        if (!set_equal(a.stale[p], b.stale[p])) return false;
+    }
+    return true;
+}
+
+int intern(HDArray *a, GState s)
+{
+    s.hash = hash_state(s);
+    for (size_t i = 0; i < a->states.size(); i++)
+        if (state_equal(a->states[i], s)) return (int)i;
+    if (a->states.size() >= 4096) {  // bound the table: keep only the current state
+        GState cur = a->states[a->cur];
+        a->states.clear();
+        a->states.push_back(cur);
+        a->cur = 0;
+        a->generation++;
+        if (state_equal(a->states[0], s)) return 0;
+    }
+    a->states.push_back(std::move(s));
+    return (int)a->states.size() - 1;
+}
+
+// Grow the number of tracked devices: a new device holds nothing that has been written.
+void grow_devices(HDArray *a, int P)
+{
+    if (P <= a->P) return;
+    for (GState &s : a->states) {
+        BoxSet written;
+        for (const BoxSet &o : s.own) written = set_union(written, o);
+        while ((int)s.own.size() < P) {
+            s.own.push_back({});
+            s.stale.push_back(written);
+        }
+        s.hash = hash_state(s);
+    }
+    a->buf.resize(P);
+    a->P = P;
+}
+
+int64_t align_down(int64_t v, int64_t a) { return v >= 0 ? (v / a) * a : -(((-v) + a - 1) / a) * a; }
+int64_t align_up(int64_t v, int64_t a) { return align_down(v + a - 1, a); }
+
+// Element offset of coordinate e (user order) inside a device buffer.
+int64_t elem_off(const DevBuf &b, const int64_t e[3])
+{
+    return (e[0] - b.alloc.lo[0]) * b.st[0] + (e[1] - b.alloc.lo[1]) * b.st[1] +
+           (e[2] - b.alloc.lo[2]) * b.st[2];
+}
+
+void set_strides(const HDArray *a, DevBuf &b)
+{
+    const Box &x = b.alloc;
+    int64_t ext[3];
+    for (int d = 0; d < 3; d++) ext[d] = x.hi[d] - x.lo[d];
+    b.st[0] = b.st[1] = b.st[2] = 0;
+    if (a->dim == 1) {
+        b.st[0] = 1;
+    } else if (a->dim == 2) {
+        b.st[1] = 1;
+        b.st[0] = ext[1];
+    } else {
+        b.st[2] = 1;
+        b.st[1] = ext[2];
+        b.st[0] = ext[2] * ext[1];
+    }
+}
+
+int copy_box_d2d(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &bx);
+
+// Make device p's buffer of a cover box `need` (coordinates), reallocating if necessary.
+int ensure_buffer(HDArray *a, int p, const Box &need)
+{
+    if (need.empty() || g->host_only) return HDARRAY_OK;
+    DevBuf &b = a->buf[p];
+    if (b.ptr && box_contains(b.alloc, need)) return HDARRAY_OK;
+    if (g->recording) g->rec_invalid = true;  // recorded launches would point at the old buffer
+    Box nb = b.ptr ? box_hull(b.alloc, need) : need;
+    const int in = a->dim - 1;
+    const int64_t al = 128 / a->esize;
+    nb.lo[in] = align_down(nb.lo[in], al);
+    nb.hi[in] = align_up(nb.hi[in], al);
+    DevBuf nbuf;
+    nbuf.alloc = nb;
+    set_strides(a, nbuf);
+    nbuf.bytes = (size_t)nb.volume() * a->esize;
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, nbuf.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return HDARRAY_ERR_NOMEM;
+    }
+    nbuf.ptr = (char *)ptr;
+    CUDA_TRY(cudaMemsetAsync(nbuf.ptr, 0, nbuf.bytes, g->stream));
+    if (b.ptr) {
+        int rc = copy_box_d2d(a, b, nbuf, b.alloc);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        cudaFree(b.ptr);
+    }
+    b = nbuf;
+    a->epoch++;
+    return HDARRAY_OK;
+}
+
+// 3-level view of a box: outer x mid rows of inner contiguous elements.
+struct View3 {
+    int64_t n_outer, n_mid, n_inner;
+    int64_t s_outer, s_mid;  // element strides in the buffer
+};
+
+View3 view_of(const HDArray *a, const DevBuf &b, const Box &bx)
+{
+    View3 v;
+    if (a->dim == 1) {
+        v.n_outer = 1; v.n_mid = 1; v.n_inner = bx.hi[0] - bx.lo[0];
+        v.s_outer = 0; v.s_mid = 0;
+    } else if (a->dim == 2) {
+        v.n_outer = 1; v.n_mid = bx.hi[0] - bx.lo[0]; v.n_inner = bx.hi[1] - bx.lo[1];
+        v.s_outer = 0; v.s_mid = b.st[0];
+    } else {
+        v.n_outer = bx.hi[0] - bx.lo[0]; v.n_mid = bx.hi[1] - bx.lo[1]; v.n_inner = bx.hi[2] - bx.lo[2];
+        v.s_outer = b.st[0]; v.s_mid = b.st[1];
+    }
+    return v;
+}
+
+int vec_for(std::initializer_list<int64_t> vals)
+{
+    for (int v : {16, 8, 4, 2}) {
+        bool ok = true;
+        for (int64_t x : vals) ok = ok && (x % v == 0);
+        if (ok) return v;
+    }
+    return 1;
+}
+
+const int64_t TASK_BYTES = 256 * 1024;
+
+// Append copy tasks moving box bx of array a from device buffer src to device buffer dst.
+void copy_tasks(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &bx,
+                std::vector<CopyTask> &out)
+{
+    if (bx.empty()) return;
+    View3 vs = view_of(a, src, bx), vd = view_of(a, dst, bx);
+    const int64_t es = a->esize;
+    CopyTask t;
+    t.src = src.ptr + elem_off(src, bx.lo) * es;
+    t.dst = dst.ptr + elem_off(dst, bx.lo) * es;
+    t.s_outer = vs.s_outer * es;
+    t.s_mid = vs.s_mid * es;
+    t.d_outer = vd.s_outer * es;
+    t.d_mid = vd.s_mid * es;
+    t.n_mid = (int32_t)vs.n_mid;
+    t.inner = (int32_t)(vs.n_inner * es);
+    t.vec = vec_for({(int64_t)(uintptr_t)t.src, (int64_t)(uintptr_t)t.dst, t.s_outer, t.s_mid,
+                     t.d_outer, t.d_mid, (int64_t)t.inner});
+    if (t.vec < 2) t.vec = 2;
+    t.pad = 0;
+    const int64_t rows = vs.n_outer * vs.n_mid;
+    const int64_t per = std::max<int64_t>(1, TASK_BYTES / std::max<int64_t>(1, t.inner));
+    for (int64_t r = 0; r < rows; r += per) {
+        t.row_begin = (int32_t)r;
+        t.row_end = (int32_t)std::min(rows, r + per);
+        out.push_back(t);
+    }
+}
+
+int upload(const std::vector<std::pair<const void *, size_t>> &parts, std::shared_ptr<DevMem> &mem,
+           std::vector<const char *> &addrs)
+{
+    size_t total = 0;
+    std::vector<size_t> offs;
+    for (auto &p : parts) {
+        offs.push_back(total);
+        total += (p.second + 255) / 256 * 256;
+    }
+    mem = std::make_shared<DevMem>();
+    addrs.clear();
+    if (total == 0) {
+        for (size_t i = 0; i < parts.size(); i++) addrs.push_back(nullptr);
+        return HDARRAY_OK;
+    }
+    if (cudaMalloc(&mem->ptr, total) != cudaSuccess) {
+        cudaGetLastError();
+        mem->ptr = nullptr;
+        return HDARRAY_ERR_NOMEM;
+    }
+    mem->bytes = total;
+    std::vector<char> host(total, 0);
+    for (size_t i = 0; i < parts.size(); i++)
+        if (parts[i].second) memcpy(host.data() + offs[i], parts[i].first, parts[i].second);
+    CUDA_TRY(cudaMemcpy(mem->ptr, host.data(), total, cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < parts.size(); i++) addrs.push_back((const char *)mem->ptr + offs[i]);
+    return HDARRAY_OK;
+}
+
+int copy_box_d2d(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &bx)
+{
+    std::vector<CopyTask> tasks;
+    copy_tasks(a, src, dst, bx, tasks);
+    if (tasks.empty()) return HDARRAY_OK;
+    std::shared_ptr<DevMem> mem;
+    std::vector<const char *> addr;
+    int rc = upload({{tasks.data(), tasks.size() * sizeof(CopyTask)}}, mem, addr);
+    if (rc) return rc;
+    CUDA_TRY(launch_copy((const CopyTask *)addr[0], (int)tasks.size(), g->stream));
+    g->counters[0]++;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return HDARRAY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Communication generation (Eq. 1-4)
+// ------------------------------------------------------------------------------------------
+
+// The message step for one array: for every device p, the elements of LUSE_p it does not hold
+// come from their last writers.  SEND_{q,p} = sGDEF_{q,p} n LUSE_p = own[q] n stale[p] n LUSE_p
+// (Eq. 1); RECV_{p,q} = SEND_{q,p} (Eq. 2).  Afterwards p holds all of LUSE_p (the subtraction of
+// Eq. 3-4).
+int use_step(GState &s, const std::vector<BoxSet> &luse, std::vector<Move> &moves)
+{
+    const int P = (int)s.own.size();
+    for (int p = 0; p < (int)luse.size() && p < P; p++) {
+        if (luse[p].empty()) continue;
+        BoxSet need = set_intersect(luse[p], s.stale[p]);
+        if (need.empty()) continue;
+        int64_t got = 0;
+        for (int q = 0; q < P; q++) {
+            if (q == p) continue;
+            BoxSet m = set_intersect(s.own[q], need);
+            for (const Box &b : m) {
+                moves.push_back(Move{q, p, b});
+                got += b.volume();
+            }
+        }
+        if (got != set_volume(need)) return HDARRAY_ERR_STATE;  // an element nobody holds
+        s.stale[p] = set_subtract(s.stale[p], luse[p]);
+    }
+    return HDARRAY_OK;
+}
+
+// The definition step (Eq. 3-4, last writer wins): device p becomes the writer of LDEF_p, every
+// other device's copy of it becomes stale, and older writers stop owning it.
+int def_step(GState &s, const std::vector<BoxSet> &ldef)
+{
+    const int P = (int)s.own.size();
+    for (int p = 0; p < (int)ldef.size(); p++)
+        for (int q = p + 1; q < (int)ldef.size(); q++)
+            if (!ldef[p].empty() && !ldef[q].empty() && set_overlaps(ldef[p], ldef[q]))
+                return HDARRAY_ERR_RACE;
+    for (int p = 0; p < (int)ldef.size() && p < P; p++) {
+        const BoxSet &d = ldef[p];
+        if (d.empty()) continue;
+        for (int r = 0; r < P; r++) {
+            if (r == p) {
+                s.own[r] = set_union(s.own[r], d);
+                s.stale[r] = set_subtract(s.stale[r], d);
+            } else {
+                if (!s.own[r].empty()) s.own[r] = set_subtract(s.own[r], d);
+                s.stale[r] = set_union(s.stale[r], d);
+            }
+        }
+    }
+    return HDARRAY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Sections of a call (LUSE/LDEF, Sec. 3 offset clauses and absolute sections)
+// ------------------------------------------------------------------------------------------
+
+BoxSet clip_set(const std::vector<Box> &boxes, const HDArray *a)
+{
+    Box ext = make_box(0, 0, 0, a->n[0], a->n[1], a->n[2]);
+    std::vector<Box> c;
+    for (const Box &b : boxes) {
+        Box x = box_intersect(b, ext);
+        if (!x.empty()) c.push_back(x);
+    }
+    return set_from_boxes(c);
+}
+
+void clause_sets(const Part &pt, const HDArray *a, const std::vector<Offset> &offs,
+                 const std::map<int, std::vector<Box>> *absolute, std::vector<BoxSet> &out)
+{
+    out.assign(pt.nparts, BoxSet{});
+    if (absolute) {
+        for (auto &kv : *absolute)
+            if (kv.first >= 0 && kv.first < pt.nparts) out[kv.first] = clip_set(kv.second, a);
+        return;
+    }
+    if (offs.empty()) return;
+    for (int p = 0; p < pt.nparts; p++) {
+        const Box &w = pt.box[p];
+        if (w.empty()) continue;
+        std::vector<Box> bs;
+        for (const Offset &o : offs) bs.push_back(offset_box(w, o.o, a->n));
+        out[p] = set_from_boxes(bs);
+    }
+}
+
+std::string memo_key(const KernelDef &k, int part, const std::vector<HDArray *> &args,
+                     const std::vector<uint64_t> &absv)
+{
+    std::string key = k.name;
+    char buf[96];
+    snprintf(buf, sizeof(buf), "|%llu|%d", (unsigned long long)k.version, part);
+    key += buf;
+    for (size_t i = 0; i < args.size(); i++) {
+        snprintf(buf, sizeof(buf), "|%llu:%llu:%d:%llu", (unsigned long long)args[i]->uid,
+                 (unsigned long long)args[i]->generation, args[i]->cur,
+                 (unsigned long long)absv[i]);
+        key += buf;
+    }
+    return key;
+}
+
+// ------------------------------------------------------------------------------------------
+// Compiling a plan into launches
+// ------------------------------------------------------------------------------------------
+
+std::string epoch_sig(const Plan &pl)
+{
+    std::string s;
+    char buf[48];
+    for (HDArray *a : pl.args) {
+        snprintf(buf, sizeof(buf), "%llu,", (unsigned long long)a->epoch);
+        s += buf;
+    }
+    return s;
+}
+
+// Tiles of the fused Jacobi kernel for one device.  Returns false if the device's incoming
+// sections are not exactly the halo strips of its tiles (then the exchange runs as a separate
+// copy launch).
+bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
+                  const std::vector<Move> &recv, bool want_segs, Sten2DHost &h)
+{
+    const DevBuf &bx = X->buf[p], &by = Y->buf[p];
+    StenPart2D P;
+    P.x = bx.ptr;
+    P.y = by.ptr;
+    P.xlo0 = bx.alloc.lo[0];
+    P.xlo1 = bx.alloc.lo[1];
+    P.xs = bx.st[0];
+    P.ylo0 = by.alloc.lo[0];
+    P.ylo1 = by.alloc.lo[1];
+    P.ys = by.st[0];
+    h.parts.push_back(P);
+    const int VEC = 16 / X->esize, BAND = 32 * VEC;
+    const int H = std::max(1, g->tile_rows);
+    bool exact = true;
+    int64_t covered = 0, need = 0;
+    for (const Move &m : recv) {
+        need += m.box.volume();
+        if (box_overlaps(m.box, W)) exact = false;
+    }
+    const int64_t cb0 = align_down(W.lo[1], VEC);
+    for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += H) {
+        for (int64_t cb = cb0; cb < W.hi[1]; cb += BAND) {
+            StenTile2D t;
+            t.part = part_index;
+            t.r0 = (int32_t)rb;
+            t.r1 = (int32_t)std::min<int64_t>(rb + H, W.hi[0]);
+            t.c0 = (int32_t)std::max<int64_t>(W.lo[1], cb);
+            t.c1 = (int32_t)std::min<int64_t>(W.hi[1], cb + BAND);
+            t.cb = (int32_t)cb;
+            t.seg0 = (int32_t)h.segs.size();
+            t.nseg = 0;
+            if (want_segs && exact) {
+                const Box strips[4] = {
+                    make_box(t.r0 - 1, t.c0, 0, t.r0, t.c1, 1), make_box(t.r1, t.c0, 0, t.r1 + 1, t.c1, 1),
+                    make_box(t.r0, t.c0 - 1, 0, t.r1, t.c0, 1), make_box(t.r0, t.c1, 0, t.r1, t.c1 + 1, 1)};
+                for (const Move &m : recv) {
+                    const DevBuf &src = X->buf[m.src];
+                    for (int s = 0; s < 4; s++) {
+                        Box I = box_intersect(m.box, strips[s]);
+                        if (I.empty()) continue;
+                        Seg sg;
+                        sg.src = src.ptr + elem_off(src, I.lo) * X->esize;
+                        sg.dst = bx.ptr + elem_off(bx, I.lo) * X->esize;
+                        if (s < 2) {  // a row run
+                            sg.n = (int32_t)(I.hi[1] - I.lo[1]);
+                            sg.ss = 1;
+                            sg.ds = 1;
+                        } else {      // a column run
+                            sg.n = (int32_t)(I.hi[0] - I.lo[0]);
+                            sg.ss = src.st[0];
+                            sg.ds = bx.st[0];
+                        }
+                        sg.pad = 0;
+                        covered += I.volume();
+                        h.segs.push_back(sg);
+                        t.nseg++;
+                    }
+                }
+            }
+            h.tiles.push_back(t);
+        }
+    }
+    return exact && covered == need;
+}
+
+int compile_plan(Plan &pl)
+{
+    pl.launches.clear();
+    pl.copy_host.clear();
+    pl.s2 = Sten2DHost{};
+    pl.fused = false;
+    pl.tables.reset();
+    const KernelDef &k = *pl.k;
+    const Part &pt = g->parts[pl.part];
+    const bool plain = g->mode == HDARRAY_MODE_PLAIN;
+    std::vector<std::pair<const void *, size_t>> blobs;
+
+    // every exchange of every array, as copy tasks (one group per move for the plain form)
+    std::vector<CopyTask> xfer;
+    std::vector<std::pair<int, int>> xfer_groups;  // [begin, end) per move
+    auto add_moves = [&](const ArrStep &st) {
+        for (const Move &m : st.moves) {
+            int b = (int)xfer.size();
+            copy_tasks(st.a, st.a->buf[m.src], st.a->buf[m.dst], m.box, xfer);
+            xfer_groups.push_back({b, (int)xfer.size()});
+        }
+    };
+
+    if (k.kind == K_JACOBI2D) {
+        HDArray *X = pl.args[0], *Y = pl.args[1];
+        const ArrStep *sx = nullptr;
+        for (const ArrStep &st : pl.steps)
+            if (st.a == X) sx = &st;
+        bool fused = !plain;
+        Sten2DHost h;
+        h.dtype = X->dtype;
+        std::vector<std::pair<int, int>> dev_ranges;
+        int idx = 0;
+        for (int p = 0; p < pt.nparts; p++) {
+            if (pt.box[p].empty()) continue;
+            std::vector<Move> recv;
+            if (sx)
+                for (const Move &m : sx->moves)
+                    if (m.dst == p) recv.push_back(m);
+            int t0 = (int)h.tiles.size();
+            bool ok = jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h);
+            if (!ok) fused = false;
+            dev_ranges.push_back({t0, (int)h.tiles.size()});
+        }
+        if (!fused) {  // drop the segments: the exchange runs as copies
+            h.segs.clear();
+            for (StenTile2D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
+            if (sx) add_moves(*sx);
+        }
+        blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
+        blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart2D)});
+        blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile2D)});
+        blobs.push_back({h.segs.data(), h.segs.size() * sizeof(Seg)});
+        std::vector<const char *> addr;
+        int rc = upload(blobs, pl.tables, addr);
+        if (rc) return rc;
+        const CopyTask *dx = (const CopyTask *)addr[0];
+        if (plain) {
+            for (auto &gr : xfer_groups)
+                if (gr.second > gr.first) {
+                    LaunchRec L; L.kind = L_COPY; L.p0 = dx + gr.first; L.n0 = gr.second - gr.first;
+                    pl.launches.push_back(L);
+                }
+            for (auto &r : dev_ranges) {
+                if (r.second <= r.first) continue;
+                LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
+                L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
+                L.n0 = r.second - r.first; L.n1 = g->warps_per_cta;
+                pl.launches.push_back(L);
+            }
+        } else {
+            if (!xfer.empty()) {
+                LaunchRec L; L.kind = L_COPY; L.p0 = dx; L.n0 = (int64_t)xfer.size();
+                pl.launches.push_back(L);
+            }
+            if (!h.tiles.empty()) {
+                LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
+                L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = g->warps_per_cta;
+                pl.launches.push_back(L);
+            }
+        }
+        pl.fused = fused;
+        pl.copy_host = xfer;
+        pl.s2 = std::move(h);
+        return HDARRAY_OK;
+    }
+
+    for (const ArrStep &st : pl.steps) add_moves(st);
+    std::vector<CopyTask> local;       // within-device copies (kernel "copy")
+    std::vector<std::pair<int, int>> local_groups;
+    std::vector<PwTask> pw;
+    std::vector<std::pair<int, int>> pw_groups;
+    std::vector<GemmPart> gp;
+    int max_rows = 0, max_cols = 0;
+    for (int p = 0; p < pt.nparts; p++) {
+        const Box &W = pt.box[p];
+        if (W.empty()) continue;
+        if (k.kind == K_COPY) {
+            int b = (int)local.size();
+            copy_tasks(pl.args[0], pl.args[0]->buf[p], pl.args[1]->buf[p], W, local);
+            local_groups.push_back({b, (int)local.size()});
+        } else if (k.kind == K_SQDIFF) {
+            HDArray *X = pl.args[0], *Y = pl.args[1], *R = pl.args[2];
+            const DevBuf &bx = X->buf[p], &by = Y->buf[p], &br = R->buf[p];
+            View3 vx = view_of(X, bx, W), vy = view_of(Y, by, W), vr = view_of(R, br, W);
+            PwTask t;
+            t.x = bx.ptr + elem_off(bx, W.lo) * X->esize;
+            t.y = by.ptr + elem_off(by, W.lo) * Y->esize;
+            t.r = (double *)(br.ptr + elem_off(br, W.lo) * 8);
+            t.xs_outer = vx.s_outer; t.xs_mid = vx.s_mid;
+            t.ys_outer = vy.s_outer; t.ys_mid = vy.s_mid;
+            t.rs_outer = vr.s_outer; t.rs_mid = vr.s_mid;
+            t.n_mid = (int32_t)vx.n_mid; t.n_inner = (int32_t)vx.n_inner;
+            const int64_t rows = vx.n_outer * vx.n_mid;
+            const int64_t per = std::max<int64_t>(1, 65536 / std::max<int64_t>(1, vx.n_inner));
+            int b = (int)pw.size();
+            for (int64_t r = 0; r < rows; r += per) {
+                t.row_begin = (int32_t)r;
+                t.row_end = (int32_t)std::min(rows, r + per);
+                pw.push_back(t);
+            }
+            pw_groups.push_back({b, (int)pw.size()});
+        } else if (k.kind == K_GEMM || k.kind == K_TRMM) {
+            HDArray *A = pl.args[0], *B = pl.args[1], *C = pl.args[2];
+            const DevBuf &ba = A->buf[p], &bb = B->buf[p], &bc = C->buf[p];
+            GemmPart q;
+            q.a = ba.ptr; q.b = bb.ptr; q.c = bc.ptr;
+            q.alo0 = ba.alloc.lo[0]; q.alo1 = ba.alloc.lo[1]; q.as = ba.st[0];
+            q.blo0 = bb.alloc.lo[0]; q.blo1 = bb.alloc.lo[1]; q.bs = bb.st[0];
+            q.clo0 = bc.alloc.lo[0]; q.clo1 = bc.alloc.lo[1]; q.cs = bc.st[0];
+            q.i0 = (int32_t)W.lo[0]; q.i1 = (int32_t)W.hi[0];
+            q.j0 = (int32_t)W.lo[1]; q.j1 = (int32_t)W.hi[1];
+            q.nk = (int32_t)A->n[1];
+            q.lower = k.kind == K_TRMM ? 1 : 0;
+            gp.push_back(q);
+            max_rows = std::max<int>(max_rows, q.i1 - q.i0);
+            max_cols = std::max<int>(max_cols, q.j1 - q.j0);
+        } else {
+            return HDARRAY_ERR_UNSUPPORTED;
+        }
+    }
+    blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
+    blobs.push_back({local.data(), local.size() * sizeof(CopyTask)});
+    blobs.push_back({pw.data(), pw.size() * sizeof(PwTask)});
+    blobs.push_back({gp.data(), gp.size() * sizeof(GemmPart)});
+    std::vector<const char *> addr;
+    int rc = upload(blobs, pl.tables, addr);
+    if (rc) return rc;
+    auto push_copy = [&](const CopyTask *base, const std::vector<std::pair<int, int>> &groups, int64_t total) {
+        if (plain) {
+            for (auto &gr : groups)
+                if (gr.second > gr.first) {
+                    LaunchRec L; L.kind = L_COPY; L.p0 = base + gr.first; L.n0 = gr.second - gr.first;
+                    pl.launches.push_back(L);
+                }
+        } else if (total > 0) {
+            LaunchRec L; L.kind = L_COPY; L.p0 = base; L.n0 = total;
+            pl.launches.push_back(L);
+        }
+    };
+    push_copy((const CopyTask *)addr[0], xfer_groups, (int64_t)xfer.size());
+    push_copy((const CopyTask *)addr[1], local_groups, (int64_t)local.size());
+    if (!pw.empty()) {
+        auto add = [&](int b, int e) {
+            LaunchRec L; L.kind = L_SQDIFF; L.dtype = pl.args[0]->dtype;
+            L.p0 = (const PwTask *)addr[2] + b; L.n0 = e - b;
+            pl.launches.push_back(L);
+        };
+        if (plain) for (auto &gr : pw_groups) add(gr.first, gr.second);
+        else add(0, (int)pw.size());
+    }
+    if (!gp.empty()) {
+        auto add = [&](int b, int e, int mr, int mc) {
+            LaunchRec L; L.kind = L_GEMM64;
+            L.p0 = (const GemmPart *)addr[3] + b; L.n0 = e - b; L.n1 = mr; L.n2 = mc;
+            L.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
+            L.f1 = pl.scal.size() > 1 ? pl.scal[1] : 0.0;
+            pl.launches.push_back(L);
+        };
+        if (plain)
+            for (size_t i = 0; i < gp.size(); i++) add((int)i, (int)i + 1, gp[i].i1 - gp[i].i0, gp[i].j1 - gp[i].j0);
+        else
+            add(0, (int)gp.size(), max_rows, max_cols);
+    }
+    pl.copy_host = xfer;
+    return HDARRAY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Issuing launches (directly, into a batch, or into a graph recording)
+// ------------------------------------------------------------------------------------------
+
+int issue_recorded(const LaunchRec &L)
+{
+    cudaError_t e = issue(L, g->stream);
+    if (e != cudaSuccess) {
+        if (trace()) fprintf(stderr, "hdarray: launch failed: %s\n", cudaGetErrorString(e));
+        return HDARRAY_ERR_CUDA;
+    }
+    g->counters[0]++;
+    if (g->recording) g->rec.push_back(L);
+    return HDARRAY_OK;
+}
+
+int run_plan(const std::shared_ptr<Plan> &pl)
+{
+    if (g->host_only) return HDARRAY_OK;
+    for (const LaunchRec &L : pl->launches) {
+        int rc = issue_recorded(L);
+        if (rc) return rc;
+    }
+    if (g->recording) g->rec_refs.push_back(pl);
+    return HDARRAY_OK;
+}
+
+int flush_batch();
+
+// ------------------------------------------------------------------------------------------
+// Applying a kernel
+// ------------------------------------------------------------------------------------------
+
+int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray *> &a)
+{
+    for (HDArray *x : a)
+        if (!x || !g->arrays.count(x)) return HDARRAY_ERR_INVAL;
+    const HDArray *sp = a[k.space];
+    if (pt.dim != sp->dim) return HDARRAY_ERR_INVAL;
+    for (int d = 0; d < 3; d++)
+        if (pt.n[d] != sp->n[d]) return HDARRAY_ERR_INVAL;
+    auto same = [](const HDArray *x, const HDArray *y) {
+        return x->dim == y->dim && x->n[0] == y->n[0] && x->n[1] == y->n[1] && x->n[2] == y->n[2];
+    };
+    switch (k.kind) {
+    case K_JACOBI2D:
+    case K_STENCIL3D:
+        if (a[0] == a[1] || !same(a[0], a[1]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
+        if (a[0]->dim != (k.kind == K_JACOBI2D ? 2 : 3)) return HDARRAY_ERR_INVAL;
+        for (int p = 0; p < pt.nparts; p++) {  // every work element needs all its neighbours
+            const Box &w = pt.box[p];
+            if (w.empty()) continue;
+            for (int d = 0; d < a[0]->dim; d++)
+                if (w.lo[d] < 1 || w.hi[d] > a[0]->n[d] - 1) return HDARRAY_ERR_RANGE;
+        }
+        if (k.kind == K_STENCIL3D) return HDARRAY_ERR_UNSUPPORTED;
+        break;
+    case K_COPY:
+        if (a[0] == a[1] || !same(a[0], a[1]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
+        break;
+    case K_SQDIFF:
+        if (!same(a[0], a[1]) || !same(a[0], a[2]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
+        if (a[2]->dtype != DT_F64 || a[2] == a[0] || a[2] == a[1]) return HDARRAY_ERR_INVAL;
+        break;
+    case K_GEMM:
+    case K_TRMM: {
+        const HDArray *A = a[0], *B = a[1], *C = a[2];
+        if (A->dim != 2 || B->dim != 2 || C->dim != 2) return HDARRAY_ERR_INVAL;
+        if (A->n[0] != C->n[0] || A->n[1] != B->n[0] || B->n[1] != C->n[1]) return HDARRAY_ERR_INVAL;
+        if (C == A || C == B) return HDARRAY_ERR_INVAL;
+        if (A->dtype != B->dtype || A->dtype != C->dtype) return HDARRAY_ERR_INVAL;
+        if (A->dtype != DT_F64) return HDARRAY_ERR_UNSUPPORTED;
+        break;
+    }
+    }
+    return HDARRAY_OK;
+}
+
+int apply(const char *kname, int part, const std::vector<HDArray *> &args, const std::vector<double> &scal)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!kname) return HDARRAY_ERR_INVAL;
+    auto kit = g->kernels.find(kname);
+    if (kit == g->kernels.end()) return HDARRAY_ERR_INVAL;
+    const KernelDef &k = kit->second;
+    if (part < 0 || part >= (int)g->parts.size()) return HDARRAY_ERR_INVAL;
+    if ((int)args.size() != k.narr) return HDARRAY_ERR_INVAL;
+    const Part &pt = g->parts[part];
+    int rc = validate_args(k, pt, args);
+    if (rc) return rc;
+    for (HDArray *a : args) grow_devices(a, pt.nparts);
+
+    std::vector<uint64_t> absv(args.size(), 0);
+    std::vector<const Ctx::AbsSpec *> abss(args.size(), nullptr);
+    for (size_t i = 0; i < args.size(); i++) {
+        auto it = g->abs.find(std::make_tuple(k.name, part, args[i]->uid));
+        if (it != g->abs.end()) {
+            absv[i] = it->second.version;
+            abss[i] = &it->second;
+        }
+    }
+    const std::string key = memo_key(k, part, args, absv);
+    std::shared_ptr<Plan> pl;
+    auto mit = g->memo.find(key);
+    if (mit != g->memo.end()) {
+        pl = mit->second;
+        g->counters[3]++;
+    } else {
+        pl = std::make_shared<Plan>();
+        pl->id = g->next_plan++;
+        pl->k = &k;
+        pl->part = part;
+        pl->args = args;
+        pl->scal = scal;
+        pl->luse.resize(args.size());
+        pl->ldef.resize(args.size());
+        for (size_t i = 0; i < args.size(); i++) {
+            const auto *au = abss[i] && abss[i]->has_use ? &abss[i]->use : nullptr;
+            const auto *ad = abss[i] && abss[i]->has_def ? &abss[i]->def : nullptr;
+            clause_sets(pt, args[i], k.use[i], au, pl->luse[i]);
+            clause_sets(pt, args[i], k.def[i], ad, pl->ldef[i]);
+        }
+        // one step per distinct array: union of its arguments' sections
+        for (size_t i = 0; i < args.size(); i++) {
+            bool seen = false;
+            for (ArrStep &st : pl->steps) seen = seen || st.a == args[i];
+            if (seen) continue;
+            ArrStep st;
+            st.a = args[i];
+            std::vector<BoxSet> U(pt.nparts), D(pt.nparts);
+            for (size_t j = i; j < args.size(); j++) {
+                if (args[j] != args[i]) continue;
+                for (int p = 0; p < pt.nparts; p++) {
+                    U[p] = set_union(U[p], pl->luse[j][p]);
+                    D[p] = set_union(D[p], pl->ldef[j][p]);
+                }
+            }
+            for (int p = 0; p < pt.nparts; p++) {
+                st.used = st.used || !U[p].empty();
+                st.defined = st.defined || !D[p].empty();
+            }
+            GState s = args[i]->states[args[i]->cur];
+            st.pre = args[i]->cur;
+            rc = use_step(s, U, st.moves);
+            if (rc) return rc;
+            rc = def_step(s, D);
+            if (rc) return rc;
+            st.post = intern(args[i], std::move(s));
+            pl->steps.push_back(std::move(st));
+        }
+        g->memo[key] = pl;
+        g->counters[2]++;
+        if (trace()) {
+            int64_t nb = 0;
+            for (auto &st : pl->steps) for (auto &m : st.moves) nb += m.box.volume() * st.a->esize;
+            fprintf(stderr, "hdarray: plan %llu for %s part %d: %lld bytes to move\n",
+                    (unsigned long long)pl->id, k.name.c_str(), part, (long long)nb);
+        }
+    }
+    // buffers must cover every device's sections before anything is compiled or launched
+    if (!g->host_only) {
+        for (size_t i = 0; i < args.size(); i++) {
+            for (int p = 0; p < pt.nparts; p++) {
+                Box need = box_hull(set_bbox(pl->luse[i][p]), set_bbox(pl->ldef[i][p]));
+                if (need.empty()) continue;
+                if (g->batching && !(args[i]->buf[p].ptr && box_contains(args[i]->buf[p].alloc, need))) {
+                    rc = flush_batch();
+                    if (rc) return rc;
+                }
+                rc = ensure_buffer(args[i], p, need);
+                if (rc) return rc;
+            }
+        }
+        // a plan may be shared by signatures whose buffers moved: recompile when they did
+        const std::string sig = epoch_sig(*pl);
+        if (pl->compiled_sig != sig) {
+            rc = compile_plan(*pl);
+            if (rc) return rc;
+            pl->compiled_sig = sig;
+        }
+    }
+    // bookkeeping moves on; the GPU work is issued now or at the end of the batch
+    for (ArrStep &st : pl->steps) {
+        if (g->recording && !g->rec_pre.count(st.a)) g->rec_pre[st.a] = {st.a->cur, st.a->generation};
+        st.a->cur = st.post;
+        if (st.used) st.a->last_moves = st.moves;
+        for (const Move &m : st.moves) g->counters[1] += m.box.volume() * st.a->esize;
+    }
+    if (g->batching) {
+        g->batch.push_back(pl);
+        return HDARRAY_OK;
+    }
+    return run_plan(pl);
+}
+
+// ------------------------------------------------------------------------------------------
+// Batches: independent calls fused into as few launches as possible
+// ------------------------------------------------------------------------------------------
+
+int flush_batch()
+{
+    std::vector<std::shared_ptr<Plan>> plans;
+    plans.swap(g->batch);
+    if (plans.empty() || g->host_only) return HDARRAY_OK;
+    // hazards: a defined array may appear in no other call of the batch
+    for (size_t i = 0; i < plans.size(); i++)
+        for (const ArrStep &si : plans[i]->steps) {
+            if (!si.defined) continue;
+            for (size_t j = 0; j < plans.size(); j++) {
+                if (j == i) continue;
+                for (const ArrStep &sj : plans[j]->steps)
+                    if (sj.a == si.a) return HDARRAY_ERR_RACE;
+            }
+        }
+    std::string key;
+    char buf[64];
+    for (auto &p : plans) {
+        snprintf(buf, sizeof(buf), "%llu/%s;", (unsigned long long)p->id, p->compiled_sig.c_str());
+        key += buf;
+    }
+    auto it = g->batch_cache.find(key);
+    if (it == g->batch_cache.end()) {
+        // merge: all exchanges first, then every fused 2-D stencil of the same type, then the rest
+        std::vector<CopyTask> copies;
+        std::map<int, Sten2DHost> sten;
+        std::vector<LaunchRec> rest;
+        for (auto &p : plans) {
+            if (p->k->kind == K_JACOBI2D && g->mode == HDARRAY_MODE_FUSED) {
+                copies.insert(copies.end(), p->copy_host.begin(), p->copy_host.end());
+                Sten2DHost &h = sten[p->s2.dtype];
+                h.dtype = p->s2.dtype;
+                const int pbase = (int)h.parts.size(), sbase = (int)h.segs.size();
+                h.parts.insert(h.parts.end(), p->s2.parts.begin(), p->s2.parts.end());
+                h.segs.insert(h.segs.end(), p->s2.segs.begin(), p->s2.segs.end());
+                for (StenTile2D t : p->s2.tiles) {
+                    t.part += pbase;
+                    t.seg0 += sbase;
+                    h.tiles.push_back(t);
+                }
+            } else {
+                rest.insert(rest.end(), p->launches.begin(), p->launches.end());
+            }
+        }
+        std::vector<std::pair<const void *, size_t>> blobs;
+        blobs.push_back({copies.data(), copies.size() * sizeof(CopyTask)});
+        for (auto &kv : sten) {
+            blobs.push_back({kv.second.parts.data(), kv.second.parts.size() * sizeof(StenPart2D)});
+            blobs.push_back({kv.second.tiles.data(), kv.second.tiles.size() * sizeof(StenTile2D)});
+            blobs.push_back({kv.second.segs.data(), kv.second.segs.size() * sizeof(Seg)});
+        }
+        std::shared_ptr<DevMem> mem;
+        std::vector<const char *> addr;
+        int rc = upload(blobs, mem, addr);
+        if (rc) return rc;
+        std::vector<LaunchRec> ls;
+        if (!copies.empty()) {
+            LaunchRec L; L.kind = L_COPY; L.p0 = addr[0]; L.n0 = (int64_t)copies.size();
+            ls.push_back(L);
+        }
+        int ai = 1;
+        for (auto &kv : sten) {
+            LaunchRec L; L.kind = L_JACOBI2D; L.dtype = kv.first;
+            L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2];
+            L.n0 = (int64_t)kv.second.tiles.size(); L.n1 = g->warps_per_cta;
+            ai += 3;
+            if (L.n0 > 0) ls.push_back(L);
+        }
+        ls.insert(ls.end(), rest.begin(), rest.end());
+        if (g->batch_cache.size() > 64) g->batch_cache.clear();
+        it = g->batch_cache.emplace(key, std::make_pair(mem, ls)).first;
+    }
+    for (const LaunchRec &L : it->second.second) {
+        int rc = issue_recorded(L);
+        if (rc) return rc;
+    }
+    if (g->recording) {
+        g->rec_mems.push_back(it->second.first);
+        for (auto &p : plans) g->rec_refs.push_back(p);
+    }
+    return HDARRAY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Data movement between user arrays and device buffers (Write / Read / Reduce)
+// ------------------------------------------------------------------------------------------
+
+int check_part_for(const HDArray *a, int part)
+{
+    if (part < 0 || part >= (int)g->parts.size()) return HDARRAY_ERR_INVAL;
+    const Part &pt = g->parts[part];
+    if (pt.dim != a->dim) return HDARRAY_ERR_INVAL;
+    for (int d = 0; d < 3; d++)
+        if (pt.n[d] != a->n[d]) return HDARRAY_ERR_INVAL;
+    return HDARRAY_OK;
+}
+
+// host/device user array (dense, full size) <-> device buffer, one box
+int memcpy_box(const HDArray *a, const DevBuf &b, const Box &bx, void *user, bool to_device)
+{
+    const int64_t es = a->esize;
+    int64_t un[3], upos[3], bn[3], bpos[3], ext[3];
+    // map to (width = innermost, height = middle, depth = outer) for cudaMemcpy3D
+    int in = a->dim - 1;
+    int mid = a->dim >= 2 ? a->dim - 2 : -1;
+    int out = a->dim >= 3 ? 0 : -1;
+    auto pick = [&](int d, const int64_t *v, int64_t dflt) { return d >= 0 ? v[d] : dflt; };
+    ext[0] = (bx.hi[in] - bx.lo[in]) * es;
+    ext[1] = mid >= 0 ? bx.hi[mid] - bx.lo[mid] : 1;
+    ext[2] = out >= 0 ? bx.hi[out] - bx.lo[out] : 1;
+    un[0] = a->n[in] * es;
+    un[1] = pick(mid, a->n, 1);
+    upos[0] = bx.lo[in] * es;
+    upos[1] = mid >= 0 ? bx.lo[mid] : 0;
+    upos[2] = out >= 0 ? bx.lo[out] : 0;
+    const int64_t bw = (b.alloc.hi[in] - b.alloc.lo[in]);
+    bn[0] = bw * es;
+    bn[1] = mid >= 0 ? b.alloc.hi[mid] - b.alloc.lo[mid] : 1;
+    bpos[0] = (bx.lo[in] - b.alloc.lo[in]) * es;
+    bpos[1] = mid >= 0 ? bx.lo[mid] - b.alloc.lo[mid] : 0;
+    bpos[2] = out >= 0 ? bx.lo[out] - b.alloc.lo[out] : 0;
+    cudaMemcpy3DParms prm;
+    memset(&prm, 0, sizeof(prm));
+    cudaPitchedPtr up = make_cudaPitchedPtr(user, (size_t)un[0], (size_t)(un[0] / es), (size_t)un[1]);
+    cudaPitchedPtr bp = make_cudaPitchedPtr(b.ptr, (size_t)bn[0], (size_t)bw, (size_t)bn[1]);
+    cudaPos uo = make_cudaPos((size_t)upos[0], (size_t)upos[1], (size_t)upos[2]);
+    cudaPos bo = make_cudaPos((size_t)bpos[0], (size_t)bpos[1], (size_t)bpos[2]);
+    if (to_device) {
+        prm.srcPtr = up; prm.srcPos = uo; prm.dstPtr = bp; prm.dstPos = bo;
+    } else {
+        prm.srcPtr = bp; prm.srcPos = bo; prm.dstPtr = up; prm.dstPos = uo;
+    }
+    prm.extent = make_cudaExtent((size_t)ext[0], (size_t)ext[1], (size_t)ext[2]);
+    prm.kind = cudaMemcpyDefault;
+    CUDA_TRY(cudaMemcpy3DAsync(&prm, g->stream));
+    return HDARRAY_OK;
+}
+
+// A use of each device's region (Read, Reduce): exchange, then the bookkeeping.
+int use_regions(HDArray *a, const Part &pt)
+{
+    grow_devices(a, pt.nparts);
+    std::vector<BoxSet> U(pt.nparts);
+    for (int p = 0; p < pt.nparts; p++)
+        if (!pt.box[p].empty()) U[p] = BoxSet{pt.box[p]};
+    GState s = a->states[a->cur];
+    std::vector<Move> moves;
+    int rc = use_step(s, U, moves);
+    if (rc) return rc;
+    if (!g->host_only) {
+        for (int p = 0; p < pt.nparts; p++) {
+            rc = ensure_buffer(a, p, pt.box[p]);
+            if (rc) return rc;
+        }
+        std::vector<CopyTask> tasks;
+        for (const Move &m : moves) copy_tasks(a, a->buf[m.src], a->buf[m.dst], m.box, tasks);
+        if (!tasks.empty()) {
+            std::shared_ptr<DevMem> mem;
+            std::vector<const char *> addr;
+            rc = upload({{tasks.data(), tasks.size() * sizeof(CopyTask)}}, mem, addr);
+            if (rc) return rc;
+            LaunchRec L; L.kind = L_COPY; L.p0 = addr[0]; L.n0 = (int64_t)tasks.size();
+            rc = issue_recorded(L);
+            if (rc) return rc;
+            CUDA_TRY(cudaStreamSynchronize(g->stream));  // the tables are freed on return
+        }
+    }
+    for (const Move &m : moves) g->counters[1] += m.box.volume() * a->esize;
+    a->cur = intern(a, std::move(s));
+    a->last_moves = moves;
+    return HDARRAY_OK;
+}
+
+int write_impl(HDArray *a, const void *uA, int part)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!a || !g->arrays.count(a)) return HDARRAY_ERR_INVAL;
+    int rc = check_part_for(a, part);
+    if (rc) return rc;
+    if (g->recording) return HDARRAY_ERR_STATE;
+    if (g->batching) {
+        rc = flush_batch();
+        if (rc) return rc;
+    }
+    const Part &pt = g->parts[part];
+    grow_devices(a, pt.nparts);
+    std::vector<BoxSet> D(pt.nparts);
+    for (int p = 0; p < pt.nparts; p++)
+        if (!pt.box[p].empty()) D[p] = BoxSet{pt.box[p]};
+    GState s = a->states[a->cur];
+    rc = def_step(s, D);
+    if (rc) return rc;
+    if (!g->host_only && uA) {
+        for (int p = 0; p < pt.nparts; p++) {
+            if (pt.box[p].empty()) continue;
+            rc = ensure_buffer(a, p, pt.box[p]);
+            if (rc) return rc;
+            rc = memcpy_box(a, a->buf[p], pt.box[p], const_cast<void *>(uA), true);
+            if (rc) return rc;
+        }
+    }
+    a->cur = intern(a, std::move(s));
+    return HDARRAY_OK;
+}
+
+int read_impl(HDArray *a, void *uA, int part)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!a || !g->arrays.count(a)) return HDARRAY_ERR_INVAL;
+    int rc = check_part_for(a, part);
+    if (rc) return rc;
+    if (g->recording) return HDARRAY_ERR_STATE;
+    if (g->batching) {
+        rc = flush_batch();
+        if (rc) return rc;
+    }
+    const Part &pt = g->parts[part];
+    rc = use_regions(a, pt);
+    if (rc) return rc;
+    if (!g->host_only && uA) {
+        for (int p = 0; p < pt.nparts; p++) {
+            if (pt.box[p].empty()) continue;
+            rc = memcpy_box(a, a->buf[p], pt.box[p], uA, false);
+            if (rc) return rc;
+        }
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+    }
+    return HDARRAY_OK;
+}
+
+int ensure_reduce_scratch(int nblocks)
+{
+    if (g->red_blocks >= nblocks) return HDARRAY_OK;
+    if (g->red_partials) cudaFree(g->red_partials);
+    g->red_partials = nullptr;
+    if (cudaMalloc(&g->red_partials, sizeof(double) * nblocks + 256) != cudaSuccess) {
+        cudaGetLastError();
+        g->red_blocks = 0;
+        return HDARRAY_ERR_NOMEM;
+    }
+    g->red_blocks = nblocks;
+    return HDARRAY_OK;
+}
+
+int reduce_impl(HDArray *a, double *res, int op, int part)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!a || !g->arrays.count(a) || !res || op < 0 || op > 3) return HDARRAY_ERR_INVAL;
+    int rc = check_part_for(a, part);
+    if (rc) return rc;
+    if (g->recording) return HDARRAY_ERR_STATE;
+    if (g->batching) {
+        rc = flush_batch();
+        if (rc) return rc;
+    }
+    const Part &pt = g->parts[part];
+    for (int p = 0; p < pt.nparts; p++)
+        for (int q = p + 1; q < pt.nparts; q++)
+            if (box_overlaps(pt.box[p], pt.box[q])) return HDARRAY_ERR_INVAL;
+    rc = use_regions(a, pt);
+    if (rc) return rc;
+    if (g->host_only) {
+        *res = 0.0;
+        return HDARRAY_OK;
+    }
+    std::vector<RedTask> tasks;
+    for (int p = 0; p < pt.nparts; p++) {
+        const Box &W = pt.box[p];
+        if (W.empty()) continue;
+        const DevBuf &b = a->buf[p];
+        View3 v = view_of(a, b, W);
+        RedTask t;
+        t.x = b.ptr + elem_off(b, W.lo) * a->esize;
+        t.s_outer = v.s_outer;
+        t.s_mid = v.s_mid;
+        t.n_mid = (int32_t)v.n_mid;
+        t.n_inner = (int32_t)v.n_inner;
+        const int64_t rows = v.n_outer * v.n_mid;
+        const int64_t per = std::max<int64_t>(1, 65536 / std::max<int64_t>(1, v.n_inner));
+        for (int64_t r = 0; r < rows; r += per) {
+            t.row_begin = (int32_t)r;
+            t.row_end = (int32_t)std::min(rows, r + per);
+            tasks.push_back(t);
+        }
+    }
+    const double ident[4] = {0.0, 1.0, -__builtin_inf(), __builtin_inf()};
+    if (tasks.empty()) {
+        *res = ident[op];
+        return HDARRAY_OK;
+    }
+    const int nblocks = (int)std::min<size_t>(tasks.size(), (size_t)2 * g->nsm);
+    rc = ensure_reduce_scratch(nblocks);
+    if (rc) return rc;
+    std::shared_ptr<DevMem> mem;
+    std::vector<const char *> addr;
+    rc = upload({{tasks.data(), tasks.size() * sizeof(RedTask)}}, mem, addr);
+    if (rc) return rc;
+    CUDA_TRY(launch_reduce(a->dtype, op, (const RedTask *)addr[0], (int)tasks.size(), nblocks,
+                           g->red_partials, g->red_counter, g->red_result, g->stream));
+    g->counters[0]++;
+    CUDA_TRY(cudaMemcpyAsync(g->host_result, g->red_result, sizeof(double), cudaMemcpyDeviceToHost,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    *res = *g->host_result;
+    return HDARRAY_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Partitions
+// ------------------------------------------------------------------------------------------
+
+void split_even(int64_t a, int64_t b, int P, int p, int64_t *lo, int64_t *hi)
+{
+    const int64_t n = b - a, q = n / P, m = n % P;
+    *lo = a + p * q + std::min<int64_t>(p, m);
+    *hi = *lo + q + (p < m ? 1 : 0);
+}
+
+int make_partition(int type, int nparts, int dim, const int64_t *sizes, const int64_t *lo, const int64_t *hi)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (dim < 1 || dim > 3 || !sizes || !lo || !hi) return HDARRAY_ERR_INVAL;
+    if (nparts <= 0) nparts = g->ndev;
+    if (nparts > 32767) return HDARRAY_ERR_INVAL;
+    Part pt;
+    pt.dim = dim;
+    pt.nparts = nparts;
+    Box region = make_box(0, 0, 0, 1, 1, 1);
+    for (int d = 0; d < dim; d++) {
+        pt.n[d] = sizes[d];
+        if (sizes[d] < 1 || lo[d] < 0 || hi[d] > sizes[d] || lo[d] > hi[d]) return HDARRAY_ERR_RANGE;
+        region.lo[d] = lo[d];
+        region.hi[d] = hi[d];
+    }
+    if ((type == HDARRAY_COL || type == HDARRAY_BLOCK) && dim < 2) return HDARRAY_ERR_INVAL;
+    int Pr = 1, Pc = nparts;
+    if (type == HDARRAY_BLOCK) {
+        for (int d = 1; d * d <= nparts; d++)
+            if (nparts % d == 0) Pr = d;
+        Pc = nparts / Pr;
+    }
+    for (int p = 0; p < nparts; p++) {
+        Box b = region;
+        if (type == HDARRAY_ROW) split_even(region.lo[0], region.hi[0], nparts, p, &b.lo[0], &b.hi[0]);
+        else if (type == HDARRAY_COL) split_even(region.lo[1], region.hi[1], nparts, p, &b.lo[1], &b.hi[1]);
+        else if (type == HDARRAY_BLOCK) {
+            split_even(region.lo[0], region.hi[0], Pr, p / Pc, &b.lo[0], &b.hi[0]);
+            split_even(region.lo[1], region.hi[1], Pc, p % Pc, &b.lo[1], &b.hi[1]);
+        } else {
+            return HDARRAY_ERR_INVAL;
+        }
+        pt.box.push_back(b);
+    }
+    g->parts.push_back(pt);
+    return (int)g->parts.size() - 1;
+}
+
+int set_abs(const char *kname, int part, HDArray *a, int dev, const std::vector<Box> &boxes, bool use)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!kname || !a || !g->arrays.count(a) || dev < 0 || dev > 32767) return HDARRAY_ERR_INVAL;
+    if (part < 0 || part >= (int)g->parts.size()) return HDARRAY_ERR_INVAL;
+    Ctx::AbsSpec &s = g->abs[std::make_tuple(std::string(kname), part, a->uid)];
+    auto &m = use ? s.use : s.def;
+    auto &v = m[dev];
+    v.insert(v.end(), boxes.begin(), boxes.end());
+    if (use) s.has_use = true;
+    else s.has_def = true;
+    s.version = ++g->abs_version;
+    return HDARRAY_OK;
+}
+
+int abs_box(const char *kname, int part, HDArray *a, int dev, int dim, const int64_t *lo,
+            const int64_t *hi, bool use)
+{
+    if (!g || !a || !lo || !hi || dim != a->dim) return HDARRAY_ERR_INVAL;
+    Box b = make_box(0, 0, 0, 1, 1, 1);
+    for (int d = 0; d < dim; d++) {
+        b.lo[d] = lo[d];
+        b.hi[d] = hi[d];
+        if (lo[d] < 0 || hi[d] > a->n[d]) return HDARRAY_ERR_RANGE;
+    }
+    return set_abs(kname, part, a, dev, {b}, use);
+}
+
+int abs_trap(const char *kname, int part, HDArray *a, int dev, const int64_t *c, bool use)
+{
+    if (!g || !a || !c || a->dim != 2) return HDARRAY_ERR_INVAL;
+    BoxSet s;
+    if (!trapezoid_boxes(c, &s)) return HDARRAY_ERR_INVAL;
+    for (const Box &b : s)
+        if (b.lo[0] < 0 || b.hi[0] > a->n[0] || b.lo[1] < 0 || b.hi[1] > a->n[1]) return HDARRAY_ERR_RANGE;
+    return set_abs(kname, part, a, dev, std::vector<Box>(s.begin(), s.end()), use);
+}
+
+void free_array_buffers(HDArray *a)
+{
+    for (DevBuf &b : a->buf)
+        if (b.ptr) cudaFree(b.ptr);
+    a->buf.clear();
+}
+
+void drop_plans_of(HDArray *a)
+{
+    for (auto it = g->memo.begin(); it != g->memo.end();) {
+        bool hit = false;
+        for (HDArray *x : it->second->args) hit = hit || x == a;
+        if (hit) it = g->memo.erase(it);
+        else ++it;
+    }
+    g->batch_cache.clear();
+}
+
+int init_impl(int ndev, unsigned flags)
+{
+    if (g && g->inited) return HDARRAY_OK;
+    if (ndev < 1) return HDARRAY_ERR_INVAL;
+    g = new Ctx();
+    g->ndev = ndev;
+    g->host_only = (flags & HDARRAY_INIT_HOST_ONLY) != 0;
+    register_builtins(*g);
+    if (!g->host_only) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            g = nullptr;
+            return HDARRAY_ERR_CUDA;
+        }
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) g->nsm = prop.multiProcessorCount;
+        if (cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            g = nullptr;
+            return HDARRAY_ERR_CUDA;
+        }
+        g->stream = g->own_stream;
+        void *p = nullptr;
+        if (cudaMalloc(&p, 256) != cudaSuccess) {
+            cudaGetLastError();
+            return HDARRAY_ERR_NOMEM;
+        }
+        g->red_counter = (unsigned *)p;
+        g->red_result = (double *)((char *)p + 128);
+        cudaMemset(p, 0, 256);
+        if (cudaMallocHost(&g->host_result, sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return HDARRAY_ERR_NOMEM;
+        }
+        const char *tr = getenv("HDARRAY_TILE_ROWS");
+        if (tr && atoi(tr) > 0) g->tile_rows = atoi(tr);
+        const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
+        if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
+    }
+    g->inited = true;
+    return HDARRAY_OK;
+}
+
+}  // namespace
+
+namespace hda {
+
+DevMem::~DevMem()
+{
+    if (ptr) cudaFree(ptr);
+}
+
+cudaError_t issue(const LaunchRec &L, cudaStream_t s)
+{
+    switch (L.kind) {
+    case L_COPY: return launch_copy((const CopyTask *)L.p0, (int)L.n0, s);
+    case L_JACOBI2D:
+        return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                               (const Seg *)L.p2, (int)L.n1, s);
+    case L_SQDIFF: return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, s);
+    case L_GEMM64:
+        return launch_gemm_f64((const GemmPart *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, L.f0, L.f1, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace hda
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+
+extern "C" {
+
+int HDArrayInitEx(int ndev, unsigned flags) { return init_impl(ndev, flags); }
+
+int HDArrayInit(int argc, char *argv[], const char *kpath, const char *dpath)
+{
+    (void)argc;
+    (void)argv;
+    (void)kpath;
+    int ndev = 1;
+    const char *env = getenv("HDARRAY_NDEV");
+    if (env && atoi(env) > 0) ndev = atoi(env);
+    if (dpath) {
+        FILE *f = fopen(dpath, "r");
+        if (!f) return HDARRAY_ERR_INVAL;
+        int n = 0;
+        if (fscanf(f, "%d", &n) != 1 || n < 1) {
+            fclose(f);
+            return HDARRAY_ERR_INVAL;
+        }
+        fclose(f);
+        ndev = n;
+    }
+    int rc = init_impl(ndev, 0);
+    return rc < 0 ? rc : 0;
+}
+
+void HDArrayExit(void)
+{
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (auto &kv : g->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    g->graphs.clear();
+    g->memo.clear();
+    g->batch.clear();
+    g->batch_cache.clear();
+    g->rec_refs.clear();
+    g->rec_mems.clear();
+    for (HDArray *a : g->arrays) {
+        free_array_buffers(a);
+        delete a;
+    }
+    g->arrays.clear();
+    if (g->red_partials) cudaFree(g->red_partials);
+    if (g->red_counter) cudaFree(g->red_counter);
+    if (g->host_result) cudaFreeHost(g->host_result);
+    if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    delete g;
+    g = nullptr;
+}
+
+void HDArrayShowDeviceInfo(int devID)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, devID) != cudaSuccess) {
+        cudaGetLastError();
+        printf("HDArray device %d: no CUDA device\n", devID);
+        return;
+    }
+    printf("HDArray device %d: %s, sm_%d%d, %d SMs, %.1f GiB, %d logical devices\n", devID, prop.name,
+           prop.major, prop.minor, prop.multiProcessorCount, prop.totalGlobalMem / 1073741824.0,
+           g ? g->ndev : 0);
+}
+
+HDArray_t *HDArrayCreatev(const char *sym, const char *type, void *uA, int dim, const int64_t *sizes)
+{
+    (void)uA;
+    if (!g || !g->inited) {
+        set_err(HDARRAY_ERR_STATE);
+        return nullptr;
+    }
+    int esize = 0;
+    int dt = dtype_of(type, &esize);
+    if (dt < 0 || dim < 1 || dim > 3 || !sizes) {
+        set_err(HDARRAY_ERR_INVAL);
+        return nullptr;
+    }
+    HDArray *a = new HDArray();
+    a->sym = sym ? sym : "";
+    a->dtype = dt;
+    a->esize = esize;
+    a->dim = dim;
+    for (int d = 0; d < dim; d++) {
+        if (sizes[d] < 1 || sizes[d] > (int64_t)1 << 31) {
+            delete a;
+            set_err(HDARRAY_ERR_INVAL);
+            return nullptr;
+        }
+        a->n[d] = sizes[d];
+    }
+    a->uid = g->next_uid++;
+    a->states.push_back(GState{});
+    a->states[0].hash = hash_state(a->states[0]);
+    a->cur = 0;
+    g->arrays.insert(a);
+    return a;
+}
+
+HDArray_t *HDArrayCreate(const char *sym, const char *type, void *uA, int dim, ...)
+{
+    if (dim < 1 || dim > 3) {
+        set_err(HDARRAY_ERR_INVAL);
+        return nullptr;
+    }
+    int64_t sizes[3];
+    va_list ap;
+    va_start(ap, dim);
+    for (int d = 0; d < dim; d++) sizes[d] = va_arg(ap, int);
+    va_end(ap);
+    return HDArrayCreatev(sym, type, uA, dim, sizes);
+}
+
+int HDArrayFree(HDArray_t *hA)
+{
+    if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    drop_plans_of(hA);
+    for (auto it = g->abs.begin(); it != g->abs.end();) {
+        if (std::get<2>(it->first) == hA->uid) it = g->abs.erase(it);
+        else ++it;
+    }
+    free_array_buffers(hA);
+    g->arrays.erase(hA);
+    delete hA;
+    return HDARRAY_OK;
+}
+
+int HDArrayPartitionv(PART_T type, int nparts, int dim, const int64_t *sizes, const int64_t *lo,
+                      const int64_t *hi)
+{
+    return make_partition((int)type, nparts, dim, sizes, lo, hi);
+}
+
+int HDArrayPartition(PART_T type, int dim, ...)
+{
+    if (dim < 1 || dim > 3) return set_err(HDARRAY_ERR_INVAL);
+    int64_t s[3], lo[3], hi[3];
+    va_list ap;
+    va_start(ap, dim);
+    for (int d = 0; d < dim; d++) s[d] = va_arg(ap, int);
+    for (int d = 0; d < dim; d++) lo[d] = va_arg(ap, int);
+    for (int d = 0; d < dim; d++) hi[d] = va_arg(ap, int);
+    va_end(ap);
+    int rc = make_partition((int)type, 0, dim, s, lo, hi);
+    if (rc < 0) set_err(rc);
+    return rc;
+}
+
+int HDArrayPartitionManual(int dim, const int64_t *sizes, int nparts, const int64_t *lo, const int64_t *hi)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (dim < 1 || dim > 3 || nparts < 1 || nparts > 32767 || !sizes || !lo || !hi) return HDARRAY_ERR_INVAL;
+    Part pt;
+    pt.dim = dim;
+    pt.nparts = nparts;
+    for (int d = 0; d < dim; d++) {
+        if (sizes[d] < 1) return HDARRAY_ERR_INVAL;
+        pt.n[d] = sizes[d];
+    }
+    for (int p = 0; p < nparts; p++) {
+        Box b = make_box(0, 0, 0, 1, 1, 1);
+        for (int d = 0; d < dim; d++) {
+            b.lo[d] = lo[p * dim + d];
+            b.hi[d] = hi[p * dim + d];
+            if (b.lo[d] < 0 || b.hi[d] > sizes[d]) return HDARRAY_ERR_RANGE;
+        }
+        if (b.empty()) b = make_box(0, 0, 0, 0, 0, 0);
+        pt.box.push_back(b);
+    }
+    g->parts.push_back(pt);
+    return (int)g->parts.size() - 1;
+}
+
+int HDArrayApplyKernelv(const char *kName, int partID, int narr, HDArray_t *const *arrs, int nscal,
+                        const double *scal)
+{
+    if (narr < 0 || (narr > 0 && !arrs) || nscal < 0 || (nscal > 0 && !scal)) return HDARRAY_ERR_INVAL;
+    std::vector<HDArray *> a(arrs, arrs + narr);
+    std::vector<double> s(scal, scal + nscal);
+    int rc = apply(kName, partID, a, s);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+void HDArrayApplyKernel(const char *kName, int partID, ...)
+{
+    if (!g || !g->inited || !kName) {
+        set_err(HDARRAY_ERR_STATE);
+        return;
+    }
+    auto it = g->kernels.find(kName);
+    if (it == g->kernels.end()) {
+        set_err(HDARRAY_ERR_INVAL);
+        return;
+    }
+    const KernelDef &k = it->second;
+    std::vector<HDArray *> a;
+    std::vector<double> s;
+    va_list ap;
+    va_start(ap, partID);
+    for (int i = 0; i < k.narr; i++) a.push_back(va_arg(ap, HDArray *));
+    for (int i = 0; i < k.nscal_f; i++) s.push_back(va_arg(ap, double));
+    for (int i = 0; i < k.nscal_i; i++) s.push_back((double)va_arg(ap, int));
+    va_end(ap);
+    int rc = apply(kName, partID, a, s);
+    if (rc) set_err(rc);
+}
+
+int HDArrayWritev(HDArray_t *hA, const void *uA, int partID)
+{
+    int rc = write_impl(hA, uA, partID);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+void HDArrayWrite(HDArray_t *hA, void *uA, int partID) { HDArrayWritev(hA, uA, partID); }
+
+int HDArrayReadv(HDArray_t *hA, void *uA, int partID)
+{
+    int rc = read_impl(hA, uA, partID);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+void HDArrayRead(HDArray_t *hA, void *uA, int partID) { HDArrayReadv(hA, uA, partID); }
+
+int HDArrayReduceD(HDArray_t *hA, double *res, REDUCE_OP op, int partID)
+{
+    int rc = reduce_impl(hA, res, (int)op, partID);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+int HDArrayReducev(HDArray_t *hA, void *res, REDUCE_OP op, int partID)
+{
+    if (!res) return set_err(HDARRAY_ERR_INVAL);
+    double d = 0.0;
+    int rc = reduce_impl(hA, &d, (int)op, partID);
+    if (rc) return set_err(rc);
+    if (hA->dtype == DT_F64) {
+        *(double *)res = d;
+    } else if (hA->dtype == DT_F32) {
+        *(float *)res = (float)d;
+    } else {  // bfloat16, round to nearest even
+        float f = (float)d;
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        uint32_t up = u >> 16, low = u & 0xffffu;
+        if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x7fffffu)) up |= 0x40;
+        else if (low > 0x8000u || (low == 0x8000u && (up & 1u))) up += 1;
+        *(uint16_t *)res = (uint16_t)up;
+    }
+    return HDARRAY_OK;
+}
+
+void HDArrayReduce(HDArray_t *hA, void *res, REDUCE_OP op, int partID) { HDArrayReducev(hA, res, op, partID); }
+
+int HDArraySetAbsoluteUsev(const char *kName, int partID, HDArray_t *hA, int devID, int dim,
+                           const int64_t *lo, const int64_t *hi)
+{
+    int rc = abs_box(kName, partID, hA, devID, dim, lo, hi, true);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+int HDArraySetAbsoluteDefv(const char *kName, int partID, HDArray_t *hA, int devID, int dim,
+                           const int64_t *lo, const int64_t *hi)
+{
+    int rc = abs_box(kName, partID, hA, devID, dim, lo, hi, false);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+static void abs_varargs(const char *kName, int partID, HDArray_t *hA, int devID, int dim, va_list ap, bool use)
+{
+    if (dim < 1 || dim > 3) {
+        set_err(HDARRAY_ERR_INVAL);
+        return;
+    }
+    int64_t lo[3], hi[3];
+    for (int d = 0; d < dim; d++) lo[d] = va_arg(ap, int);
+    for (int d = 0; d < dim; d++) hi[d] = va_arg(ap, int);
+    int rc = abs_box(kName, partID, hA, devID, dim, lo, hi, use);
+    if (rc) set_err(rc);
+}
+
+void HDArraySetAbsoluteUse(const char *kName, int partID, HDArray_t *hA, int devID, int dim, ...)
+{
+    va_list ap;
+    va_start(ap, dim);
+    abs_varargs(kName, partID, hA, devID, dim, ap, true);
+    va_end(ap);
+}
+
+void HDArraySetAbsoluteDef(const char *kName, int partID, HDArray_t *hA, int devID, int dim, ...)
+{
+    va_list ap;
+    va_start(ap, dim);
+    abs_varargs(kName, partID, hA, devID, dim, ap, false);
+    va_end(ap);
+}
+
+int HDArraySetTrapezoidUsev(const char *kName, int partID, HDArray_t *hA, int devID, const int64_t *corners)
+{
+    int rc = abs_trap(kName, partID, hA, devID, corners, true);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+int HDArraySetTrapezoidDefv(const char *kName, int partID, HDArray_t *hA, int devID, const int64_t *corners)
+{
+    int rc = abs_trap(kName, partID, hA, devID, corners, false);
+    if (rc) set_err(rc);
+    return rc;
+}
+
+static void trap_varargs(const char *kName, int partID, HDArray_t *hA, int devID, int dim, va_list ap, bool use)
+{
+    if (dim != 2) {
+        set_err(HDARRAY_ERR_INVAL);
+        return;
+    }
+    int64_t c[8];
+    for (int i = 0; i < 8; i++) c[i] = va_arg(ap, int);
+    int rc = abs_trap(kName, partID, hA, devID, c, use);
+    if (rc) set_err(rc);
+}
+
+void HDArraySetTrapezoidUse(const char *kName, int partID, HDArray_t *hA, int devID, int dim, ...)
+{
+    va_list ap;
+    va_start(ap, dim);
+    trap_varargs(kName, partID, hA, devID, dim, ap, true);
+    va_end(ap);
+}
+
+void HDArraySetTrapezoidDef(const char *kName, int partID, HDArray_t *hA, int devID, int dim, ...)
+{
+    va_list ap;
+    va_start(ap, dim);
+    trap_varargs(kName, partID, hA, devID, dim, ap, false);
+    va_end(ap);
+}
+
+static int set_offsets(const char *kName, int argIndex, int noff, const int32_t *offs, bool use)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!kName || noff < 0 || (noff > 0 && !offs)) return HDARRAY_ERR_INVAL;
+    auto it = g->kernels.find(kName);
+    if (it == g->kernels.end()) return HDARRAY_ERR_INVAL;
+    KernelDef &k = it->second;
+    if (argIndex < 0 || argIndex >= k.narr) return HDARRAY_ERR_INVAL;
+    std::vector<Offset> v;
+    for (int i = 0; i < noff; i++) v.push_back(Offset{{offs[3 * i], offs[3 * i + 1], offs[3 * i + 2]}});
+    (use ? k.use : k.def)[argIndex] = v;
+    k.version++;
+    return HDARRAY_OK;
+}
+
+int HDArraySetOffsetUse(const char *kName, int argIndex, int noff, const int32_t *offs)
+{
+    return set_offsets(kName, argIndex, noff, offs, true);
+}
+
+int HDArraySetOffsetDef(const char *kName, int argIndex, int noff, const int32_t *offs)
+{
+    return set_offsets(kName, argIndex, noff, offs, false);
+}
+
+int HDArrayNumDevices(void) { return g ? g->ndev : 0; }
+
+int HDArraySetStream(void *stream)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (g->recording || g->batching) return HDARRAY_ERR_STATE;
+    g->stream = stream ? (cudaStream_t)stream : g->own_stream;
+    return HDARRAY_OK;
+}
+
+int HDArraySetMode(int mode)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (mode != HDARRAY_MODE_FUSED && mode != HDARRAY_MODE_PLAIN) return HDARRAY_ERR_INVAL;
+    if (g->recording || g->batching) return HDARRAY_ERR_STATE;
+    if (mode != g->mode) {
+        g->mode = mode;
+        for (auto &kv : g->memo) kv.second->compiled_sig.clear();
+        g->batch_cache.clear();
+    }
+    return HDARRAY_OK;
+}
+
+int HDArrayBatchBegin(void)
+{
+    if (!g || !g->inited || g->batching) return HDARRAY_ERR_STATE;
+    g->batching = true;
+    return HDARRAY_OK;
+}
+
+int HDArrayBatchEnd(void)
+{
+    if (!g || !g->inited || !g->batching) return HDARRAY_ERR_STATE;
+    g->batching = false;
+    int rc = flush_batch();
+    if (rc) set_err(rc);
+    return rc;
+}
+
+int HDArrayGraphBegin(void)
+{
+    if (!g || !g->inited || g->recording || g->batching) return HDARRAY_ERR_STATE;
+    if (g->host_only) return HDARRAY_ERR_UNSUPPORTED;
+    g->recording = true;
+    g->rec_invalid = false;
+    g->rec.clear();
+    g->rec_refs.clear();
+    g->rec_mems.clear();
+    g->rec_pre.clear();
+    return HDARRAY_OK;
+}
+
+int HDArrayGraphEnd(int *graphID)
+{
+    if (!g || !g->inited || !g->recording || !graphID) return HDARRAY_ERR_STATE;
+    g->recording = false;
+    if (g->rec_invalid) return set_err(HDARRAY_ERR_STATE);
+    GraphRec gr;
+    for (auto &kv : g->rec_pre) {
+        HDArray *a = kv.first;
+        if (a->generation != kv.second.second) return set_err(HDARRAY_ERR_STATE);
+        gr.arrays.push_back({a, a->generation, a->epoch, kv.second.first, a->cur});
+    }
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    CUDA_TRY(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    for (const LaunchRec &L : g->rec) {
+        cudaError_t e = issue(L, g->stream);
+        if (e != cudaSuccess) {
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(g->stream, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+            return set_err(HDARRAY_ERR_CUDA);
+        }
+    }
+    CUDA_TRY(cudaStreamEndCapture(g->stream, &gr.graph));
+    CUDA_TRY(cudaGraphInstantiate(&gr.exec, gr.graph, 0));
+    gr.refs = g->rec_refs;
+    gr.mems = g->rec_mems;
+    gr.nkernels = (int64_t)g->rec.size();
+    g->rec.clear();
+    g->rec_refs.clear();
+    g->rec_mems.clear();
+    const int id = g->next_graph++;
+    g->graphs[id] = std::move(gr);
+    *graphID = id;
+    return HDARRAY_OK;
+}
+
+int HDArrayGraphLaunch(int graphID, int nrep)
+{
+    if (!g || !g->inited || g->recording || g->batching) return HDARRAY_ERR_STATE;
+    auto it = g->graphs.find(graphID);
+    if (it == g->graphs.end() || nrep < 0) return HDARRAY_ERR_INVAL;
+    GraphRec &gr = it->second;
+    for (auto &ai : gr.arrays) {
+        if (!g->arrays.count(ai.a)) return set_err(HDARRAY_ERR_STATE);
+        if (ai.a->generation != ai.generation || ai.a->epoch != ai.epoch || ai.a->cur != ai.pre)
+            return set_err(HDARRAY_ERR_STATE);
+        if (nrep > 1 && ai.pre != ai.post) return set_err(HDARRAY_ERR_STATE);
+    }
+    for (int r = 0; r < nrep; r++) CUDA_TRY(cudaGraphLaunch(gr.exec, g->stream));
+    if (nrep > 0)
+        for (auto &ai : gr.arrays) ai.a->cur = ai.post;
+    g->counters[0] += gr.nkernels * nrep;
+    g->counters[4] += nrep;
+    return HDARRAY_OK;
+}
+
+int HDArrayGraphDestroy(int graphID)
+{
+    if (!g) return HDARRAY_ERR_STATE;
+    auto it = g->graphs.find(graphID);
+    if (it == g->graphs.end()) return HDARRAY_ERR_INVAL;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+    if (it->second.graph) cudaGraphDestroy(it->second.graph);
+    g->graphs.erase(it);
+    return HDARRAY_OK;
+}
+
+int HDArraySync(void)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (g->host_only) return HDARRAY_OK;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return HDARRAY_OK;
+}
+
+int HDArrayGetLastError(void)
+{
+    if (!g) return HDARRAY_ERR_STATE;
+    int e = g->last_error;
+    g->last_error = 0;
+    return e;
+}
+
+const char *HDArrayErrorString(int code)
+{
+    switch (code) {
+    case HDARRAY_OK: return "ok";
+    case HDARRAY_ERR_INVAL: return "invalid argument";
+    case HDARRAY_ERR_NOMEM: return "out of memory";
+    case HDARRAY_ERR_RACE: return "two devices define the same element in one call";
+    case HDARRAY_ERR_RANGE: return "section outside the array";
+    case HDARRAY_ERR_TIMEOUT: return "device-side wait timed out";
+    case HDARRAY_ERR_CUDA: return "CUDA error";
+    case HDARRAY_ERR_STATE: return "invalid state";
+    case HDARRAY_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown error";
+    }
+}
+
+static void to_user(const Box &b, int64_t *out)
+{
+    for (int d = 0; d < 3; d++) {
+        out[d] = b.lo[d];
+        out[3 + d] = b.hi[d];
+    }
+}
+
+int64_t HDArrayGetPlan(HDArray_t *hA, int64_t *out, int64_t cap)
+{
+    if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
+    const auto &mv = hA->last_moves;
+    for (int64_t i = 0; i < (int64_t)mv.size() && i < cap && out; i++) {
+        out[8 * i] = mv[i].src;
+        out[8 * i + 1] = mv[i].dst;
+        to_user(mv[i].box, out + 8 * i + 2);
+    }
+    return (int64_t)mv.size();
+}
+
+int64_t HDArrayGetGDEF(HDArray_t *hA, int p, int q, int64_t *out, int64_t cap)
+{
+    if (!g || !hA || !g->arrays.count(hA) || p < 0 || q < 0) return HDARRAY_ERR_INVAL;
+    const GState &s = hA->states[hA->cur];
+    if (p >= (int)s.own.size() || q >= (int)s.own.size() || p == q) return 0;
+    BoxSet x = set_intersect(s.own[p], s.stale[q]);
+    for (int64_t i = 0; i < (int64_t)x.size() && i < cap && out; i++) to_user(x[i], out + 6 * i);
+    return (int64_t)x.size();
+}
+
+int HDArrayGetDeviceBuffer(HDArray_t *hA, int dev, void **ptr, int64_t *lo, int64_t *hi, int64_t *strides)
+{
+    if (!g || !hA || !g->arrays.count(hA) || dev < 0 || !ptr) return HDARRAY_ERR_INVAL;
+    *ptr = nullptr;
+    if (dev >= (int)hA->buf.size()) return HDARRAY_OK;
+    const DevBuf &b = hA->buf[dev];
+    *ptr = b.ptr;
+    for (int d = 0; d < 3; d++) {
+        if (lo) lo[d] = b.alloc.lo[d];
+        if (hi) hi[d] = b.alloc.hi[d];
+        if (strides) strides[d] = b.st[d];
+    }
+    return HDARRAY_OK;
+}
+
+int HDArrayReadDeviceBuffer(HDArray_t *hA, int dev, const int64_t *lo, const int64_t *hi, void *out)
+{
+    if (!g || !g->inited || !hA || !g->arrays.count(hA) || dev < 0 || !lo || !hi || !out)
+        return HDARRAY_ERR_INVAL;
+    if (g->host_only) return HDARRAY_ERR_STATE;
+    if (dev >= (int)hA->buf.size() || !hA->buf[dev].ptr) return HDARRAY_ERR_RANGE;
+    const DevBuf &b = hA->buf[dev];
+    Box bx = make_box(0, 0, 0, 1, 1, 1);
+    for (int d = 0; d < hA->dim; d++) {
+        bx.lo[d] = lo[d];
+        bx.hi[d] = hi[d];
+    }
+    if (bx.empty()) return HDARRAY_OK;
+    if (!box_contains(b.alloc, bx)) return HDARRAY_ERR_RANGE;
+    // view `out` as a dense array shaped like the box: a one-box "user array"
+    HDArray tmp;
+    tmp.dim = hA->dim;
+    tmp.esize = hA->esize;
+    for (int d = 0; d < 3; d++) tmp.n[d] = bx.hi[d] - bx.lo[d];
+    DevBuf shifted = b;
+    for (int d = 0; d < 3; d++) {
+        shifted.alloc.lo[d] -= bx.lo[d];
+        shifted.alloc.hi[d] -= bx.lo[d];
+    }
+    Box local = make_box(0, 0, 0, tmp.n[0], tmp.n[1], tmp.n[2]);
+    int rc = memcpy_box(&tmp, shifted, local, out, false);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return HDARRAY_OK;
+}
+
+int HDArrayGetCounters(int64_t *out, int n)
+{
+    if (!g || !out || n < 0) return HDARRAY_ERR_INVAL;
+    for (int i = 0; i < n && i < 5; i++) out[i] = g->counters[i];
+    return HDARRAY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,350 @@
+"""Python binding of libhdarray.so: the C ABI of include/hdarray.h under the same names.
+
+Argument marshalling only: every step of the hot path (section bookkeeping, exchange, kernels,
+reductions) runs inside the library.  Arrays are passed as numpy arrays (host memory) or torch
+tensors (host or CUDA memory); the library reads or writes them through their data pointers.
+
+A call that fails raises HDArrayError with the library's error code.  Loading fails loudly when
+the library has not been built (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libhdarray.so")
+
+HDARRAY_ROW, HDARRAY_COL, HDARRAY_BLOCK = 0, 1, 2
+ROW, COL, BLOCK = HDARRAY_ROW, HDARRAY_COL, HDARRAY_BLOCK
+HDARRAY_SUM, HDARRAY_PROD, HDARRAY_MAX, HDARRAY_MIN = 0, 1, 2, 3
+SUM, PROD, MAX, MIN = HDARRAY_SUM, HDARRAY_PROD, HDARRAY_MAX, HDARRAY_MIN
+HDARRAY_ALL = -(2 ** 31)
+HDARRAY_MODE_FUSED, HDARRAY_MODE_PLAIN = 0, 1
+HDARRAY_INIT_HOST_ONLY = 1
+
+ERRORS = {0: "ok", -1: "INVAL", -2: "NOMEM", -3: "RACE", -4: "RANGE", -5: "TIMEOUT", -6: "CUDA",
+          -7: "STATE", -8: "UNSUPPORTED"}
+
+
+class HDArrayError(RuntimeError):
+    def __init__(self, code, call):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (call, ERRORS.get(code, "?"), code))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); the variadic paper prototypes are exported too but the binding
+# calls the fixed-argument forms.
+SIGNATURES = {
+    "HDArrayInit": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_char_p, ctypes.c_char_p]),
+    "HDArrayInitEx": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint]),
+    "HDArrayExit": (None, []),
+    "HDArrayShowDeviceInfo": (None, [ctypes.c_int]),
+    "HDArrayCreatev": (_P, [ctypes.c_char_p, ctypes.c_char_p, _P, ctypes.c_int, _I64P]),
+    "HDArrayFree": (ctypes.c_int, [_P]),
+    "HDArrayPartitionv": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64P, _I64P, _I64P]),
+    "HDArrayPartitionManual": (ctypes.c_int, [ctypes.c_int, _I64P, ctypes.c_int, _I64P, _I64P]),
+    "HDArrayApplyKernelv": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(_P), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "HDArrayReadv": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "HDArrayWritev": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "HDArrayReducev": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+    "HDArrayReduceD": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int]),
+    "HDArraySetAbsoluteUsev": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, _P, ctypes.c_int,
+                                              ctypes.c_int, _I64P, _I64P]),
+    "HDArraySetAbsoluteDefv": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, _P, ctypes.c_int,
+                                              ctypes.c_int, _I64P, _I64P]),
+    "HDArraySetTrapezoidUsev": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, _P, ctypes.c_int, _I64P]),
+    "HDArraySetTrapezoidDefv": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, _P, ctypes.c_int, _I64P]),
+    "HDArraySetOffsetUse": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "HDArraySetOffsetDef": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    "HDArrayNumDevices": (ctypes.c_int, []),
+    "HDArraySetStream": (ctypes.c_int, [_P]),
+    "HDArraySetMode": (ctypes.c_int, [ctypes.c_int]),
+    "HDArrayBatchBegin": (ctypes.c_int, []),
+    "HDArrayBatchEnd": (ctypes.c_int, []),
+    "HDArrayGraphBegin": (ctypes.c_int, []),
+    "HDArrayGraphEnd": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
+    "HDArrayGraphLaunch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "HDArrayGraphDestroy": (ctypes.c_int, [ctypes.c_int]),
+    "HDArraySync": (ctypes.c_int, []),
+    "HDArrayGetLastError": (ctypes.c_int, []),
+    "HDArrayErrorString": (ctypes.c_char_p, [ctypes.c_int]),
+    "HDArrayGetPlan": (ctypes.c_int64, [_P, _I64P, ctypes.c_int64]),
+    "HDArrayGetGDEF": (ctypes.c_int64, [_P, ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64]),
+    "HDArrayGetDeviceBuffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _I64P, _I64P, _I64P]),
+    "HDArrayGetCounters": (ctypes.c_int, [_I64P, ctypes.c_int]),
+    "HDArrayReadDeviceBuffer": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _I64P, _P]),
+}
+
+
+def lib():
+    """The loaded library.  Raises if it has not been built: there is no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise ImportError("libhdarray.so not built: run paper_1809_05657_gb300/build.py "
+                              "(or __graft_entry__.build())")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _chk(rc, call):
+    if rc is None or rc < 0:
+        raise HDArrayError(rc if rc is not None else -1, call)
+    return rc
+
+
+def _i64(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int64).ravel())
+    return a, a.ctypes.data_as(_I64P)
+
+
+def _ptr(x):
+    """Data pointer of a numpy array, a torch tensor, an int address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+class HDArray:
+    """Handle returned by HDArrayCreate."""
+
+    def __init__(self, handle, sym, dtype, dims):
+        self.handle = handle
+        self.sym = sym
+        self.dtype = dtype
+        self.dims = tuple(dims)
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.handle)
+
+
+# -------------------------------------------------------------------------------------------
+# The paper's calls (Table 2) and the extensions, same names as the C ABI
+# -------------------------------------------------------------------------------------------
+
+def HDArrayInit(argv=None, kpath=None, dpath=None, ndev=None, host_only=False):
+    if ndev is not None or host_only:
+        return _chk(lib().HDArrayInitEx(ndev or 1, HDARRAY_INIT_HOST_ONLY if host_only else 0),
+                    "HDArrayInitEx")
+    return _chk(lib().HDArrayInit(0, None, kpath.encode() if kpath else None,
+                                  dpath.encode() if dpath else None), "HDArrayInit")
+
+
+def HDArrayExit():
+    lib().HDArrayExit()
+
+
+def HDArrayShowDeviceInfo(dev=0):
+    lib().HDArrayShowDeviceInfo(dev)
+
+
+def HDArrayCreate(sym, dtype, uA, *sizes):
+    s, sp = _i64(sizes)
+    h = lib().HDArrayCreatev(sym.encode(), dtype.encode(), _ptr(uA), len(sizes), sp)
+    if not h:
+        raise HDArrayError(lib().HDArrayGetLastError(), "HDArrayCreate")
+    return HDArray(h, sym, dtype, sizes)
+
+
+def HDArrayFree(h):
+    _chk(lib().HDArrayFree(h), "HDArrayFree")
+
+
+def HDArrayPartition(ptype, sizes, lo, hi, nparts=0):
+    dim = len(sizes)
+    s, sp = _i64(sizes)
+    l, lp = _i64(lo)
+    u, up = _i64(hi)
+    return _chk(lib().HDArrayPartitionv(ptype, nparts, dim, sp, lp, up), "HDArrayPartition")
+
+
+def HDArrayPartitionManual(sizes, boxes):
+    """boxes: per device (lo, hi) tuples (empty box for a device without work)."""
+    dim = len(sizes)
+    s, sp = _i64(sizes)
+    l, lp = _i64([b[0] for b in boxes])
+    u, up = _i64([b[1] for b in boxes])
+    return _chk(lib().HDArrayPartitionManual(dim, sp, len(boxes), lp, up), "HDArrayPartitionManual")
+
+
+def HDArrayApplyKernel(kname, part, *args):
+    arrs = [a for a in args if isinstance(a, HDArray)]
+    scal = [float(a) for a in args if not isinstance(a, HDArray)]
+    A = (_P * max(1, len(arrs)))(*[a.handle for a in arrs])
+    S = (ctypes.c_double * max(1, len(scal)))(*scal)
+    return _chk(lib().HDArrayApplyKernelv(kname.encode(), part, len(arrs), A, len(scal), S),
+                "HDArrayApplyKernel(%s)" % kname)
+
+
+def HDArrayWrite(h, uA, part):
+    return _chk(lib().HDArrayWritev(h, _ptr(uA), part), "HDArrayWrite")
+
+
+def HDArrayRead(h, uA, part):
+    return _chk(lib().HDArrayReadv(h, _ptr(uA), part), "HDArrayRead")
+
+
+def HDArrayReduce(h, op, part):
+    """The double accumulator of HDArrayReduce (HDArrayReduceD)."""
+    out = ctypes.c_double()
+    _chk(lib().HDArrayReduceD(h, ctypes.byref(out), op, part), "HDArrayReduce")
+    return out.value
+
+
+def HDArraySetAbsoluteUse(kname, part, h, dev, lo, hi):
+    l, lp = _i64(lo)
+    u, up = _i64(hi)
+    return _chk(lib().HDArraySetAbsoluteUsev(kname.encode(), part, h, dev, len(lo), lp, up),
+                "HDArraySetAbsoluteUse")
+
+
+def HDArraySetAbsoluteDef(kname, part, h, dev, lo, hi):
+    l, lp = _i64(lo)
+    u, up = _i64(hi)
+    return _chk(lib().HDArraySetAbsoluteDefv(kname.encode(), part, h, dev, len(lo), lp, up),
+                "HDArraySetAbsoluteDef")
+
+
+def HDArraySetTrapezoidUse(kname, part, h, dev, corners):
+    c, cp = _i64(corners)
+    return _chk(lib().HDArraySetTrapezoidUsev(kname.encode(), part, h, dev, cp),
+                "HDArraySetTrapezoidUse")
+
+
+def HDArraySetTrapezoidDef(kname, part, h, dev, corners):
+    c, cp = _i64(corners)
+    return _chk(lib().HDArraySetTrapezoidDefv(kname.encode(), part, h, dev, cp),
+                "HDArraySetTrapezoidDef")
+
+
+def _offs(offs):
+    a = np.zeros((len(offs), 3), np.int32)
+    for i, o in enumerate(offs):
+        a[i, : len(o)] = o
+    a = np.ascontiguousarray(a)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def HDArraySetOffsetUse(kname, arg, offs):
+    a, ap = _offs(offs)
+    return _chk(lib().HDArraySetOffsetUse(kname.encode(), arg, len(offs), ap), "HDArraySetOffsetUse")
+
+
+def HDArraySetOffsetDef(kname, arg, offs):
+    a, ap = _offs(offs)
+    return _chk(lib().HDArraySetOffsetDef(kname.encode(), arg, len(offs), ap), "HDArraySetOffsetDef")
+
+
+def HDArraySetStream(stream=None):
+    """stream: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    return _chk(lib().HDArraySetStream(stream), "HDArraySetStream")
+
+
+def HDArraySetMode(mode):
+    return _chk(lib().HDArraySetMode(mode), "HDArraySetMode")
+
+
+def HDArrayBatchBegin():
+    return _chk(lib().HDArrayBatchBegin(), "HDArrayBatchBegin")
+
+
+def HDArrayBatchEnd():
+    return _chk(lib().HDArrayBatchEnd(), "HDArrayBatchEnd")
+
+
+def HDArrayGraphBegin():
+    return _chk(lib().HDArrayGraphBegin(), "HDArrayGraphBegin")
+
+
+def HDArrayGraphEnd():
+    gid = ctypes.c_int()
+    _chk(lib().HDArrayGraphEnd(ctypes.byref(gid)), "HDArrayGraphEnd")
+    return gid.value
+
+
+def HDArrayGraphLaunch(gid, nrep=1):
+    return _chk(lib().HDArrayGraphLaunch(gid, nrep), "HDArrayGraphLaunch")
+
+
+def HDArrayGraphDestroy(gid):
+    return _chk(lib().HDArrayGraphDestroy(gid), "HDArrayGraphDestroy")
+
+
+def HDArraySync():
+    return _chk(lib().HDArraySync(), "HDArraySync")
+
+
+def HDArrayGetLastError():
+    return lib().HDArrayGetLastError()
+
+
+def HDArrayGetPlan(h):
+    """Exchange of the last call that moved h: list of (src, dst, lo(3), hi(3))."""
+    n = _chk(lib().HDArrayGetPlan(h, None, 0), "HDArrayGetPlan")
+    buf = np.zeros(max(1, n) * 8, np.int64)
+    _chk(lib().HDArrayGetPlan(h, buf.ctypes.data_as(_I64P), n), "HDArrayGetPlan")
+    out = []
+    for i in range(n):
+        r = buf[8 * i: 8 * i + 8]
+        out.append((int(r[0]), int(r[1]), tuple(int(v) for v in r[2:5]), tuple(int(v) for v in r[5:8])))
+    return out
+
+
+def HDArrayGetGDEF(h, p, q):
+    n = _chk(lib().HDArrayGetGDEF(h, p, q, None, 0), "HDArrayGetGDEF")
+    buf = np.zeros(max(1, n) * 6, np.int64)
+    _chk(lib().HDArrayGetGDEF(h, p, q, buf.ctypes.data_as(_I64P), n), "HDArrayGetGDEF")
+    return [(tuple(int(v) for v in buf[6 * i: 6 * i + 3]), tuple(int(v) for v in buf[6 * i + 3: 6 * i + 6]))
+            for i in range(n)]
+
+
+def HDArrayGetDeviceBuffer(h, dev):
+    """(device pointer or None, alloc lo (3), alloc hi (3), element strides (3))."""
+    p = _P()
+    lo = np.zeros(3, np.int64)
+    hi = np.zeros(3, np.int64)
+    st = np.zeros(3, np.int64)
+    _chk(lib().HDArrayGetDeviceBuffer(h, dev, ctypes.byref(p), lo.ctypes.data_as(_I64P),
+                                      hi.ctypes.data_as(_I64P), st.ctypes.data_as(_I64P)),
+         "HDArrayGetDeviceBuffer")
+    return p.value, tuple(int(v) for v in lo), tuple(int(v) for v in hi), tuple(int(v) for v in st)
+
+
+def HDArrayReadDeviceBuffer(h, dev, lo, hi, out):
+    """Raw contents of box [lo, hi) of device dev's buffer into the dense array `out`."""
+    l, lp = _i64(lo)
+    u, up = _i64(hi)
+    return _chk(lib().HDArrayReadDeviceBuffer(h, dev, lp, up, _ptr(out)), "HDArrayReadDeviceBuffer")
+
+
+def HDArrayGetCounters():
+    """dict: launches, bytes_moved, plans, plan_hits, graph_launches."""
+    buf = np.zeros(5, np.int64)
+    _chk(lib().HDArrayGetCounters(buf.ctypes.data_as(_I64P), 5), "HDArrayGetCounters")
+    return dict(zip(["launches", "bytes_moved", "plans", "plan_hits", "graph_launches"],
+                    (int(v) for v in buf)))

@@ -1,0 +1,404 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Bar: section sets (every call's exchange) and every copied or computed element bit-exact; the
+Jacobi kernels sum in the paper's order in the storage precision, so their results are bit-exact
+too.  Floating-point results with a different summation order (reductions, GEMM) are within the
+bounds stated in each test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from harness import LibraryRun, OracleRun, compare_messages
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_1809_05657_gb300.hdarray")
+ROW, COL, BLOCK = 0, 1, 2
+NP = {"double": np.float64, "float": np.float32, "bf16": np.uint16}
+
+
+@pytest.fixture
+def gpu_lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from __graft_entry__ import build_library
+    build_library()
+    torch.cuda.init()
+    yield lambda ndev: H.HDArrayInit(ndev=ndev)
+    H.HDArrayExit()
+
+
+def device_buffers_match(lib_run, orc_run, names):
+    """Every element a device holds as current equals the global value, bit for bit."""
+    for name in names:
+        a = lib_run.arrays[name]
+        oa = orc_run.arrays[name]
+        owner, have = oa.state_get()
+        dims = oa.dims
+        n3 = list(dims) + [1] * (3 - len(dims))
+        for p in range(oa.P):
+            ptr, lo, hi, st = H.HDArrayGetDeviceBuffer(a, p)
+            if ptr is None:
+                assert not have[p].any() or (owner[have[p].astype(bool)] == -1).all()
+                continue
+            blo = [max(lo[d], 0) for d in range(3)]
+            bhi = [min(hi[d], n3[d]) for d in range(3)]
+            shape = [bhi[d] - blo[d] for d in range(3)]
+            raw = np.zeros(shape, NP[a.dtype])
+            H.HDArrayReadDeviceBuffer(a, p, blo[:len(dims)], bhi[:len(dims)], raw)
+            G = oa.G.reshape(n3)[blo[0]:bhi[0], blo[1]:bhi[1], blo[2]:bhi[2]]
+            hv = have[p].reshape(n3)[blo[0]:bhi[0], blo[1]:bhi[1], blo[2]:bhi[2]].astype(bool)
+            # elements held as current that were ever written (never-written ones are zero)
+            bad = hv & (raw.view(np.uint8).reshape(shape + [-1]) != G.view(np.uint8).reshape(shape + [-1])).any(-1)
+            assert not bad.any(), "device %d of %s: %d current elements differ" % (p, name, bad.sum())
+            # everything outside the device's buffer must be stale or never written
+            outside = np.ones(n3, bool)
+            outside[blo[0]:bhi[0], blo[1]:bhi[1], blo[2]:bhi[2]] = False
+            held_out = have[p].reshape(n3).astype(bool) & outside & (owner.reshape(n3) >= 0)
+            assert not held_out.any()
+
+
+def run_program(prog, ndev, values, gpu_lib, check_buffers=True, mode=H.HDARRAY_MODE_FUSED):
+    gpu_lib(ndev)
+    H.HDArraySetMode(mode)
+    lib = LibraryRun(H, ndev)
+    lib_out = lib.run(prog, values)
+    orc = OracleRun(ndev)
+    orc_out = orc.run(prog, values)
+    dims = {op[1]: tuple(op[3]) for op in prog if op[0] == "create"}
+    n = compare_messages(orc_out, lib_out, prog, dims, ndev)
+    if check_buffers:
+        device_buffers_match(lib, orc, list(dims))
+    return lib, orc, lib_out, orc_out, n
+
+
+def jacobi_prog(dims, P, iters, ptype=ROW, dtype="float", pingpong=True):
+    nd = len(dims)
+    kernel = "jacobi2d" if nd == 2 else "stencil3d"
+    prog = [("create", "B", dtype, dims), ("create", "A", dtype, dims),
+            ("part", "D", ptype, dims, (0,) * nd, dims, P),
+            ("part", "W", ptype, dims, (1,) * nd, tuple(n - 1 for n in dims), P),
+            ("write", "B", "D"), ("write", "A", "D")]
+    x, y = "B", "A"
+    for _ in range(iters):
+        prog.append(("apply", kernel, "W", [x, y]))
+        if pingpong:
+            x, y = y, x
+        else:
+            prog.append(("apply", "copy", "W", [y, x]))
+    return prog, x
+
+
+def read_all(lib, name, dims, dtype, part="D"):
+    out = np.zeros(dims, NP[dtype])
+    H.HDArrayRead(lib.arrays[name], out, lib.parts[part])
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Jacobi 2-D
+# ---------------------------------------------------------------------------------------------
+
+CASES = [
+    ((130, 301), 4, BLOCK, "float", True),
+    ((97, 131), 3, ROW, "double", False),
+    ((140, 270), 5, COL, "bf16", True),
+    ((259, 515), 6, BLOCK, "float", False),
+    ((70, 600), 2, ROW, "bf16", False),
+    ((300, 90), 7, ROW, "double", True),
+]
+
+
+@pytest.mark.parametrize("dims,P,ptype,dtype,pingpong", CASES)
+@pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
+def test_jacobi2d_parity(gpu_lib, dims, P, ptype, dtype, pingpong, mode):
+    x = synthetic.jacobi_field(dims, stream=11, dtype=dtype)
+    prog, last = jacobi_prog(dims, P, 5, ptype, dtype, pingpong)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib, mode=mode)
+    got = read_all(lib, last, dims, dtype)
+    want = orc.arrays[last].G
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
+def test_jacobi2d_tile_shapes(gpu_lib, monkeypatch):
+    """Tiles of several heights, a ragged last band and 1-row partitions."""
+    dims, P = (41, 1030), 13  # 39 work rows over 13 devices: 3 rows each
+    x = synthetic.jacobi_field(dims, stream=12, dtype="float")
+    prog, last = jacobi_prog(dims, P, 4, ROW, "float", True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+
+
+def test_jacobi2d_degenerate(gpu_lib):
+    """3x3 array (one work element), more devices than work rows (idle devices)."""
+    for dims, P in (((3, 3), 1), ((3, 9), 4), ((9, 3), 5)):
+        x = synthetic.jacobi_field(dims, stream=13, dtype="double")
+        prog, last = jacobi_prog(dims, P, 3, ROW, "double", False)
+        lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+        assert np.array_equal(read_all(lib, last, dims, "double"), orc.arrays[last].G)
+        H.HDArrayExit()
+
+
+# ---------------------------------------------------------------------------------------------
+# Reduce, residual
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["double", "float", "bf16"])
+def test_reduce_parity(gpu_lib, dtype):
+    dims, P = (203, 157), 6
+    u = synthetic.uniform(dims[0] * dims[1], stream=21).reshape(dims)
+    x = synthetic.to_storage(1.0 + (u - 0.5) * 0.02, dtype)  # products stay well scaled
+    prog = [("create", "X", dtype, dims), ("part", "D", BLOCK, dims, (0, 0), dims, P),
+            ("part", "C", COL, dims, (2, 3), (dims[0] - 5, dims[1] - 1), 4),
+            ("write", "X", "D")]
+    for op in (0, 1, 2, 3):
+        prog.append(("reduce", "X", op, "C"))
+        prog.append(("reduce", "X", op, "D"))
+    lib, orc, lib_out, orc_out, _ = run_program(prog, P, {"X": x}, gpu_lib)
+    for lo, oo, op in zip(lib_out, orc_out, prog):
+        if op[0] != "reduce":
+            continue
+        g, w = lo["_value"], oo["_value"]
+        if op[2] in (2, 3):
+            assert g == w
+        elif op[2] == 0:
+            assert abs(g - w) <= 1e-12 * abs(w)
+        else:
+            assert w > 1e-3 and abs(g - w) <= 4 * dims[0] * dims[1] * 2.0 ** -53 * abs(w)
+
+
+def test_residual_flow_cfg1(gpu_lib):
+    """The paper's two-kernel Jacobi (plain form, FP64, 256x256, ROW 4, 10 iterations) and the
+    FP64 residual sum((A - B)^2) via HDArrayReduce."""
+    dims, P = (256, 256), 4
+    x = synthetic.jacobi_field(dims, stream=0, dtype="double")
+    prog, _ = jacobi_prog(dims, P, 10, ROW, "double", pingpong=False)
+    prog += [("create", "R", "double", dims), ("apply", "sqdiff", "W", ["A", "B", "R"]),
+             ("reduce", "R", 0, "W")]
+    lib, orc, lib_out, orc_out, _ = run_program(prog, P, {"B": x, "A": x}, gpu_lib,
+                                                mode=H.HDARRAY_MODE_PLAIN)
+    g, w = lib_out[-1]["_value"], orc_out[-1]["_value"]
+    assert abs(g - w) <= 1e-12 * abs(w)
+
+
+# ---------------------------------------------------------------------------------------------
+# GEMM (binary64)
+# ---------------------------------------------------------------------------------------------
+
+def _gamma_bound(A, B, C0, alpha, beta, k):
+    u = 2.0 ** -53
+    gam = (k + 2) * u / (1 - (k + 2) * u)
+    return gam * (np.abs(beta * C0) + abs(alpha) * (np.abs(A) @ np.abs(B))) + 1e-300
+
+
+@pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
+def test_gemm_listing2_parity(gpu_lib, mode):
+    ni, nj, nk, P = 150, 130, 170, 4
+    a = synthetic.normal(ni * nk, stream=31).reshape(ni, nk)
+    b = synthetic.normal(nk * nj, stream=32).reshape(nk, nj)
+    c = synthetic.normal(ni * nj, stream=33).reshape(ni, nj)
+    alpha, beta = 1.5, 0.25
+    prog = [("create", "a", "double", (ni, nk)), ("create", "b", "double", (nk, nj)),
+            ("create", "c", "double", (ni, nj)),
+            ("part", "p0", ROW, (ni, nj), (0, 0), (ni, nj), P),
+            ("part", "pa", ROW, (ni, nk), (0, 0), (ni, nk), P),
+            ("part", "pb", ROW, (nk, nj), (0, 0), (nk, nj), P),
+            ("write", "a", "pa"), ("write", "b", "pb"), ("write", "c", "p0"),
+            ("apply", "gemm", "p0", ["a", "b", "c"], (alpha, beta, ni, nj, nk))]
+    lib, orc, *_ = run_program(prog, P, {"a": a, "b": b, "c": c}, gpu_lib, check_buffers=False, mode=mode)
+    device_buffers_match(lib, orc, ["a", "b"])  # the all-gathered B is bit-exact on every device
+    got = np.zeros((ni, nj))
+    H.HDArrayRead(lib.arrays["c"], got, lib.parts["p0"])
+    want = orc.arrays["c"].G
+    assert (np.abs(got - want) <= 2 * _gamma_bound(a, b, c, alpha, beta, nk)).all()
+
+
+def test_trmm_trapezoid_parity(gpu_lib):
+    n, m, P = 256, 96, 4
+    a, b = synthetic.tri_gemm_inputs(n, m, stream=34)
+    rows = [p * n // P for p in range(P + 1)]
+    prog = [("create", "A", "double", (n, n)), ("create", "B", "double", (n, m)),
+            ("create", "C", "double", (n, m)),
+            ("part", "R", ROW, (n, m), (0, 0), (n, m), P),
+            ("part", "RA", ROW, (n, n), (0, 0), (n, n), P)]
+    for p in range(P):
+        r0, r1 = rows[p], rows[p + 1]
+        prog.append(("trap_use", "trmm", "R", "A", p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1)))
+    prog += [("write", "A", "RA"), ("write", "B", "R"),
+             ("apply", "trmm", "R", ["A", "B", "C"], (1.0, 0.0)),
+             ("apply", "trmm", "R", ["A", "B", "C"], (1.0, 0.0))]
+    lib, orc, lib_out, *_ = run_program(prog, P, {"A": a, "B": b}, gpu_lib, check_buffers=False)
+    device_buffers_match(lib, orc, ["A", "B"])
+    got = np.zeros((n, m))
+    H.HDArrayRead(lib.arrays["C"], got, lib.parts["R"])
+    assert (np.abs(got - orc.arrays["C"].G) <= 2 * _gamma_bound(np.tril(a), b, 0 * got, 1.0, 0.0, n)).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# batches and graphs
+# ---------------------------------------------------------------------------------------------
+
+def test_batch_of_instances(gpu_lib):
+    insts = synthetic.jacobi_instances(9, stream=41, lo=8, hi=200)
+    ndev = max(p for _, _, p, _ in insts)
+    gpu_lib(ndev)
+    arrays = []
+    xs = []
+    for i, (r, c, P, kind) in enumerate(insts):
+        t = ROW if kind == "ROW" else COL
+        x = synthetic.jacobi_field((r, c), stream=100 + i, dtype="float")
+        B = H.HDArrayCreate("B%d" % i, "float", None, r, c)
+        A = H.HDArrayCreate("A%d" % i, "float", None, r, c)
+        D = H.HDArrayPartition(t, (r, c), (0, 0), (r, c), P)
+        W = H.HDArrayPartition(t, (r, c), (1, 1), (r - 1, c - 1), P)
+        H.HDArrayWrite(B, x, D)
+        H.HDArrayWrite(A, x, D)
+        arrays.append([B, A, D, W])
+        xs.append(x)
+    iters = 6
+    for it in range(iters):
+        H.HDArrayBatchBegin()
+        for B, A, D, W in arrays:
+            H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayBatchEnd()
+        for inst in arrays:
+            inst[0], inst[1] = inst[1], inst[0]
+    for i, ((r, c, P, kind), (B, A, D, W)) in enumerate(zip(insts, arrays)):
+        got = np.zeros((r, c), np.float32)
+        H.HDArrayRead(B, got, D)
+        o = oracle.Oracle(P)
+        t = ROW if kind == "ROW" else COL
+        ob, oa = o.create("B", "float", (r, c)), o.create("A", "float", (r, c))
+        od = o.partition(t, (r, c), (0, 0), (r, c))
+        ow = o.partition(t, (r, c), (1, 1), (r - 1, c - 1))
+        o.write(ob, xs[i], od)
+        o.write(oa, xs[i], od)
+        for it in range(iters):
+            o.apply("jacobi2d", ow, [ob, oa])
+            ob, oa = oa, ob
+        assert np.array_equal(got, ob.G), "instance %d" % i
+
+
+def test_batch_rejects_dependent_calls(gpu_lib):
+    gpu_lib(2)
+    B = H.HDArrayCreate("B", "float", None, 16, 16)
+    A = H.HDArrayCreate("A", "float", None, 16, 16)
+    W = H.HDArrayPartition(ROW, (16, 16), (1, 1), (15, 15), 2)
+    H.HDArrayBatchBegin()
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)  # uses what the first call defines
+    with pytest.raises(H.HDArrayError) as e:
+        H.HDArrayBatchEnd()
+    assert e.value.code == -3
+
+
+@pytest.mark.parametrize("dtype", ["float", "bf16"])
+def test_graph_replay(gpu_lib, dtype):
+    dims, P = (200, 330), 6
+    x = synthetic.jacobi_field(dims, stream=51, dtype=dtype)
+    gpu_lib(P)
+    B = H.HDArrayCreate("B", dtype, None, *dims)
+    A = H.HDArrayCreate("A", dtype, None, *dims)
+    D = H.HDArrayPartition(BLOCK, dims, (0, 0), dims, P)
+    W = H.HDArrayPartition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1), P)
+    H.HDArrayWrite(B, x, D)
+    H.HDArrayWrite(A, x, D)
+    for _ in range(2):  # reach the periodic state
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, 7)
+    total = 2 * 2 + 2 + 2 * 7
+    got = np.zeros(dims, NP[dtype])
+    H.HDArrayRead(B, got, D)
+    o = oracle.Oracle(P)
+    ob, oa = o.create("B", dtype, dims), o.create("A", dtype, dims)
+    od = o.partition(BLOCK, dims, (0, 0), dims)
+    ow = o.partition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1))
+    o.write(ob, x, od)
+    o.write(oa, x, od)
+    for _ in range(total // 2):
+        o.apply("jacobi2d", ow, [ob, oa])
+        o.apply("jacobi2d", ow, [oa, ob])
+    assert np.array_equal(got, ob.G)
+    # a graph recorded in another state refuses to run
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    with pytest.raises(H.HDArrayError) as e:
+        H.HDArrayGraphLaunch(gid, 1)
+    assert e.value.code == -7
+
+
+# ---------------------------------------------------------------------------------------------
+# full size, in the benchmark's configuration: sampled outputs against the oracle
+# ---------------------------------------------------------------------------------------------
+
+def light_cone(x, prec, samples, T):
+    """Value after T Jacobi steps at each sample, from the oracle on the sample's light cone."""
+    n0, n1 = x.shape
+    out = []
+    for (i, j) in samples:
+        r0, r1 = max(0, i - T - 1), min(n0, i + T + 2)
+        c0, c1 = max(0, j - T - 1), min(n1, j + T + 2)
+        B = np.ascontiguousarray(x[r0:r1, c0:c1])
+        A = B.copy()
+        work = np.zeros(B.shape, np.uint8)
+        gi = np.arange(r0, r1)[:, None]
+        gj = np.arange(c0, c1)[None, :]
+        inside = (gi >= 1) & (gi < n0 - 1) & (gj >= 1) & (gj < n1 - 1)
+        border = np.zeros(B.shape, bool)
+        border[0, :] = border[-1, :] = border[:, 0] = border[:, -1] = True
+        work[(inside & ~border)] = 1
+        L = oracle.lib()
+        for _ in range(T):
+            rc = L.orc_jacobi2d(prec, B.shape[0], B.shape[1], B.ctypes.data, A.ctypes.data, work.ctypes.data)
+            assert rc == 0
+            A, B = B, A
+        out.append(B[i - r0, j - c0])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("dtype", ["float", "bf16"])
+def test_full_size_8192_block16_graph(gpu_lib, dtype):
+    n, P, T = 8192, 16, 100
+    dims = (n, n)
+    x = synthetic.jacobi_field(dims, stream=1, dtype=dtype)
+    gpu_lib(P)
+    B = H.HDArrayCreate("B", dtype, None, n, n)
+    A = H.HDArrayCreate("A", dtype, None, n, n)
+    D = H.HDArrayPartition(BLOCK, dims, (0, 0), dims, P)
+    W = H.HDArrayPartition(BLOCK, dims, (1, 1), (n - 1, n - 1), P)
+    H.HDArrayWrite(B, x, D)
+    H.HDArrayWrite(A, x, D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, (T - 6) // 2)
+    got = np.zeros(dims, NP[dtype])
+    H.HDArrayRead(B, got, D)
+    rng = np.random.default_rng(7)
+    cuts = [1, 2, 2047, 2048, 2049, 4096, 4097, 6143, 6144, 8190]
+    samples = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(24)]
+    samples += [(c, int(rng.integers(0, n))) for c in cuts] + [(int(rng.integers(0, n)), c) for c in cuts]
+    samples += [(0, 0), (8191, 8191), (1, 1), (8190, 8190), (2048, 2048)]
+    prec = {"float": 1, "bf16": 2}[dtype]
+    want = light_cone(x, prec, samples, T)
+    gotv = np.array([got[i, j] for i, j in samples])
+    assert np.array_equal(gotv.view(np.uint8), want.view(np.uint8))
+    # accuracy against binary64 on the same samples
+    x64 = synthetic.jacobi_field(dims, stream=1, dtype="double")
+    ref = light_cone(x64, 0, samples, T)
+    vals = gotv.astype(np.float64) if dtype == "float" else oracle.bf16_to_f32(gotv).astype(np.float64)
+    err = np.abs(vals - ref).max() / np.abs(ref).max()
+    assert err <= (1e-5 if dtype == "float" else 2e-2)
