@@ -370,6 +370,168 @@ def reference_arm(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------------------------------------
+# the other workloads (not the default line): 3-D, the instance batch, the triangular GEMM and
+# the B all-gather alone.  Each prints its own JSON line.
+# ---------------------------------------------------------------------------------------------
+
+def _events(torch, stream, fn, reps):
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def workload_stencil3d(H, torch, stream, args):
+    import synthetic
+    n, nb, iters = 512, 37, 50
+    boxes = synthetic.kd_boxes(n, nb, stream=3)
+    work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
+    x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
+    H.HDArrayInit(ndev=nb)
+    H.HDArraySetStream(stream.cuda_stream)
+    B = H.HDArrayCreate("B", "float", None, n, n, n)
+    A = H.HDArrayCreate("A", "float", None, n, n, n)
+    D = H.HDArrayPartitionManual((n, n, n), boxes)
+    W = H.HDArrayPartitionManual((n, n, n), work)
+    H.HDArrayWrite(B, torch.from_numpy(x).pin_memory(), D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("stencil3d", W, B, A)
+        H.HDArrayApplyKernel("stencil3d", W, A, B)
+    H.HDArrayApplyKernel("stencil3d", W, B, A)
+    import numpy as np
+    xbytes = sum(int(np.prod(np.subtract(hi, lo))) for _, _, lo, hi in H.HDArrayGetPlan(B)) * 4
+    H.HDArrayApplyKernel("stencil3d", W, A, B)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("stencil3d", W, B, A)
+    H.HDArrayApplyKernel("stencil3d", W, A, B)
+    gid = H.HDArrayGraphEnd()
+    for _ in range(args.warmup):
+        H.HDArrayGraphLaunch(gid, iters // 2)
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
+    cells = sum(int(np.prod(np.subtract(hi, lo))) for lo, hi in work)
+    per = ms / iters
+    algo = cells * 8 + 2 * xbytes
+    hbm, src = peaks()
+    H.HDArrayExit()
+    return {"workload": "3-D 7-point 512^3 FP32, 37 uneven manual partitions, 50 iterations per step",
+            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9,
+            "ms_per_step": ms, "us_per_iter": per * 1e3,
+            "roofline": {"bound": "hbm", "kernel": "k_stencil3d<f32>", "achieved": algo / (per * 1e-3) / 1e9,
+                         "peak": hbm, "frac": algo / (per * 1e-3) / 1e9 / hbm, "peak_source": src,
+                         "algo_bytes_per_launch": algo}}
+
+
+def workload_batch(H, torch, stream, args):
+    import numpy as np
+    import synthetic
+    insts = synthetic.jacobi_instances(512, stream=5)
+    iters = 200
+    ndev = max(p for _, _, p, _ in insts)
+    H.HDArrayInit(ndev=ndev)
+    H.HDArraySetStream(stream.cuda_stream)
+    arrs = []
+    cells = 0
+    for i, (r, c, P, kind) in enumerate(insts):
+        t = H.ROW if kind == "ROW" else H.COL
+        x = synthetic.jacobi_field((r, c), stream=1000 + i, dtype="float")
+        B = H.HDArrayCreate("B", "float", None, r, c)
+        A = H.HDArrayCreate("A", "float", None, r, c)
+        D = H.HDArrayPartition(t, (r, c), (0, 0), (r, c), P)
+        W = H.HDArrayPartition(t, (r, c), (1, 1), (r - 1, c - 1), P)
+        H.HDArrayWrite(B, x, D)
+        arrs.append((B, A, W))
+        cells += (r - 2) * (c - 2)
+
+    def iteration(flip):
+        H.HDArrayBatchBegin()
+        for B, A, W in arrs:
+            if flip:
+                H.HDArrayApplyKernel("jacobi2d", W, A, B)
+            else:
+                H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayBatchEnd()
+
+    for _ in range(2):
+        iteration(False)
+        iteration(True)
+    H.HDArrayGraphBegin()
+    iteration(False)
+    iteration(True)
+    gid = H.HDArrayGraphEnd()
+    for _ in range(args.warmup):
+        H.HDArrayGraphLaunch(gid, iters // 2)
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
+    per = ms / iters
+    hbm, src = peaks()
+    H.HDArrayExit()
+    return {"workload": "batch of 512 Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL parts, "
+                        "FP32), all instances in one launch per iteration, 200 iterations per step",
+            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9, "cells": cells,
+            "ms_per_step": ms, "us_per_iter": per * 1e3,
+            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d<f32> (batched)",
+                         "achieved": cells * 8 / (per * 1e-3) / 1e9, "peak": hbm,
+                         "frac": cells * 8 / (per * 1e-3) / 1e9 / hbm, "peak_source": src}}
+
+
+def workload_trmm(H, torch, stream, args):
+    import numpy as np
+    import synthetic
+    n, m, P = 8192, 4096, 8
+    a, b = synthetic.tri_gemm_inputs(n, m, stream=4, dtype="double")
+    H.HDArrayInit(ndev=P)
+    H.HDArraySetStream(stream.cuda_stream)
+    A = H.HDArrayCreate("A", "double", None, n, n)
+    B = H.HDArrayCreate("B", "double", None, n, m)
+    C = H.HDArrayCreate("C", "double", None, n, m)
+    R = H.HDArrayPartition(H.ROW, (n, m), (0, 0), (n, m), P)
+    RA = H.HDArrayPartition(H.ROW, (n, n), (0, 0), (n, n), P)
+    rows = [n * p // P for p in range(P + 1)]
+    for p in range(P):
+        r0, r1 = rows[p], rows[p + 1]
+        H.HDArraySetTrapezoidUse("trmm", R, A, p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1))
+        H.HDArraySetAbsoluteUse("exchange", R, B, p, (0, 0), (n, m))
+    bh = torch.from_numpy(b).pin_memory()
+    H.HDArrayWrite(A, torch.from_numpy(a).pin_memory(), RA)
+    # the all-gather of B alone (7/8 of B to each of 8 devices), timed from freshly written B
+    ex = []
+    for _ in range(max(2, args.steps // 2)):
+        H.HDArrayWrite(B, bh, R)
+        ex.append(_events(torch, stream, lambda: H.HDArrayApplyKernel("exchange", R, B), 1))
+    moved = 7 * n * m * 8
+    exch_ms = min(ex[1:]) if len(ex) > 1 else ex[0]
+    H.HDArrayWrite(B, bh, R)
+    H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)  # first call carries the all-gather
+    H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)
+    ms = _events(torch, stream, lambda: H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0), max(1, args.steps // 4))
+    flops = 2.0 * m * (n * (n + 1) / 2)
+    H.HDArrayExit()
+    hbm, src = peaks()
+    return {"workload": "tril(A) 8192x8192 x B 8192x4096, FP64 plain form, 8 row partitions",
+            "metric": "TFLOP/s (algorithmic)", "value": flops / (ms * 1e-3) / 1e12, "ms_per_call": ms,
+            "exchange": {"bytes": moved, "ms": exch_ms, "GB_s": 2 * moved / (exch_ms * 1e-3) / 1e9,
+                         "hbm_frac": 2 * moved / (exch_ms * 1e-3) / 1e9 / hbm, "peak_source": src}}
+
+
+def run_workload(args):
+    import torch
+    from __graft_entry__ import build_library
+    from paper_1809_05657_gb300 import hdarray as H
+    build_library()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm}[args.workload]
+    out = fn(H, torch, stream, args)
+    out["steps"] = args.steps
+    out["warmup"] = args.warmup
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,6 +542,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=8192,
                     help="grid side (default 8192; smaller only for profiling captures)")
+    ap.add_argument("--workload", default="jacobi2d",
+                    choices=["jacobi2d", "stencil3d", "batch", "trmm"],
+                    help="jacobi2d is the benchmark line; the others print their own line")
     args = ap.parse_args()
     global N, CELLS
     N = args.grid
@@ -388,6 +553,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload != "jacobi2d":
+        return run_workload(args)
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)

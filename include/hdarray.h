@@ -118,6 +118,7 @@ int HDArrayPartition(PART_T type, int dim, ...);
  *   "sqdiff"    (HDArray_t *X, HDArray_t *Y, HDArray_t *R) R = (X - Y)^2 in double
  *   "gemm"      (A, B, C, double alpha, double beta, int ni, int nj, int nk)   (Listing 3)
  *   "trmm"      (A, B, C, double alpha, double beta)       the same with A lower triangular
+ *   "exchange"  (HDArray_t *X)                             the communication step alone
  * Asynchronous on the library stream. */
 void HDArrayApplyKernel(const char *kName, int partID, ...);
 

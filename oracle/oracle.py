@@ -224,6 +224,8 @@ KERNELS = {
     "gemm": KernelSpec(3, {0: [(0, ALL)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_gemm, nscal=2),
     # The same contraction with A lower triangular; its use of A is normally given as trapezoids.
     "trmm": KernelSpec(3, {0: [(0, ALL)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_gemm, nscal=2),
+    # The communication step alone (use at zero offsets or absolute sections, no definition).
+    "exchange": KernelSpec(1, {0: [(0, 0, 0)]}, {}, None),
     # Sec. 5, 2-D convolution: the Jacobi offsets plus the four diagonals (sets only).
     "conv2d": KernelSpec(2, {0: _C2 + [(0, 0)]}, {1: [(0, 0)]}, None),
 }

@@ -15,94 +15,54 @@
 // load.  Before marching, the warp copies its receive segments -- the parts of the sections its
 // device receives in this call (Eq. 1-2) that only this tile reads -- from the sender's buffer into
 // its own; __syncwarp then orders those stores before the march reads them.
-#include <cuda_bf16.h>
-
-#include "kernels.h"
+#include "stencil_common.cuh"
 
 namespace hda {
 
+// One output row of a tile: up / mid / dn are the rows above, at and below.
 template <int DT>
-struct Elem;
-template <>
-struct Elem<DT_F64> {
-    using E = double;   // storage
-    using A = double;   // arithmetic
-    using V = double2;  // 16-byte chunk
-    static constexpr int VEC = 2;
-    __device__ static void unpack(const V &v, A *a) { a[0] = v.x; a[1] = v.y; }
-    __device__ static V pack(const A *a) { return make_double2(a[0], a[1]); }
-    __device__ static A load1(const E *p) { return *p; }
-    __device__ static void store1(E *p, A a) { *p = a; }
-};
-template <>
-struct Elem<DT_F32> {
-    using E = float;
-    using A = float;
-    using V = float4;
-    static constexpr int VEC = 4;
-    __device__ static void unpack(const V &v, A *a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
-    __device__ static V pack(const A *a) { return make_float4(a[0], a[1], a[2], a[3]); }
-    __device__ static A load1(const E *p) { return *p; }
-    __device__ static void store1(E *p, A a) { *p = a; }
-};
-template <>
-struct Elem<DT_BF16> {
-    using E = __nv_bfloat16;
-    using A = float;
-    using V = uint4;
-    static constexpr int VEC = 8;
-    __device__ static void unpack(const V &v, A *a)
-    {
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            a[2 * i] = __uint_as_float(w[i] << 16);
-            a[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-        }
-    }
-    __device__ static uint32_t bits(A a) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)); }
-    __device__ static V pack(const A *a)
-    {
-        V v;
-        v.x = bits(a[0]) | (bits(a[1]) << 16);
-        v.y = bits(a[2]) | (bits(a[3]) << 16);
-        v.z = bits(a[4]) | (bits(a[5]) << 16);
-        v.w = bits(a[6]) | (bits(a[7]) << 16);
-        return v;
-    }
-    __device__ static A load1(const E *p) { return __bfloat162float(*p); }
-    __device__ static void store1(E *p, A a) { *p = __float2bfloat16_rn(a); }
-};
-
-// One row of a tile in registers: the lane's chunk plus the band's two edge elements (only
-// meaningful on lane 0 / lane 31).
-template <int DT>
-struct Row {
-    typename Elem<DT>::A v[Elem<DT>::VEC];
-    typename Elem<DT>::A l, r;
-};
-
-template <int DT>
-__device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::E *xrow, int x,
-                                         bool act, bool needL, bool needR, int lane)
+__device__ __forceinline__ void jacobi_row(const Row<DT> &up, const Row<DT> &mid, const Row<DT> &dn,
+                                           typename Elem<DT>::E *yrow, int x, int c0, int c1, bool full,
+                                           bool act, int lane)
 {
     using EL = Elem<DT>;
-    if (act) {
-        typename EL::V v = *reinterpret_cast<const typename EL::V *>(xrow + x);
-        EL::unpack(v, row.v);
+    using A = typename EL::A;
+    constexpr int VEC = EL::VEC;
+    A left = __shfl_up_sync(0xffffffffu, mid.v[VEC - 1], 1);
+    A right = __shfl_down_sync(0xffffffffu, mid.v[0], 1);
+    if (lane == 0) left = mid.l;
+    if (lane == 31) right = mid.r;
+    A out[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; k++) {
+        const A w = k > 0 ? mid.v[k - 1] : left;
+        const A e = k < VEC - 1 ? mid.v[k + 1] : right;
+        A s = w + e;
+        s = s + up.v[k];
+        s = s + dn.v[k];
+        out[k] = s * A(0.25);
     }
-    if (lane == 0 && needL) row.l = EL::load1(xrow + x - 1);
-    if (lane == 31 && needR) row.r = EL::load1(xrow + x + EL::VEC);
+    if (full) {
+        *reinterpret_cast<typename EL::V *>(yrow) = EL::pack(out);
+    } else if (act) {
+#pragma unroll
+        for (int k = 0; k < VEC; k++)
+            if (x + k >= c0 && x + k < c1) EL::store1(yrow + k, out[k]);
+    }
 }
 
-template <int DT, int PF>
+// NR rows live in a register ring: the row above, the row itself and NR - 2 rows ahead.  The march
+// is unrolled by NR so that every ring slot is a fixed register set (no moves between steps):
+// at unrolled step u of a group starting at output row r, slot u holds row r + u - 1, slot
+// (u+1) % NR row r + u and slot (u+2) % NR row r + u + 1; after the step slot u is refilled with
+// row r + u - 1 + NR.
+template <int DT, int NR>
 __global__ void __launch_bounds__(256) k_jacobi2d(const StenPart2D *__restrict__ parts,
                                                   const StenTile2D *__restrict__ tiles, int ntiles,
                                                   const Seg *__restrict__ segs)
 {
     using EL = Elem<DT>;
     using E = typename EL::E;
-    using A = typename EL::A;
     constexpr int VEC = EL::VEC;
     const int lane = threadIdx.x & 31;
     const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -110,75 +70,180 @@ __global__ void __launch_bounds__(256) k_jacobi2d(const StenPart2D *__restrict__
     const StenTile2D t = tiles[wid];
     const StenPart2D P = parts[t.part];
 
-    // receive: this tile's share of the device's incoming sections
-    for (int s = 0; s < t.nseg; s++) {
-        const Seg g = segs[t.seg0 + s];
-        const E *src = reinterpret_cast<const E *>(g.src);
-        E *dst = reinterpret_cast<E *>(g.dst);
-        for (int k = lane; k < g.n; k += 32) dst[k * g.ds] = src[k * g.ss];
-    }
-    __syncwarp();
+    receive_segments<E>(segs, t.seg0, t.nseg, lane);
 
     const int x = t.cb + lane * VEC;
     const bool act = (x < t.c1 + 1) && (x + VEC > t.c0 - 1);
     const bool needL = (t.cb >= t.c0) && (t.cb < t.c1);
     const bool needR = (t.cb + 32 * VEC - 1 >= t.c0) && (t.cb + 32 * VEC - 1 < t.c1);
-    const E *X = reinterpret_cast<const E *>(P.x) + (x - P.xlo1);
-    E *Y = reinterpret_cast<E *>(P.y) + (x - P.ylo1);
-    const int64_t xs = P.xs, ys = P.ys;
-
-    Row<DT> up, mid, q[PF];
-    load_row<DT>(up, X + (t.r0 - 1 - P.xlo0) * xs, 0, act, false, false, lane);
-    load_row<DT>(mid, X + (t.r0 - P.xlo0) * xs, 0, act, needL, needR, lane);
-#pragma unroll
-    for (int k = 0; k < PF; k++)
-        if (t.r0 + 1 + k <= t.r1) load_row<DT>(q[k], X + (t.r0 + 1 + k - P.xlo0) * xs, 0, act, needL, needR, lane);
-
     const bool full = (x >= t.c0) && (x + VEC <= t.c1);
-    for (int r = t.r0; r < t.r1; r++) {
-        const Row<DT> &dn = q[0];
-        A left = __shfl_up_sync(0xffffffffu, mid.v[VEC - 1], 1);
-        A right = __shfl_down_sync(0xffffffffu, mid.v[0], 1);
-        if (lane == 0) left = mid.l;
-        if (lane == 31) right = mid.r;
-        A out[VEC];
+    const int64_t xs = P.xs, ys = P.ys;
+    const E *xp = reinterpret_cast<const E *>(P.x) + (int64_t)(t.r0 - 1 - P.xlo0) * xs + (x - P.xlo1);
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.r0 - P.ylo0) * ys + (x - P.ylo1);
+
+    Row<DT> ring[NR];
 #pragma unroll
-        for (int k = 0; k < VEC; k++) {
-            const A w = k > 0 ? mid.v[k - 1] : left;
-            const A e = k < VEC - 1 ? mid.v[k + 1] : right;
-            A s = w + e;
-            s = s + up.v[k];
-            s = s + dn.v[k];
-            out[k] = s * A(0.25);
+    for (int k = 0; k < NR; k++) {
+        if (t.r0 - 1 + k <= t.r1) load_row<DT>(ring[k], xp, 0, act, needL, needR, lane);
+        xp += xs;
+    }
+    int r = t.r0;
+    for (; r + NR <= t.r1; r += NR) {
+#pragma unroll
+        for (int u = 0; u < NR; u++) {
+            jacobi_row<DT>(ring[u], ring[(u + 1) % NR], ring[(u + 2) % NR], yp, x, t.c0, t.c1, full, act, lane);
+            yp += ys;
+            if (r + u - 1 + NR <= t.r1) load_row<DT>(ring[u], xp, 0, act, needL, needR, lane);
+            xp += xs;
         }
-        E *yrow = Y + (r - P.ylo0) * ys;
-        if (full) {
-            *reinterpret_cast<typename EL::V *>(yrow) = EL::pack(out);
-        } else if (act) {
+    }
 #pragma unroll
-            for (int k = 0; k < VEC; k++)
-                if (x + k >= t.c0 && x + k < t.c1) EL::store1(yrow + k, out[k]);
+    for (int u = 0; u < NR; u++) {
+        if (r + u < t.r1) {
+            jacobi_row<DT>(ring[u], ring[(u + 1) % NR], ring[(u + 2) % NR], yp, x, t.c0, t.c1, full, act, lane);
+            yp += ys;
+            if (r + u - 1 + NR <= t.r1) load_row<DT>(ring[u], xp, 0, act, needL, needR, lane);
+            xp += xs;
         }
-        up = mid;
-        mid = q[0];
-#pragma unroll
-        for (int k = 0; k < PF - 1; k++) q[k] = q[k + 1];
-        const int nr = r + 1 + PF;
-        if (nr <= t.r1) load_row<DT>(q[PF - 1], X + (nr - P.xlo0) * xs, 0, act, needL, needR, lane);
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// The same tile with the prefetched rows in shared memory instead of registers: every lane
+// issues asynchronous 16-byte copies (cp.async) of its chunk of the rows ahead into a ring of NS
+// stages owned by its warp, so the bytes in flight per SM are bounded by shared memory, not by
+// registers.  Each lane reads back only what it copied itself (plus the band edges copied by lanes
+// 0 and 31), so no synchronisation beyond cp.async.wait_group is needed; horizontal neighbours
+// still come by shuffle.  Stage layout per warp: NS x (32 chunks + 2 edge slots) x 16 bytes.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cpa16(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa8(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa4(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Edge element copy: the smallest cp.async is 4 bytes, so a bfloat16 edge travels as the aligned
+// 4-byte pair that contains it.
+template <int DT>
+__device__ __forceinline__ void edge_copy(uint32_t saddr, const typename Elem<DT>::E *g, bool left)
+{
+    if (sizeof(typename Elem<DT>::E) == 8) cpa8(saddr, g);
+    else if (sizeof(typename Elem<DT>::E) == 4) cpa4(saddr, g);
+    else cpa4(saddr, left ? (const void *)(g - 1) : (const void *)g);
+}
+template <int DT>
+__device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, bool left)
+{
+    using A = typename Elem<DT>::A;
+    if (sizeof(typename Elem<DT>::E) == 8) return (A) * reinterpret_cast<const double *>(slot);
+    if (sizeof(typename Elem<DT>::E) == 4) return (A) * reinterpret_cast<const float *>(slot);
+    const uint32_t w = *reinterpret_cast<const uint32_t *>(slot);
+    return (A)__uint_as_float(left ? (w & 0xffff0000u) : (w << 16));
+}
+
+template <int DT, int NS>
+__global__ void __launch_bounds__(256) k_jacobi2d_async(const StenPart2D *__restrict__ parts,
+                                                        const StenTile2D *__restrict__ tiles,
+                                                        int ntiles, const Seg *__restrict__ segs)
+{
+    using EL = Elem<DT>;
+    using E = typename EL::E;
+    using A = typename EL::A;
+    constexpr int VEC = EL::VEC;
+    constexpr int SLOTS = 34;  // 32 chunks + left edge + right edge
+    extern __shared__ uint4 smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wid >= ntiles) return;  // warp-uniform
+    uint4 *ring = smem + (threadIdx.x >> 5) * NS * SLOTS;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+    const StenTile2D t = tiles[wid];
+    const StenPart2D P = parts[t.part];
+
+    receive_segments<E>(segs, t.seg0, t.nseg, lane);
+
+    const int x = t.cb + lane * VEC;
+    const bool act = (x < t.c1 + 1) && (x + VEC > t.c0 - 1);
+    const bool needL = (t.cb >= t.c0) && (t.cb < t.c1);
+    const bool needR = (t.cb + 32 * VEC - 1 >= t.c0) && (t.cb + 32 * VEC - 1 < t.c1);
+    const bool full = (x >= t.c0) && (x + VEC <= t.c1);
+    const bool doL = lane == 0 && needL, doR = lane == 31 && needR;
+    const int64_t xs = P.xs, ys = P.ys;
+    const E *xp = reinterpret_cast<const E *>(P.x) + (int64_t)(t.r0 - 1 - P.xlo0) * xs + (x - P.xlo1);
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.r0 - P.ylo0) * ys + (x - P.ylo1);
+
+    // prologue: rows r0-1 .. r0-2+NS into stages 0 .. NS-1
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        if (t.r0 - 1 + s <= t.r1) {
+            const uint32_t sa = ring_s + (uint32_t)(s * SLOTS) * 16u;
+            if (act) cpa16(sa + lane * 16u, xp);
+            if (doL) edge_copy<DT>(sa + 32u * 16u, xp - 1, true);
+            if (doR) edge_copy<DT>(sa + 33u * 16u, xp + VEC, false);
+        }
+        cpa_commit();
+        xp += xs;
+    }
+    for (int r = t.r0; r < t.r1; r++) {
+        const int k = r - t.r0;
+        cpa_wait<NS - 3>();  // rows up to r + 1 have landed
+        const uint4 *su = ring + (k % NS) * SLOTS, *sm = ring + ((k + 1) % NS) * SLOTS,
+                    *sd = ring + ((k + 2) % NS) * SLOTS;
+        Row<DT> up, mid, dn;
+        if (act) {
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(su + lane), up.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(sm + lane), mid.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(sd + lane), dn.v);
+        }
+        if (doL) mid.l = edge_read<DT>(sm + 32, true);
+        if (doR) mid.r = edge_read<DT>(sm + 33, false);
+        jacobi_row<DT>(up, mid, dn, yp, x, t.c0, t.c1, full, act, lane);
+        yp += ys;
+        // the row above is done with: refill its stage with row r - 1 + NS
+        if (r - 1 + NS <= t.r1) {
+            const uint32_t sa = ring_s + (uint32_t)((k % NS) * SLOTS) * 16u;
+            if (act) cpa16(sa + lane * 16u, xp);
+            if (doL) edge_copy<DT>(sa + 32u * 16u, xp - 1, true);
+            if (doR) edge_copy<DT>(sa + 33u * 16u, xp + VEC, false);
+        }
+        cpa_commit();
+        xp += xs;
+    }
+    cpa_wait<0>();
+}
+
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
-                            int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s)
+                            int ntiles, const Seg *segs, int warps_per_cta, int variant, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 4;
     const int grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const int block = 32 * warps_per_cta;
+    if (variant == 1) {
+        constexpr int NS = 8;
+        const size_t sm = (size_t)warps_per_cta * NS * 34 * 16;
+        switch (dtype) {
+        case DT_F64: k_jacobi2d_async<DT_F64, NS><<<grid, block, sm, s>>>(parts, tiles, ntiles, segs); break;
+        case DT_F32: k_jacobi2d_async<DT_F32, NS><<<grid, block, sm, s>>>(parts, tiles, ntiles, segs); break;
+        case DT_BF16: k_jacobi2d_async<DT_BF16, NS><<<grid, block, sm, s>>>(parts, tiles, ntiles, segs); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (dtype) {
-    case DT_F64: k_jacobi2d<DT_F64, 4><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
-    case DT_F32: k_jacobi2d<DT_F32, 4><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
-    case DT_BF16: k_jacobi2d<DT_BF16, 4><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
+    case DT_F64: k_jacobi2d<DT_F64, 6><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
+    case DT_F32: k_jacobi2d<DT_F32, 6><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
+    case DT_BF16: k_jacobi2d<DT_BF16, 5><<<grid, block, 0, s>>>(parts, tiles, ntiles, segs); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -49,20 +49,23 @@ struct StenTile2D {
     int32_t cb;
     int32_t seg0, nseg;
 };
-struct Seg {  // dst[k * ds] = src[k * ss] for k < n (element strides)
+struct Seg {  // dst[o * dso + k * ds] = src[o * sso + k * ss], k < n, o < m (element strides)
     const void *src;
     void *dst;
-    int64_t ss, ds;
-    int32_t n;
-    int32_t pad;
+    int64_t ss, ds;    // inner strides
+    int64_t sso, dso;  // outer strides
+    int32_t n, m;
 };
+// variant 0: prefetched rows in registers; variant 1: in shared memory via cp.async.
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
-                            int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s);
+                            int ntiles, const Seg *segs, int warps_per_cta, int variant,
+                            cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
-// 3-D 7-point step, fused with the exchange.  A tile is one CTA's job: output z in [z0, z1),
-// y in [y0, y1), x in [x0, x1) within a band of 32 vector chunks starting at xb; the CTA marches
-// along z with one warp per y row.
+// 3-D 7-point step, fused with the exchange.  A tile is one warp's job: output row y, x in
+// [x0, x1) inside a band of 32 vector chunks starting at xb, marching z over [z0, z1).
+// Consecutive tiles are consecutive rows, so the rows y-1 and y+1 a warp reads were just read by
+// its neighbours in the same CTA.
 // ------------------------------------------------------------------------------------------
 struct StenPart3D {
     const void *x;
@@ -72,12 +75,15 @@ struct StenPart3D {
 };
 struct StenTile3D {
     int32_t part;
-    int32_t z0, z1, y0, y1, x0, x1;
+    int32_t z0, z1;
+    int32_t y;
+    int32_t x0, x1;
     int32_t xb;
     int32_t seg0, nseg;
+    int32_t pad;
 };
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
-                             int ntiles, const Seg *segs, int rows_per_cta, cudaStream_t s);
+                             int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Element-wise residual R = (X - Y)^2 in double over boxes.

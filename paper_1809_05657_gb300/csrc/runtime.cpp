@@ -57,6 +57,7 @@ struct Ctx {
     // batching
     bool batching = false;
     std::vector<std::shared_ptr<Plan>> batch;
+    std::set<HDArray *> batch_used, batch_defined;  // arrays touched since HDArrayBatchBegin
     std::unordered_map<std::string, std::pair<std::shared_ptr<DevMem>, std::vector<LaunchRec>>> batch_cache;
     // graph recording
     bool recording = false, rec_invalid = false;
@@ -73,8 +74,10 @@ struct Ctx {
     double *host_result = nullptr;
     int red_blocks = 0;
     // tunables
-    int tile_rows = 64;
-    int warps_per_cta = 4;
+    int tile_rows = 64;     // 2-D tile height (rows per warp)
+    int warps_per_cta = 8;  // 2-D warps per CTA
+    int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
+    int tile_z = 64;        // 3-D tile depth (planes per warp)
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
     int last_error = 0;
@@ -138,6 +141,13 @@ void register_builtins(Ctx &c)
         k.name = "stencil3d"; k.kind = K_STENCIL3D; k.narr = 2; k.space = 1;
         k.use = {{off(0, 0, -1), off(0, 0, 1), off(0, -1, 0), off(0, 1, 0), off(-1, 0, 0), off(1, 0, 0)}, {}};
         k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // the communication step alone: bring each device's use sections of X up to date
+        KernelDef k;
+        k.name = "exchange"; k.kind = K_EXCHANGE; k.narr = 1; k.space = 0;
+        k.use = {{off(0, 0, 0)}};
+        k.def = {{}};
         add(k);
     }
     {   // residual field R = (X - Y)^2
@@ -262,10 +272,15 @@ int ensure_buffer(HDArray *a, int p, const Box &need)
     if (b.ptr && box_contains(b.alloc, need)) return HDARRAY_OK;
     if (g->recording) g->rec_invalid = true;  // recorded launches would point at the old buffer
     Box nb = b.ptr ? box_hull(b.alloc, need) : need;
+    // Innermost dimension: rows padded to whole 128-byte lines, with the origin at 1 (mod the line)
+    // in array coordinates, the same for every buffer.  Coordinate 1 -- the first element after a
+    // one-element boundary ring -- and every 128 bytes after it then start a line, so a work region
+    // that starts right after the ring is chunk-aligned for 16-byte vector access, and two buffers
+    // always agree on which coordinates are vector-aligned.
     const int in = a->dim - 1;
     const int64_t al = 128 / a->esize;
-    nb.lo[in] = align_down(nb.lo[in], al);
-    nb.hi[in] = align_up(nb.hi[in], al);
+    nb.lo[in] = align_down(nb.lo[in] - 1, al) + 1;
+    nb.hi[in] = align_up(nb.hi[in] - 1, al) + 1;
     DevBuf nbuf;
     nbuf.alloc = nb;
     set_strides(a, nbuf);
@@ -485,7 +500,7 @@ void clause_sets(const Part &pt, const HDArray *a, const std::vector<Offset> &of
 }
 
 std::string memo_key(const KernelDef &k, int part, const std::vector<HDArray *> &args,
-                     const std::vector<uint64_t> &absv)
+                     const std::vector<uint64_t> &absv, const std::vector<double> &scal)
 {
     std::string key = k.name;
     char buf[96];
@@ -495,6 +510,10 @@ std::string memo_key(const KernelDef &k, int part, const std::vector<HDArray *> 
         snprintf(buf, sizeof(buf), "|%llu:%llu:%d:%llu", (unsigned long long)args[i]->uid,
                  (unsigned long long)args[i]->generation, args[i]->cur,
                  (unsigned long long)absv[i]);
+        key += buf;
+    }
+    for (double v : scal) {  // scalars are compiled into the launches
+        snprintf(buf, sizeof(buf), "|%.17g", v);
         key += buf;
     }
     return key;
@@ -540,7 +559,8 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
         need += m.box.volume();
         if (box_overlaps(m.box, W)) exact = false;
     }
-    const int64_t cb0 = align_down(W.lo[1], VEC);
+    // bands start on 16-byte chunks of X's buffer (Y's buffer has the same phase, checked by the caller)
+    const int64_t cb0 = bx.alloc.lo[1] + align_down(W.lo[1] - bx.alloc.lo[1], VEC);
     for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += H) {
         for (int64_t cb = cb0; cb < W.hi[1]; cb += BAND) {
             StenTile2D t;
@@ -573,7 +593,9 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
                             sg.ss = src.st[0];
                             sg.ds = bx.st[0];
                         }
-                        sg.pad = 0;
+                        sg.m = 1;
+                        sg.sso = 0;
+                        sg.dso = 0;
                         covered += I.volume();
                         h.segs.push_back(sg);
                         t.nseg++;
@@ -581,6 +603,75 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
                 }
             }
             h.tiles.push_back(t);
+        }
+    }
+    return exact && covered == need;
+}
+
+// Tiles of the fused 3-D kernel for one device: one warp per (z chunk, x band, row y); the
+// receive segments are the parts of the incoming faces on the tile's six strips.
+bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
+                     const std::vector<Move> &recv, bool want_segs, Sten3DHost &h)
+{
+    const DevBuf &bx = X->buf[p], &by = Y->buf[p];
+    StenPart3D P;
+    P.x = bx.ptr;
+    P.y = by.ptr;
+    P.xlo0 = bx.alloc.lo[0]; P.xlo1 = bx.alloc.lo[1]; P.xlo2 = bx.alloc.lo[2];
+    P.xs0 = bx.st[0]; P.xs1 = bx.st[1];
+    P.ylo0 = by.alloc.lo[0]; P.ylo1 = by.alloc.lo[1]; P.ylo2 = by.alloc.lo[2];
+    P.ys0 = by.st[0]; P.ys1 = by.st[1];
+    h.parts.push_back(P);
+    const int VEC = 16 / X->esize, BAND = 32 * VEC;
+    const int ZC = std::max(1, g->tile_z);
+    bool exact = true;
+    int64_t covered = 0, need = 0;
+    for (const Move &m : recv) {
+        need += m.box.volume();
+        if (box_overlaps(m.box, W)) exact = false;
+    }
+    const int64_t xb0 = bx.alloc.lo[2] + align_down(W.lo[2] - bx.alloc.lo[2], VEC);
+    for (int64_t zc = W.lo[0]; zc < W.hi[0]; zc += ZC) {
+        for (int64_t xb = xb0; xb < W.hi[2]; xb += BAND) {
+            for (int64_t y = W.lo[1]; y < W.hi[1]; y++) {
+                StenTile3D t;
+                t.part = part_index;
+                t.z0 = (int32_t)zc;
+                t.z1 = (int32_t)std::min<int64_t>(zc + ZC, W.hi[0]);
+                t.y = (int32_t)y;
+                t.x0 = (int32_t)std::max<int64_t>(W.lo[2], xb);
+                t.x1 = (int32_t)std::min<int64_t>(W.hi[2], xb + BAND);
+                t.xb = (int32_t)xb;
+                t.seg0 = (int32_t)h.segs.size();
+                t.nseg = 0;
+                t.pad = 0;
+                if (want_segs && exact) {
+                    const Box strips[6] = {
+                        make_box(t.z0 - 1, y, t.x0, t.z0, y + 1, t.x1), make_box(t.z1, y, t.x0, t.z1 + 1, y + 1, t.x1),
+                        make_box(t.z0, y - 1, t.x0, t.z1, y, t.x1), make_box(t.z0, y + 1, t.x0, t.z1, y + 2, t.x1),
+                        make_box(t.z0, y, t.x0 - 1, t.z1, y + 1, t.x0), make_box(t.z0, y, t.x1, t.z1, y + 1, t.x1 + 1)};
+                    for (const Move &m : recv) {
+                        const DevBuf &src = X->buf[m.src];
+                        for (int s = 0; s < 6; s++) {
+                            Box I = box_intersect(m.box, strips[s]);
+                            if (I.empty()) continue;
+                            Seg sg;
+                            sg.src = src.ptr + elem_off(src, I.lo) * X->esize;
+                            sg.dst = bx.ptr + elem_off(bx, I.lo) * X->esize;
+                            sg.n = (int32_t)(I.hi[2] - I.lo[2]);  // along x (contiguous)
+                            sg.m = (int32_t)(I.hi[0] - I.lo[0]);  // along z
+                            sg.ss = 1;
+                            sg.ds = 1;
+                            sg.sso = src.st[0];
+                            sg.dso = bx.st[0];
+                            covered += I.volume();
+                            h.segs.push_back(sg);
+                            t.nseg++;
+                        }
+                    }
+                }
+                h.tiles.push_back(t);
+            }
         }
     }
     return exact && covered == need;
@@ -619,8 +710,10 @@ int compile_plan(Plan &pl)
         h.dtype = X->dtype;
         std::vector<std::pair<int, int>> dev_ranges;
         int idx = 0;
+        const int VEC2 = 16 / X->esize;
         for (int p = 0; p < pt.nparts; p++) {
             if (pt.box[p].empty()) continue;
+            if ((Y->buf[p].alloc.lo[1] - X->buf[p].alloc.lo[1]) % VEC2 != 0) return HDARRAY_ERR_STATE;
             std::vector<Move> recv;
             if (sx)
                 for (const Move &m : sx->moves)
@@ -653,7 +746,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = g->warps_per_cta;
+                L.n0 = r.second - r.first; L.n1 = g->warps_per_cta; L.n2 = g->variant;
                 pl.launches.push_back(L);
             }
         } else {
@@ -664,13 +757,79 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = g->warps_per_cta;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = g->warps_per_cta; L.n2 = g->variant;
                 pl.launches.push_back(L);
             }
         }
         pl.fused = fused;
         pl.copy_host = xfer;
         pl.s2 = std::move(h);
+        return HDARRAY_OK;
+    }
+
+    if (k.kind == K_STENCIL3D) {
+        HDArray *X = pl.args[0], *Y = pl.args[1];
+        const ArrStep *sx = nullptr;
+        for (const ArrStep &st : pl.steps)
+            if (st.a == X) sx = &st;
+        bool fused = !plain;
+        Sten3DHost h;
+        h.dtype = X->dtype;
+        std::vector<std::pair<int, int>> dev_ranges;
+        int idx = 0;
+        const int VEC = 16 / X->esize;
+        for (int p = 0; p < pt.nparts; p++) {
+            if (pt.box[p].empty()) continue;
+            if ((Y->buf[p].alloc.lo[2] - X->buf[p].alloc.lo[2]) % VEC != 0) return HDARRAY_ERR_STATE;
+            std::vector<Move> recv;
+            if (sx)
+                for (const Move &m : sx->moves)
+                    if (m.dst == p) recv.push_back(m);
+            int t0 = (int)h.tiles.size();
+            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h)) fused = false;
+            dev_ranges.push_back({t0, (int)h.tiles.size()});
+        }
+        if (!fused) {
+            h.segs.clear();
+            for (StenTile3D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
+            if (sx) add_moves(*sx);
+        }
+        blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
+        blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart3D)});
+        blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile3D)});
+        blobs.push_back({h.segs.data(), h.segs.size() * sizeof(Seg)});
+        std::vector<const char *> addr;
+        int rc = upload(blobs, pl.tables, addr);
+        if (rc) return rc;
+        const CopyTask *dx = (const CopyTask *)addr[0];
+        if (plain) {
+            for (auto &gr : xfer_groups)
+                if (gr.second > gr.first) {
+                    LaunchRec L; L.kind = L_COPY; L.p0 = dx + gr.first; L.n0 = gr.second - gr.first;
+                    pl.launches.push_back(L);
+                }
+            for (auto &r : dev_ranges) {
+                if (r.second <= r.first) continue;
+                LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
+                L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
+                L.n0 = r.second - r.first; L.n1 = 8;
+                pl.launches.push_back(L);
+            }
+        } else {
+            if (!xfer.empty()) {
+                LaunchRec L; L.kind = L_COPY; L.p0 = dx; L.n0 = (int64_t)xfer.size();
+                pl.launches.push_back(L);
+            }
+            if (!h.tiles.empty()) {
+                LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
+                L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = 8;
+                pl.launches.push_back(L);
+            }
+        }
+        pl.fused = fused;
+        pl.copy_host = xfer;
+        pl.s3 = std::move(h);
         return HDARRAY_OK;
     }
 
@@ -724,6 +883,8 @@ int compile_plan(Plan &pl)
             gp.push_back(q);
             max_rows = std::max<int>(max_rows, q.i1 - q.i0);
             max_cols = std::max<int>(max_cols, q.j1 - q.j0);
+        } else if (k.kind == K_EXCHANGE) {
+            continue;
         } else {
             return HDARRAY_ERR_UNSUPPORTED;
         }
@@ -830,7 +991,6 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
             for (int d = 0; d < a[0]->dim; d++)
                 if (w.lo[d] < 1 || w.hi[d] > a[0]->n[d] - 1) return HDARRAY_ERR_RANGE;
         }
-        if (k.kind == K_STENCIL3D) return HDARRAY_ERR_UNSUPPORTED;
         break;
     case K_COPY:
         if (a[0] == a[1] || !same(a[0], a[1]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
@@ -838,6 +998,8 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
     case K_SQDIFF:
         if (!same(a[0], a[1]) || !same(a[0], a[2]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
         if (a[2]->dtype != DT_F64 || a[2] == a[0] || a[2] == a[1]) return HDARRAY_ERR_INVAL;
+        break;
+    case K_EXCHANGE:
         break;
     case K_GEMM:
     case K_TRMM: {
@@ -876,7 +1038,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
             abss[i] = &it->second;
         }
     }
-    const std::string key = memo_key(k, part, args, absv);
+    const std::string key = memo_key(k, part, args, absv, scal);
     std::shared_ptr<Plan> pl;
     auto mit = g->memo.find(key);
     if (mit != g->memo.end()) {
@@ -925,6 +1087,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
             st.post = intern(args[i], std::move(s));
             pl->steps.push_back(std::move(st));
         }
+        if (g->memo.size() >= 16384) g->memo.clear();  // bounded; plans held by graphs stay alive
         g->memo[key] = pl;
         g->counters[2]++;
         if (trace()) {
@@ -932,6 +1095,17 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
             for (auto &st : pl->steps) for (auto &m : st.moves) nb += m.box.volume() * st.a->esize;
             fprintf(stderr, "hdarray: plan %llu for %s part %d: %lld bytes to move\n",
                     (unsigned long long)pl->id, k.name.c_str(), part, (long long)nb);
+        }
+    }
+    // calls of one batch must be independent: refuse one that touches what another defines
+    if (g->batching) {
+        for (const ArrStep &st : pl->steps) {
+            if (g->batch_defined.count(st.a)) return HDARRAY_ERR_RACE;
+            if (st.defined && g->batch_used.count(st.a)) return HDARRAY_ERR_RACE;
+        }
+        for (const ArrStep &st : pl->steps) {
+            if (st.defined) g->batch_defined.insert(st.a);
+            else g->batch_used.insert(st.a);
         }
     }
     // buffers must cover every device's sections before anything is compiled or launched
@@ -1038,7 +1212,7 @@ int flush_batch()
         for (auto &kv : sten) {
             LaunchRec L; L.kind = L_JACOBI2D; L.dtype = kv.first;
             L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2];
-            L.n0 = (int64_t)kv.second.tiles.size(); L.n1 = g->warps_per_cta;
+            L.n0 = (int64_t)kv.second.tiles.size(); L.n1 = g->warps_per_cta; L.n2 = g->variant;
             ai += 3;
             if (L.n0 > 0) ls.push_back(L);
         }
@@ -1428,6 +1602,10 @@ int init_impl(int ndev, unsigned flags)
         if (tr && atoi(tr) > 0) g->tile_rows = atoi(tr);
         const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
+        const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
+        if (vv && (atoi(vv) == 0 || atoi(vv) == 1)) g->variant = atoi(vv);
+        const char *tz = getenv("HDARRAY_TILE_Z");
+        if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
     }
     g->inited = true;
     return HDARRAY_OK;
@@ -1448,7 +1626,10 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_COPY: return launch_copy((const CopyTask *)L.p0, (int)L.n0, s);
     case L_JACOBI2D:
         return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
-                               (const Seg *)L.p2, (int)L.n1, s);
+                               (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
+    case L_STENCIL3D:
+        return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
+                                (const Seg *)L.p2, (int)L.n1, s);
     case L_SQDIFF: return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, s);
     case L_GEMM64:
         return launch_gemm_f64((const GemmPart *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, L.f0, L.f1, s);
@@ -1861,6 +2042,8 @@ int HDArrayBatchBegin(void)
 {
     if (!g || !g->inited || g->batching) return HDARRAY_ERR_STATE;
     g->batching = true;
+    g->batch_used.clear();
+    g->batch_defined.clear();
     return HDARRAY_OK;
 }
 
@@ -1868,6 +2051,8 @@ int HDArrayBatchEnd(void)
 {
     if (!g || !g->inited || !g->batching) return HDARRAY_ERR_STATE;
     g->batching = false;
+    g->batch_used.clear();
+    g->batch_defined.clear();
     int rc = flush_batch();
     if (rc) set_err(rc);
     return rc;

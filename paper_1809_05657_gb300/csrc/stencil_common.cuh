@@ -1,0 +1,103 @@
+// stencil_common.cuh -- storage types, register rows and the receive phase shared by the fused
+// stencil kernels (k_stencil2d.cu, k_stencil3d.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace hda {
+
+template <int DT>
+struct Elem;
+template <>
+struct Elem<DT_F64> {
+    using E = double;   // storage
+    using A = double;   // arithmetic
+    using V = double2;  // 16-byte chunk
+    static constexpr int VEC = 2;
+    __device__ static void unpack(const V &v, A *a) { a[0] = v.x; a[1] = v.y; }
+    __device__ static V pack(const A *a) { return make_double2(a[0], a[1]); }
+    __device__ static A load1(const E *p) { return *p; }
+    __device__ static void store1(E *p, A a) { *p = a; }
+};
+template <>
+struct Elem<DT_F32> {
+    using E = float;
+    using A = float;
+    using V = float4;
+    static constexpr int VEC = 4;
+    __device__ static void unpack(const V &v, A *a) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+    __device__ static V pack(const A *a) { return make_float4(a[0], a[1], a[2], a[3]); }
+    __device__ static A load1(const E *p) { return *p; }
+    __device__ static void store1(E *p, A a) { *p = a; }
+};
+template <>
+struct Elem<DT_BF16> {
+    using E = __nv_bfloat16;
+    using A = float;
+    using V = uint4;
+    static constexpr int VEC = 8;
+    __device__ static void unpack(const V &v, A *a)
+    {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            a[2 * i] = __uint_as_float(w[i] << 16);
+            a[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+    __device__ static uint32_t bits(A a) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    __device__ static V pack(const A *a)
+    {
+        V v;
+        v.x = bits(a[0]) | (bits(a[1]) << 16);
+        v.y = bits(a[2]) | (bits(a[3]) << 16);
+        v.z = bits(a[4]) | (bits(a[5]) << 16);
+        v.w = bits(a[6]) | (bits(a[7]) << 16);
+        return v;
+    }
+    __device__ static A load1(const E *p) { return __bfloat162float(*p); }
+    __device__ static void store1(E *p, A a) { *p = __float2bfloat16_rn(a); }
+};
+
+// Copy a tile's receive segments (sender buffer -> own buffer), then order those stores before
+// the warp's loads of its own buffer.
+template <typename E>
+__device__ __forceinline__ void receive_segments(const Seg *__restrict__ segs, int seg0, int nseg, int lane)
+{
+    for (int s = 0; s < nseg; s++) {
+        const Seg g = segs[seg0 + s];
+        const E *src = reinterpret_cast<const E *>(g.src);
+        E *dst = reinterpret_cast<E *>(g.dst);
+        const int total = g.n * g.m;
+        for (int i = lane; i < total; i += 32) {
+            const int o = i / g.n, k = i - o * g.n;
+            dst[o * g.dso + k * g.ds] = src[o * g.sso + k * g.ss];
+        }
+    }
+    __syncwarp();
+}
+
+// One row of a tile in registers: the lane's chunk plus the band's two edge elements (only
+// meaningful on lane 0 / lane 31).
+template <int DT>
+struct Row {
+    typename Elem<DT>::A v[Elem<DT>::VEC];
+    typename Elem<DT>::A l, r;
+};
+
+template <int DT>
+__device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::E *xrow, int x,
+                                         bool act, bool needL, bool needR, int lane)
+{
+    using EL = Elem<DT>;
+    if (act) {
+        typename EL::V v = *reinterpret_cast<const typename EL::V *>(xrow + x);
+        EL::unpack(v, row.v);
+    }
+    if (lane == 0 && needL) row.l = EL::load1(xrow + x - 1);
+    if (lane == 31 && needR) row.r = EL::load1(xrow + x + EL::VEC);
+}
+
+}  // namespace hda

@@ -291,10 +291,10 @@ def test_batch_rejects_dependent_calls(gpu_lib):
     W = H.HDArrayPartition(ROW, (16, 16), (1, 1), (15, 15), 2)
     H.HDArrayBatchBegin()
     H.HDArrayApplyKernel("jacobi2d", W, B, A)
-    H.HDArrayApplyKernel("jacobi2d", W, A, B)  # uses what the first call defines
     with pytest.raises(H.HDArrayError) as e:
-        H.HDArrayBatchEnd()
+        H.HDArrayApplyKernel("jacobi2d", W, A, B)  # uses what the first call defines
     assert e.value.code == -3
+    H.HDArrayBatchEnd()  # the first call still runs
 
 
 @pytest.mark.parametrize("dtype", ["float", "bf16"])
@@ -400,5 +400,119 @@ def test_full_size_8192_block16_graph(gpu_lib, dtype):
     x64 = synthetic.jacobi_field(dims, stream=1, dtype="double")
     ref = light_cone(x64, 0, samples, T)
     vals = gotv.astype(np.float64) if dtype == "float" else oracle.bf16_to_f32(gotv).astype(np.float64)
-    err = np.abs(vals - ref).max() / np.abs(ref).max()
-    assert err <= (1e-5 if dtype == "float" else 2e-2)
+    if dtype == "float":
+        assert np.abs(vals - ref).max() / np.abs(ref).max() <= 1e-5
+    else:
+        # one rounding to bfloat16 per step, each at most 2^-9 of the field's maximum, and the
+        # Jacobi average does not amplify errors: after T steps the error is at most T * 2^-9 * max|x0|
+        assert np.abs(vals - ref).max() <= T * 2.0 ** -9 * np.abs(x64).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# 3-D 7-point stencil on uneven manual partitions
+# ---------------------------------------------------------------------------------------------
+
+def stencil3d_prog(n, boxes, iters, dtype):
+    work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
+    dims = (n, n, n)
+    prog = [("create", "B", dtype, dims), ("create", "A", dtype, dims),
+            ("manual", "D", dims, boxes), ("manual", "W", dims, work),
+            ("write", "B", "D")]
+    x, y = "B", "A"
+    for _ in range(iters):
+        prog.append(("apply", "stencil3d", "W", [x, y]))
+        x, y = y, x
+    return prog, x
+
+
+@pytest.mark.parametrize("dtype", ["float", "double", "bf16"])
+@pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
+def test_stencil3d_parity(gpu_lib, dtype, mode):
+    n = 40
+    boxes = synthetic.kd_boxes(n, 9, stream=61, min_ext=6, max_ext=40)
+    x = synthetic.jacobi_field((n, n, n), stream=62, dtype=dtype)
+    prog, last = stencil3d_prog(n, boxes, 4, dtype)
+    lib, orc, *_ = run_program(prog, len(boxes), {"B": x}, gpu_lib, mode=mode)
+    got = np.zeros((n, n, n), NP[dtype])
+    H.HDArrayRead(lib.arrays[last], got, lib.parts["D"])
+    assert np.array_equal(got.view(np.uint8), orc.arrays[last].G.view(np.uint8))
+
+
+def test_stencil3d_wide_rows(gpu_lib):
+    """Boxes wider than one band (several x bands per row) and ragged z chunks."""
+    n = 70
+    dims = (n, n, 300)
+    boxes = [((0, 0, 0), (35, 70, 130)), ((0, 0, 130), (35, 70, 300)), ((35, 0, 0), (70, 33, 300)),
+             ((35, 33, 0), (70, 70, 300))]
+    work = [(tuple(max(1, v) for v in lo), tuple(min(d - 1, v) for v, d in zip(hi, dims))) for lo, hi in boxes]
+    x = synthetic.jacobi_field(dims, stream=63, dtype="float")
+    prog = [("create", "B", "float", dims), ("create", "A", "float", dims),
+            ("manual", "D", dims, boxes), ("manual", "W", dims, work), ("write", "B", "D"),
+            ("apply", "stencil3d", "W", ["B", "A"]), ("apply", "stencil3d", "W", ["A", "B"]),
+            ("apply", "stencil3d", "W", ["B", "A"])]
+    lib, orc, *_ = run_program(prog, 4, {"B": x}, gpu_lib)
+    got = np.zeros(dims, np.float32)
+    H.HDArrayRead(lib.arrays["A"], got, lib.parts["D"])
+    assert np.array_equal(got, orc.arrays["A"].G)
+
+
+def light_cone3(x, prec, samples, T):
+    n0, n1, n2 = x.shape
+    out = []
+    L = oracle.lib()
+    for (i, j, k) in samples:
+        lo = [max(0, v - T - 1) for v in (i, j, k)]
+        hi = [min(n, v + T + 2) for v, n in zip((i, j, k), (n0, n1, n2))]
+        B = np.ascontiguousarray(x[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])
+        A = B.copy()
+        g = np.meshgrid(*[np.arange(a, b) for a, b in zip(lo, hi)], indexing="ij")
+        inside = np.ones(B.shape, bool)
+        for d, n in enumerate((n0, n1, n2)):
+            inside &= (g[d] >= 1) & (g[d] < n - 1)
+        border = np.zeros(B.shape, bool)
+        for d in range(3):
+            idx = [slice(None)] * 3
+            idx[d] = 0
+            border[tuple(idx)] = True
+            idx[d] = -1
+            border[tuple(idx)] = True
+        work = np.ascontiguousarray((inside & ~border).astype(np.uint8))
+        for _ in range(T):
+            rc = L.orc_stencil3d(prec, B.shape[0], B.shape[1], B.shape[2], B.ctypes.data, A.ctypes.data,
+                                 work.ctypes.data)
+            assert rc == 0
+            A, B = B, A
+        out.append(B[i - lo[0], j - lo[1], k - lo[2]])
+    return np.array(out)
+
+
+def test_full_size_stencil3d_512_37_boxes(gpu_lib):
+    n, T = 512, 50
+    boxes = synthetic.kd_boxes(n, 37, stream=3)
+    x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
+    gpu_lib(37)
+    B = H.HDArrayCreate("B", "float", None, n, n, n)
+    A = H.HDArrayCreate("A", "float", None, n, n, n)
+    D = H.HDArrayPartitionManual((n, n, n), boxes)
+    work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
+    W = H.HDArrayPartitionManual((n, n, n), work)
+    H.HDArrayWrite(B, x, D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("stencil3d", W, B, A)
+        H.HDArrayApplyKernel("stencil3d", W, A, B)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("stencil3d", W, B, A)
+    H.HDArrayApplyKernel("stencil3d", W, A, B)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, (T - 6) // 2)
+    got = np.zeros((n, n, n), np.float32)
+    H.HDArrayRead(B, got, D)
+    rng = np.random.default_rng(9)
+    samples = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(6)]
+    for lo, hi in boxes[:6]:  # box corners and faces: T-junctions of uneven partitions
+        samples.append((lo[0], min(hi[1], n - 1), lo[2]))
+        samples.append((min(hi[0], n - 1) - 1, lo[1], max(lo[2] - 1, 0)))
+    samples += [(0, 0, 0), (1, 1, 1), (510, 510, 510)]
+    want = light_cone3(x, 1, samples, T)
+    gotv = np.array([got[s] for s in samples])
+    assert np.array_equal(gotv, want)

@@ -228,6 +228,20 @@ def test_full_size_stencil3d_37_boxes(host_lib):
     assert run_both(prog, 37, host_lib, coords={"A": coords, "B": coords}) >= 3
 
 
+def test_full_size_stencil3d_kernel_37_boxes(host_lib):
+    n = 512
+    boxes = synthetic.kd_boxes(n, 37, stream=3)
+    work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
+    cuts = [sorted({b[0][d] for b in boxes} | {b[1][d] for b in boxes}) for d in range(3)]
+    coords = boundary_samples((n, n, n), cuts, 4000, stream=5, per_line=24)
+    prog = [("create", "B", "float", (n, n, n)), ("create", "A", "float", (n, n, n)),
+            ("manual", "D", (n, n, n), boxes), ("manual", "W", (n, n, n), work),
+            ("write", "B", "D"),
+            ("apply", "stencil3d", "W", ["B", "A"]), ("apply", "stencil3d", "W", ["A", "B"]),
+            ("apply", "stencil3d", "W", ["B", "A"]), ("apply", "stencil3d", "W", ["A", "B"])]
+    assert run_both(prog, 37, host_lib, coords={"A": coords, "B": coords}) >= 4
+
+
 def test_full_size_trmm_8192(host_lib):
     n, m, P = 8192, 4096, 8
     rows = [1024 * p for p in range(P + 1)]
