@@ -51,15 +51,32 @@ __global__ void __launch_bounds__(256) k_reduce(const RedTask *__restrict__ task
     __shared__ double wsum[8];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double acc = ident<OP>();
+    // four independent accumulators per lane (column c goes to accumulator (c / 32) % 4), folded
+    // together in a fixed order: more loads in flight, same result on every run
+    double a0 = ident<OP>(), a1 = a0, a2 = a0, a3 = a0;
     for (int ti = blockIdx.x; ti < ntasks; ti += gridDim.x) {
         const RedTask t = tasks[ti];
         for (int r = t.row_begin + warp; r < t.row_end; r += nw) {
             const int o = r / t.n_mid, m = r - o * t.n_mid;
             const int64_t base = o * t.s_outer + m * t.s_mid;
-            for (int c = lane; c < t.n_inner; c += 32) acc = fold<OP>(acc, ldd<DT>(t.x, base + c));
+            int c = lane;
+            for (; c + 96 < t.n_inner; c += 128) {
+                const double x0 = ldd<DT>(t.x, base + c), x1 = ldd<DT>(t.x, base + c + 32);
+                const double x2 = ldd<DT>(t.x, base + c + 64), x3 = ldd<DT>(t.x, base + c + 96);
+                a0 = fold<OP>(a0, x0);
+                a1 = fold<OP>(a1, x1);
+                a2 = fold<OP>(a2, x2);
+                a3 = fold<OP>(a3, x3);
+            }
+            for (int u = 0; c < t.n_inner; c += 32, u++) {
+                const double x = ldd<DT>(t.x, base + c);
+                if (u == 0) a0 = fold<OP>(a0, x);
+                else if (u == 1) a1 = fold<OP>(a1, x);
+                else a2 = fold<OP>(a2, x);
+            }
         }
     }
+    double acc = fold<OP>(fold<OP>(a0, a1), fold<OP>(a2, a3));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc = fold<OP>(acc, __shfl_xor_sync(0xffffffffu, acc, off));
     if (lane == 0) wsum[warp] = acc;

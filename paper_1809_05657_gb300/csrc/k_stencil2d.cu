@@ -116,41 +116,6 @@ __global__ void __launch_bounds__(256) k_jacobi2d(const StenPart2D *__restrict__
 // 0 and 31), so no synchronisation beyond cp.async.wait_group is needed; horizontal neighbours
 // still come by shuffle.  Stage layout per warp: NS x (32 chunks + 2 edge slots) x 16 bytes.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cpa16(uint32_t saddr, const void *g)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cpa8(uint32_t saddr, const void *g)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cpa4(uint32_t saddr, const void *g)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Edge element copy: the smallest cp.async is 4 bytes, so a bfloat16 edge travels as the aligned
-// 4-byte pair that contains it.
-template <int DT>
-__device__ __forceinline__ void edge_copy(uint32_t saddr, const typename Elem<DT>::E *g, bool left)
-{
-    if (sizeof(typename Elem<DT>::E) == 8) cpa8(saddr, g);
-    else if (sizeof(typename Elem<DT>::E) == 4) cpa4(saddr, g);
-    else cpa4(saddr, left ? (const void *)(g - 1) : (const void *)g);
-}
-template <int DT>
-__device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, bool left)
-{
-    using A = typename Elem<DT>::A;
-    if (sizeof(typename Elem<DT>::E) == 8) return (A) * reinterpret_cast<const double *>(slot);
-    if (sizeof(typename Elem<DT>::E) == 4) return (A) * reinterpret_cast<const float *>(slot);
-    const uint32_t w = *reinterpret_cast<const uint32_t *>(slot);
-    return (A)__uint_as_float(left ? (w & 0xffff0000u) : (w << 16));
-}
-
 template <int DT, int NS>
 __global__ void __launch_bounds__(256) k_jacobi2d_async(const StenPart2D *__restrict__ parts,
                                                         const StenTile2D *__restrict__ tiles,
@@ -253,25 +218,35 @@ cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D
 // R = (X - Y)^2 in binary64 (a residual field for HDArrayReduce).
 // ------------------------------------------------------------------------------------------
 template <int DT>
-__device__ __forceinline__ double ld64(const void *p, int64_t i)
-{
-    return (double)Elem<DT>::load1(reinterpret_cast<const typename Elem<DT>::E *>(p) + i);
-}
-
-template <int DT>
 __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks)
 {
+    using E = typename Elem<DT>::E;
     const PwTask t = tasks[blockIdx.x];
-    const int nrows = t.row_end - t.row_begin;
-    const int64_t total = (int64_t)nrows * t.n_inner;
-    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
-        const int rr = (int)(i / t.n_inner), c = (int)(i - (int64_t)rr * t.n_inner);
-        const int row = t.row_begin + rr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n = t.n_inner;
+    for (int row = t.row_begin + warp; row < t.row_end; row += nw) {  // a warp per row
         const int o = row / t.n_mid, m = row - o * t.n_mid;
-        const double a = ld64<DT>(t.x, o * t.xs_outer + m * t.xs_mid + c);
-        const double b = ld64<DT>(t.y, o * t.ys_outer + m * t.ys_mid + c);
-        const double d = a - b;
-        t.r[o * t.rs_outer + m * t.rs_mid + c] = d * d;
+        const E *x = reinterpret_cast<const E *>(t.x) + o * t.xs_outer + m * t.xs_mid;
+        const E *y = reinterpret_cast<const E *>(t.y) + o * t.ys_outer + m * t.ys_mid;
+        double *r = t.r + o * t.rs_outer + m * t.rs_mid;
+        int c = lane;
+        for (; c + 96 < n; c += 128) {  // four independent loads in flight per lane
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                a[u] = (double)Elem<DT>::load1(x + c + 32 * u);
+                b[u] = (double)Elem<DT>::load1(y + c + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double d = a[u] - b[u];
+                r[c + 32 * u] = d * d;
+            }
+        }
+        for (; c < n; c += 32) {
+            const double d = (double)Elem<DT>::load1(x + c) - (double)Elem<DT>::load1(y + c);
+            r[c] = d * d;
+        }
     }
 }
 

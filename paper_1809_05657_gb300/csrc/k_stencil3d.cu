@@ -95,10 +95,130 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// CTA variant: one CTA per tile of ny <= 8 consecutive rows (one warp each) of one band, marching
+// z.  Plane z' of rows y0-1 .. y0+ny (the tile's rows and their y neighbours) goes into stage
+// (z' - z0 + 1) % NS of a shared-memory ring by cp.async from every thread, so each input row
+// is fetched once per CTA and NS - 4 planes are in flight ahead of the one being computed.  At step
+// z the CTA reads planes z-1, z, z+1 and refills the stage of plane z-2 (read by nobody since the
+// barrier of this step).  Stage layout: (8 + 2) rows x (32 chunks + 2 edge slots) x 16 bytes.
+// ------------------------------------------------------------------------------------------
+template <int DT, int NS>
+__global__ void __launch_bounds__(256) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
+                                                       const StenTile3D *__restrict__ tiles,
+                                                       const Seg *__restrict__ segs)
+{
+    using EL = Elem<DT>;
+    using E = typename EL::E;
+    using A = typename EL::A;
+    constexpr int VEC = EL::VEC;
+    constexpr int ROWS = 10, SLOTS = 34, STAGE = ROWS * SLOTS;  // in 16-byte slots
+    extern __shared__ uint4 smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const StenTile3D t = tiles[blockIdx.x];
+    const StenPart3D P = parts[t.part];
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(smem);
+
+    receive_segments_cta<E>(segs, t.seg0, t.nseg);
+
+    const int ny = t.ny;
+    const int64_t zs = P.xs0, ys = P.xs1;
+    // row rr (0 .. ny+1) of the staged planes is array row y0 - 1 + rr
+    const E *xbase = reinterpret_cast<const E *>(P.x) + (int64_t)(t.y - 1 - P.xlo1) * ys + (t.xb - P.xlo2);
+    const int nrows = ny + 2;
+    const bool needL = (t.xb >= t.x0) && (t.xb < t.x1);
+    const bool needR = (t.xb + 32 * VEC - 1 >= t.x0) && (t.xb + 32 * VEC - 1 < t.x1);
+
+    auto issue_plane = [&](int zp) {  // every thread copies its share of plane zp
+        const int stage = (zp - t.z0 + 1) % NS;
+        const uint32_t sbase = ring_s + (uint32_t)(stage * STAGE) * 16u;
+        const E *pz = xbase + (int64_t)(zp - P.xlo0) * zs;
+        for (int q = threadIdx.x; q < nrows * 32; q += blockDim.x) {
+            const int rr = q >> 5, ch = q & 31;
+            const int x = t.xb + ch * VEC;
+            if (x < t.x1 + 1 && x + VEC > t.x0 - 1) cpa16(sbase + (uint32_t)(rr * SLOTS + ch) * 16u, pz + rr * ys + ch * VEC);
+        }
+        const int q = threadIdx.x;  // band-end edges of the tile's own rows (1 .. ny)
+        if (q < ny && needL) edge_copy<DT>(sbase + (uint32_t)((q + 1) * SLOTS + 32) * 16u, pz + (q + 1) * ys - 1, true);
+        if (q >= 32 && q < 32 + ny && needR)
+            edge_copy<DT>(sbase + (uint32_t)((q - 32 + 1) * SLOTS + 33) * 16u, pz + (q - 32 + 1) * ys + 32 * VEC, false);
+    };
+
+    // prologue: planes z0-1 .. z0+NS-3
+#pragma unroll 1
+    for (int k = 0; k < NS - 1; k++) {
+        const int zp = t.z0 - 1 + k;
+        if (zp <= t.z1) issue_plane(zp);
+        cpa_commit();
+    }
+    const int x = t.xb + lane * VEC;
+    const bool act = (x < t.x1 + 1) && (x + VEC > t.x0 - 1);
+    const bool full = (x >= t.x0) && (x + VEC <= t.x1);
+    const bool mine = w < ny;
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.y + w - P.ylo1) * P.ys1 + (x - P.ylo2) +
+            (int64_t)(t.z0 - P.ylo0) * P.ys0;
+    for (int z = t.z0; z < t.z1; z++) {
+        cpa_wait<NS - 4>();  // planes up to z + 1 have landed (this thread's copies)
+        __syncthreads();     // ... and every other thread's
+        if (z - 2 + NS <= t.z1) issue_plane(z - 2 + NS);
+        cpa_commit();
+        if (mine) {
+            const uint4 *sm1 = smem + ((z - 1 - t.z0 + 1) % NS) * STAGE;
+            const uint4 *s0 = smem + ((z - t.z0 + 1) % NS) * STAGE;
+            const uint4 *sp1 = smem + ((z + 1 - t.z0 + 1) % NS) * STAGE;
+            const int me = w + 1;  // my row in the staged planes
+            Row<DT> c, ym, yp1, zm, zp;
+            if (act) {
+                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me * SLOTS + lane), c.v);
+                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + (me - 1) * SLOTS + lane), ym.v);
+                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + (me + 1) * SLOTS + lane), yp1.v);
+                EL::unpack(*reinterpret_cast<const typename EL::V *>(sm1 + me * SLOTS + lane), zm.v);
+                EL::unpack(*reinterpret_cast<const typename EL::V *>(sp1 + me * SLOTS + lane), zp.v);
+            }
+            A left = __shfl_up_sync(0xffffffffu, c.v[VEC - 1], 1);
+            A right = __shfl_down_sync(0xffffffffu, c.v[0], 1);
+            if (lane == 0 && needL) left = edge_read<DT>(s0 + me * SLOTS + 32, true);
+            if (lane == 31 && needR) right = edge_read<DT>(s0 + me * SLOTS + 33, false);
+            A out[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; k++) {
+                const A wv = k > 0 ? c.v[k - 1] : left;
+                const A ev = k < VEC - 1 ? c.v[k + 1] : right;
+                A s = wv + ev;
+                s = s + ym.v[k];
+                s = s + yp1.v[k];
+                s = s + zm.v[k];
+                s = s + zp.v[k];
+                out[k] = s / A(6);
+            }
+            if (full) {
+                *reinterpret_cast<typename EL::V *>(yp) = EL::pack(out);
+            } else if (act) {
+#pragma unroll
+                for (int k = 0; k < VEC; k++)
+                    if (x + k >= t.x0 && x + k < t.x1) EL::store1(yp + k, out[k]);
+            }
+        }
+        yp += P.ys0;
+    }
+    cpa_wait<0>();
+}
+
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
-                             int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s)
+                             int ntiles, const Seg *segs, int warps_per_cta, int variant, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (variant == 1) {
+        constexpr int NS = 8;
+        const size_t sm = (size_t)NS * 10 * 34 * 16;
+        switch (dtype) {
+        case DT_F64: k_stencil3d_cta<DT_F64, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
+        case DT_F32: k_stencil3d_cta<DT_F32, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
+        case DT_BF16: k_stencil3d_cta<DT_BF16, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 8;
     const int grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const int block = 32 * warps_per_cta;

@@ -76,14 +76,17 @@ struct StenPart3D {
 struct StenTile3D {
     int32_t part;
     int32_t z0, z1;
-    int32_t y;
+    int32_t y;   // first row
     int32_t x0, x1;
     int32_t xb;
     int32_t seg0, nseg;
-    int32_t pad;
+    int32_t ny;  // rows: 1 for the per-warp variant, up to the CTA's warps for the CTA variant
 };
+// variant 0: one warp per tile (a row), prefetch in registers;
+// variant 1: one CTA per tile (warps_per_cta rows), planes prefetched into shared memory (cp.async).
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
-                             int ntiles, const Seg *segs, int warps_per_cta, cudaStream_t s);
+                             int ntiles, const Seg *segs, int warps_per_cta, int variant,
+                             cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Element-wise residual R = (X - Y)^2 in double over boxes.
@@ -131,5 +134,30 @@ struct GemmPart {
 };
 cudaError_t launch_gemm_f64(const GemmPart *parts, int nparts, int max_rows, int max_cols,
                             double alpha, double beta, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// The same GEMM on binary32 arrays with the tensor cores (bf16x3 split, binary32 accumulation).
+// One CTA per 128 x 256 tile of C; kend = the K extent the tile needs (triangular A: its last row
+// + 1).  *err is set if a bounded wait gave up.
+// ------------------------------------------------------------------------------------------
+struct TcPart {
+    const void *a;
+    const void *b;
+    void *c;
+    int64_t alo0, alo1, as;
+    int64_t blo0, blo1, bs;
+    int64_t clo0, clo1, cs;
+    int32_t i1, j1;  // ends of the device's work box (rows, columns)
+    int32_t lower;
+    int32_t pad;
+};
+struct TcTile {
+    int32_t part;
+    int32_t i0, j0;
+    int32_t kend;
+};
+size_t gemm_tc_smem_bytes();
+cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles, float alpha, float beta,
+                           unsigned *err, cudaStream_t s);
 
 }  // namespace hda

@@ -71,13 +71,15 @@ struct Ctx {
     double *red_partials = nullptr;
     unsigned *red_counter = nullptr;
     double *red_result = nullptr;
+    unsigned *err_word = nullptr;  // set by kernels whose bounded waits gave up
     double *host_result = nullptr;
     int red_blocks = 0;
     // tunables
     int tile_rows = 64;     // 2-D tile height (rows per warp)
     int warps_per_cta = 8;  // 2-D warps per CTA
     int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
-    int tile_z = 64;        // 3-D tile depth (planes per warp)
+    int tile_z = 64;        // 3-D tile depth (planes per tile)
+    int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per 8 rows with a plane ring)
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
     int last_error = 0;
@@ -608,10 +610,44 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     return exact && covered == need;
 }
 
-// Tiles of the fused 3-D kernel for one device: one warp per (z chunk, x band, row y); the
-// receive segments are the parts of the incoming faces on the tile's six strips.
+// A receive segment for box I (at most two dimensions longer than one element) moved from buffer
+// src to buffer dst: the innermost long dimension is the inner run, the next one the outer run.
+void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &I, std::vector<Seg> &out)
+{
+    int dims[3], nd = 0;
+    for (int d = 2; d >= 0; d--)
+        if (I.hi[d] - I.lo[d] > 1) dims[nd++] = d;
+    if (nd == 3) {  // not a face: one segment per outermost index
+        for (int64_t z = I.lo[0]; z < I.hi[0]; z++) {
+            Box J = I;
+            J.lo[0] = z;
+            J.hi[0] = z + 1;
+            box_segments(a, src, dst, J, out);
+        }
+        return;
+    }
+    Seg sg;
+    sg.src = src.ptr + elem_off(src, I.lo) * a->esize;
+    sg.dst = dst.ptr + elem_off(dst, I.lo) * a->esize;
+    sg.n = 1; sg.ss = 1; sg.ds = 1;
+    sg.m = 1; sg.sso = 0; sg.dso = 0;
+    if (nd >= 1) {
+        sg.n = (int32_t)(I.hi[dims[0]] - I.lo[dims[0]]);
+        sg.ss = src.st[dims[0]];
+        sg.ds = dst.st[dims[0]];
+    }
+    if (nd == 2) {
+        sg.m = (int32_t)(I.hi[dims[1]] - I.lo[dims[1]]);
+        sg.sso = src.st[dims[1]];
+        sg.dso = dst.st[dims[1]];
+    }
+    out.push_back(sg);
+}
+
+// Tiles of the fused 3-D kernel for one device: (z chunk, x band, rows_per_tile rows); the
+// receive segments are the parts of the incoming faces on the tile's six face strips.
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
-                     const std::vector<Move> &recv, bool want_segs, Sten3DHost &h)
+                     const std::vector<Move> &recv, bool want_segs, int rows_per_tile, Sten3DHost &h)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart3D P;
@@ -633,40 +669,32 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
     const int64_t xb0 = bx.alloc.lo[2] + align_down(W.lo[2] - bx.alloc.lo[2], VEC);
     for (int64_t zc = W.lo[0]; zc < W.hi[0]; zc += ZC) {
         for (int64_t xb = xb0; xb < W.hi[2]; xb += BAND) {
-            for (int64_t y = W.lo[1]; y < W.hi[1]; y++) {
+            for (int64_t y = W.lo[1]; y < W.hi[1]; y += rows_per_tile) {
                 StenTile3D t;
                 t.part = part_index;
                 t.z0 = (int32_t)zc;
                 t.z1 = (int32_t)std::min<int64_t>(zc + ZC, W.hi[0]);
                 t.y = (int32_t)y;
+                t.ny = (int32_t)std::min<int64_t>(rows_per_tile, W.hi[1] - y);
                 t.x0 = (int32_t)std::max<int64_t>(W.lo[2], xb);
                 t.x1 = (int32_t)std::min<int64_t>(W.hi[2], xb + BAND);
                 t.xb = (int32_t)xb;
                 t.seg0 = (int32_t)h.segs.size();
                 t.nseg = 0;
-                t.pad = 0;
                 if (want_segs && exact) {
+                    const int64_t y1 = y + t.ny;
                     const Box strips[6] = {
-                        make_box(t.z0 - 1, y, t.x0, t.z0, y + 1, t.x1), make_box(t.z1, y, t.x0, t.z1 + 1, y + 1, t.x1),
-                        make_box(t.z0, y - 1, t.x0, t.z1, y, t.x1), make_box(t.z0, y + 1, t.x0, t.z1, y + 2, t.x1),
-                        make_box(t.z0, y, t.x0 - 1, t.z1, y + 1, t.x0), make_box(t.z0, y, t.x1, t.z1, y + 1, t.x1 + 1)};
+                        make_box(t.z0 - 1, y, t.x0, t.z0, y1, t.x1), make_box(t.z1, y, t.x0, t.z1 + 1, y1, t.x1),
+                        make_box(t.z0, y - 1, t.x0, t.z1, y, t.x1), make_box(t.z0, y1, t.x0, t.z1, y1 + 1, t.x1),
+                        make_box(t.z0, y, t.x0 - 1, t.z1, y1, t.x0), make_box(t.z0, y, t.x1, t.z1, y1, t.x1 + 1)};
                     for (const Move &m : recv) {
-                        const DevBuf &src = X->buf[m.src];
                         for (int s = 0; s < 6; s++) {
                             Box I = box_intersect(m.box, strips[s]);
                             if (I.empty()) continue;
-                            Seg sg;
-                            sg.src = src.ptr + elem_off(src, I.lo) * X->esize;
-                            sg.dst = bx.ptr + elem_off(bx, I.lo) * X->esize;
-                            sg.n = (int32_t)(I.hi[2] - I.lo[2]);  // along x (contiguous)
-                            sg.m = (int32_t)(I.hi[0] - I.lo[0]);  // along z
-                            sg.ss = 1;
-                            sg.ds = 1;
-                            sg.sso = src.st[0];
-                            sg.dso = bx.st[0];
+                            const size_t before = h.segs.size();
+                            box_segments(X, X->buf[m.src], bx, I, h.segs);
+                            t.nseg += (int32_t)(h.segs.size() - before);
                             covered += I.volume();
-                            h.segs.push_back(sg);
-                            t.nseg++;
                         }
                     }
                 }
@@ -786,7 +814,8 @@ int compile_plan(Plan &pl)
                 for (const Move &m : sx->moves)
                     if (m.dst == p) recv.push_back(m);
             int t0 = (int)h.tiles.size();
-            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h)) fused = false;
+            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->variant3 == 1 ? 8 : 1, h))
+                fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
         if (!fused) {
@@ -812,7 +841,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = 8;
+                L.n0 = r.second - r.first; L.n1 = 8; L.n2 = g->variant3;
                 pl.launches.push_back(L);
             }
         } else {
@@ -823,7 +852,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = 8;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = 8; L.n2 = g->variant3;
                 pl.launches.push_back(L);
             }
         }
@@ -839,6 +868,8 @@ int compile_plan(Plan &pl)
     std::vector<PwTask> pw;
     std::vector<std::pair<int, int>> pw_groups;
     std::vector<GemmPart> gp;
+    std::vector<TcPart> tp;
+    std::vector<TcTile> tt;
     int max_rows = 0, max_cols = 0;
     for (int p = 0; p < pt.nparts; p++) {
         const Box &W = pt.box[p];
@@ -880,9 +911,27 @@ int compile_plan(Plan &pl)
             q.j0 = (int32_t)W.lo[1]; q.j1 = (int32_t)W.hi[1];
             q.nk = (int32_t)A->n[1];
             q.lower = k.kind == K_TRMM ? 1 : 0;
-            gp.push_back(q);
-            max_rows = std::max<int>(max_rows, q.i1 - q.i0);
-            max_cols = std::max<int>(max_cols, q.j1 - q.j0);
+            if (A->dtype == DT_F32) {  // tensor cores, bf16x3
+                TcPart t;
+                t.a = q.a; t.b = q.b; t.c = q.c;
+                t.alo0 = q.alo0; t.alo1 = q.alo1; t.as = q.as;
+                t.blo0 = q.blo0; t.blo1 = q.blo1; t.bs = q.bs;
+                t.clo0 = q.clo0; t.clo1 = q.clo1; t.cs = q.cs;
+                t.i1 = q.i1; t.j1 = q.j1; t.lower = q.lower; t.pad = 0;
+                const int pi = (int)tp.size();
+                tp.push_back(t);
+                for (int ti = q.i0; ti < q.i1; ti += 128)
+                    for (int tj = q.j0; tj < q.j1; tj += 256) {
+                        TcTile x;
+                        x.part = pi; x.i0 = ti; x.j0 = tj;
+                        x.kend = q.lower ? std::min(q.nk, std::min(ti + 128, q.i1)) : q.nk;
+                        tt.push_back(x);
+                    }
+            } else {
+                gp.push_back(q);
+                max_rows = std::max<int>(max_rows, q.i1 - q.i0);
+                max_cols = std::max<int>(max_cols, q.j1 - q.j0);
+            }
         } else if (k.kind == K_EXCHANGE) {
             continue;
         } else {
@@ -893,6 +942,10 @@ int compile_plan(Plan &pl)
     blobs.push_back({local.data(), local.size() * sizeof(CopyTask)});
     blobs.push_back({pw.data(), pw.size() * sizeof(PwTask)});
     blobs.push_back({gp.data(), gp.size() * sizeof(GemmPart)});
+    // heaviest tiles first: CTAs start in index order, so the long ones do not end up last
+    std::stable_sort(tt.begin(), tt.end(), [](const TcTile &x, const TcTile &y) { return x.kend > y.kend; });
+    blobs.push_back({tp.data(), tp.size() * sizeof(TcPart)});
+    blobs.push_back({tt.data(), tt.size() * sizeof(TcTile)});
     std::vector<const char *> addr;
     int rc = upload(blobs, pl.tables, addr);
     if (rc) return rc;
@@ -931,6 +984,13 @@ int compile_plan(Plan &pl)
             for (size_t i = 0; i < gp.size(); i++) add((int)i, (int)i + 1, gp[i].i1 - gp[i].i0, gp[i].j1 - gp[i].j0);
         else
             add(0, (int)gp.size(), max_rows, max_cols);
+    }
+    if (!tt.empty()) {
+        LaunchRec L; L.kind = L_GEMM_TC;
+        L.p0 = addr[4]; L.p1 = addr[5]; L.p2 = g->err_word; L.n0 = (int64_t)tt.size();
+        L.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
+        L.f1 = pl.scal.size() > 1 ? pl.scal[1] : 0.0;
+        pl.launches.push_back(L);
     }
     pl.copy_host = xfer;
     return HDARRAY_OK;
@@ -1008,7 +1068,7 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
         if (A->n[0] != C->n[0] || A->n[1] != B->n[0] || B->n[1] != C->n[1]) return HDARRAY_ERR_INVAL;
         if (C == A || C == B) return HDARRAY_ERR_INVAL;
         if (A->dtype != B->dtype || A->dtype != C->dtype) return HDARRAY_ERR_INVAL;
-        if (A->dtype != DT_F64) return HDARRAY_ERR_UNSUPPORTED;
+        if (A->dtype == DT_BF16) return HDARRAY_ERR_UNSUPPORTED;  // binary64 (DFMA) or binary32 (bf16x3)
         break;
     }
     }
@@ -1245,6 +1305,8 @@ int check_part_for(const HDArray *a, int part)
     return HDARRAY_OK;
 }
 
+int check_device_error();
+
 // host/device user array (dense, full size) <-> device buffer, one box
 int memcpy_box(const HDArray *a, const DevBuf &b, const Box &bx, void *user, bool to_device)
 {
@@ -1374,6 +1436,24 @@ int read_impl(HDArray *a, void *uA, int part)
             if (rc) return rc;
         }
         CUDA_TRY(cudaStreamSynchronize(g->stream));
+        return check_device_error();
+    }
+    return HDARRAY_OK;
+}
+
+// A kernel whose bounded device-side wait gave up leaves a non-zero error word; report it once.
+int check_device_error()
+{
+    if (g->host_only || !g->err_word) return HDARRAY_OK;
+    unsigned e = 0;
+    if (cudaMemcpyAsync(&e, g->err_word, sizeof(e), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return HDARRAY_ERR_CUDA;
+    }
+    if (e) {
+        cudaMemsetAsync(g->err_word, 0, sizeof(unsigned), g->stream);
+        return HDARRAY_ERR_TIMEOUT;
     }
     return HDARRAY_OK;
 }
@@ -1452,7 +1532,7 @@ int reduce_impl(HDArray *a, double *res, int op, int part)
                              g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     *res = *g->host_result;
-    return HDARRAY_OK;
+    return check_device_error();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1592,6 +1672,7 @@ int init_impl(int ndev, unsigned flags)
             return HDARRAY_ERR_NOMEM;
         }
         g->red_counter = (unsigned *)p;
+        g->err_word = (unsigned *)((char *)p + 64);
         g->red_result = (double *)((char *)p + 128);
         cudaMemset(p, 0, 256);
         if (cudaMallocHost(&g->host_result, sizeof(double)) != cudaSuccess) {
@@ -1604,6 +1685,8 @@ int init_impl(int ndev, unsigned flags)
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
         if (vv && (atoi(vv) == 0 || atoi(vv) == 1)) g->variant = atoi(vv);
+        const char *v3 = getenv("HDARRAY_STENCIL3D_VARIANT");
+        if (v3 && (atoi(v3) == 0 || atoi(v3) == 1)) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
     }
@@ -1629,10 +1712,13 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
     case L_STENCIL3D:
         return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
-                                (const Seg *)L.p2, (int)L.n1, s);
+                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
     case L_SQDIFF: return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, s);
     case L_GEMM64:
         return launch_gemm_f64((const GemmPart *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, L.f0, L.f1, s);
+    case L_GEMM_TC:
+        return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
+                              (unsigned *)L.p2, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -2144,7 +2230,7 @@ int HDArraySync(void)
     if (!g || !g->inited) return HDARRAY_ERR_STATE;
     if (g->host_only) return HDARRAY_OK;
     CUDA_TRY(cudaStreamSynchronize(g->stream));
-    return HDARRAY_OK;
+    return check_device_error();
 }
 
 int HDArrayGetLastError(void)

@@ -66,7 +66,7 @@ struct Part {
 };
 
 // One kernel launch, recorded so that batches can merge it and graphs can replay it.
-enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D };
+enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC };
 struct LaunchRec {
     int kind = 0;
     int dtype = 0;

@@ -100,4 +100,59 @@ __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::
     if (lane == 31 && needR) row.r = EL::load1(xrow + x + EL::VEC);
 }
 
+// Asynchronous global -> shared copies (cp.async) and their group waits.
+__device__ __forceinline__ void cpa16(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa8(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa4(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Edge element copy: the smallest cp.async is 4 bytes, so a bfloat16 edge travels as the aligned
+// 4-byte pair that contains it.
+template <int DT>
+__device__ __forceinline__ void edge_copy(uint32_t saddr, const typename Elem<DT>::E *g, bool left)
+{
+    if (sizeof(typename Elem<DT>::E) == 8) cpa8(saddr, g);
+    else if (sizeof(typename Elem<DT>::E) == 4) cpa4(saddr, g);
+    else cpa4(saddr, left ? (const void *)(g - 1) : (const void *)g);
+}
+template <int DT>
+__device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, bool left)
+{
+    using A = typename Elem<DT>::A;
+    if (sizeof(typename Elem<DT>::E) == 8) return (A) * reinterpret_cast<const double *>(slot);
+    if (sizeof(typename Elem<DT>::E) == 4) return (A) * reinterpret_cast<const float *>(slot);
+    const uint32_t w = *reinterpret_cast<const uint32_t *>(slot);
+    return (A)__uint_as_float(left ? (w & 0xffff0000u) : (w << 16));
+}
+
+
+// Receive segments copied by a whole CTA (then a barrier orders them before the CTA's loads).
+template <typename E>
+__device__ __forceinline__ void receive_segments_cta(const Seg *__restrict__ segs, int seg0, int nseg)
+{
+    for (int s = 0; s < nseg; s++) {
+        const Seg g = segs[seg0 + s];
+        const E *src = reinterpret_cast<const E *>(g.src);
+        E *dst = reinterpret_cast<E *>(g.dst);
+        const int total = g.n * g.m;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int o = i / g.n, k = i - o * g.n;
+            dst[o * g.dso + k * g.ds] = src[o * g.sso + k * g.ss];
+        }
+    }
+    __threadfence_block();
+    __syncthreads();
+}
+
 }  // namespace hda

@@ -516,3 +516,54 @@ def test_full_size_stencil3d_512_37_boxes(gpu_lib):
     want = light_cone3(x, 1, samples, T)
     gotv = np.array([got[s] for s in samples])
     assert np.array_equal(gotv, want)
+
+
+# ---------------------------------------------------------------------------------------------
+# GEMM on binary32 arrays: tensor cores with the bf16x3 split
+# ---------------------------------------------------------------------------------------------
+
+def _bf16x3_bound(A, B, C0, alpha, beta, k):
+    """Componentwise bound for the bf16x3 product in binary32: each operand x = hi + lo + d with
+    |d| <= 2^-16 |x| and |lo| <= 2^-8 |x|, so dropping lo*lo and the two d terms loses at most
+    3 * 2^-16 |a||b| per product; binary32 accumulation of k terms adds (k + 2) * 2^-24."""
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    mag = abs(alpha) * (np.abs(A64) @ np.abs(B64)) + abs(beta) * np.abs(C0.astype(np.float64))
+    return (3 * 2.0 ** -16 + (k + 2) * 2.0 ** -24) * mag + 1e-30
+
+
+@pytest.mark.parametrize("shape,P,lower", [((200, 300, 150), 2, False), ((512, 256, 512), 4, True),
+                                            ((384, 520, 384), 3, True)])
+def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower):
+    ni, nj, nk = shape
+    if lower:
+        a, b = synthetic.tri_gemm_inputs(ni, nj, stream=71, dtype="float")
+    else:
+        a = synthetic.to_storage(synthetic.normal(ni * nk, stream=72).reshape(ni, nk), "float")
+        b = synthetic.to_storage(synthetic.normal(nk * nj, stream=73).reshape(nk, nj), "float")
+    c = synthetic.to_storage(synthetic.normal(ni * nj, stream=74).reshape(ni, nj), "float")
+    alpha, beta = (1.0, 0.0) if lower else (1.25, -0.5)
+    kname = "trmm" if lower else "gemm"
+    scal = (alpha, beta) if lower else (alpha, beta, ni, nj, nk)
+    prog = [("create", "A", "float", (ni, nk)), ("create", "B", "float", (nk, nj)),
+            ("create", "C", "float", (ni, nj)),
+            ("part", "R", ROW, (ni, nj), (0, 0), (ni, nj), P),
+            ("part", "RA", ROW, (ni, nk), (0, 0), (ni, nk), P),
+            ("part", "RB", ROW, (nk, nj), (0, 0), (nk, nj), P)]
+    if lower:
+        rows = [p * ni // P + min(p, ni % P) * 0 for p in range(P + 1)]
+        bx = oracle.partition_boxes(ROW, P, (ni, nj), (0, 0), (ni, nj))
+        for p, (lo, hi) in enumerate(bx):
+            r0, r1 = lo[0], hi[0]
+            prog.append(("trap_use", "trmm", "R", "A", p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1)))
+    prog += [("write", "A", "RA"), ("write", "B", "RB"), ("write", "C", "R"),
+             ("apply", kname, "R", ["A", "B", "C"], scal)]
+    lib, orc, *_ = run_program(prog, P, {"A": a, "B": b, "C": c}, gpu_lib, check_buffers=False)
+    device_buffers_match(lib, orc, ["A", "B"])  # the all-gathered B is bit-exact on every device
+    got = np.zeros((ni, nj), np.float32)
+    H.HDArrayRead(lib.arrays["C"], got, lib.parts["R"])
+    ref = beta * c.astype(np.float64) + alpha * (np.tril(a.astype(np.float64)) if lower else a.astype(np.float64)) @ b.astype(np.float64)
+    bound = _bf16x3_bound(np.tril(a) if lower else a, b, c, alpha, beta, nk)
+    err = np.abs(got.astype(np.float64) - ref)
+    assert (err <= 2 * bound).all(), float((err / bound).max())
+    # the binary64 oracle's own result agrees with numpy to far better than the bound
+    assert np.abs(orc.arrays["C"].G.astype(np.float64) - ref).max() <= 1e-5 * np.abs(ref).max()
