@@ -265,6 +265,25 @@ int HDArrayGetDeviceBuffer(HDArray_t *hA, int dev, void **ptr, int64_t *lo, int6
  * box are HDARRAY_ERR_RANGE.  For inspection and tests.  Synchronous. */
 int HDArrayReadDeviceBuffer(HDArray_t *hA, int dev, const int64_t *lo, const int64_t *hi, void *out);
 
+/* Reduce one strided box of an existing device buffer to one double, allocating nothing.  The paper
+ * has no counterpart: HDArrayReduce allocates its scratch and task table with cudaMalloc, which
+ * some callers cannot use -- code whose device memory belongs to another allocator (a framework's
+ * caching allocator that has reserved the GPU's memory) and latency-critical paths that cannot take
+ * cudaMalloc/cudaFree's implicit synchronisation.  This call keeps its scratch (1024 per-CTA
+ * partials and a completion counter) in a fixed static device array of the library instead.
+ *   x        device pointer to the box's first element; type "double", "float" or "bf16";
+ *   extent   dim (1..3) sizes; strides: dim element strides, the innermost must be 1;
+ *   op       HDARRAY_SUM / PROD / MAX / MIN, folded in double, deterministic;
+ *   result   device pointer to one double that receives the value (caller-owned);
+ *   stream   cudaStream_t to run on (NULL: the default stream); the call is asynchronous.
+ * At most 2^31 elements per call (HDARRAY_ERR_RANGE beyond, nothing launched).  The first call on
+ * each device looks up the static array's address (with that device current); make it before any
+ * stream capture on that device.  Every call shares the static scratch, which keeps the last call's
+ * contents (the counter is cleared at the start of each call): calls that overlap on the GPU race
+ * and must not be issued concurrently.  Does not touch HDArray bookkeeping. */
+int HDArrayReduceBufferNoAlloc(const void *x, const char *type, int dim, const int64_t *extent,
+                               const int64_t *strides, REDUCE_OP op, double *result, void *stream);
+
 /* Counters since HDArrayInit: [0] kernel launches issued by the library, [1] section bytes
  * moved between device buffers, [2] plans computed (cache misses), [3] plan cache hits,
  * [4] graph launches.  n values are written (n <= 5). */

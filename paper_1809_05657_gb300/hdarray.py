@@ -82,6 +82,8 @@ SIGNATURES = {
     "HDArrayGetDeviceBuffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _I64P, _I64P, _I64P]),
     "HDArrayGetCounters": (ctypes.c_int, [_I64P, ctypes.c_int]),
     "HDArrayReadDeviceBuffer": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _I64P, _P]),
+    "HDArrayReduceBufferNoAlloc": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int, _I64P, _I64P,
+                                                  ctypes.c_int, _P, _P]),
 }
 
 
@@ -340,6 +342,14 @@ def HDArrayReadDeviceBuffer(h, dev, lo, hi, out):
     l, lp = _i64(lo)
     u, up = _i64(hi)
     return _chk(lib().HDArrayReadDeviceBuffer(h, dev, lp, up, _ptr(out)), "HDArrayReadDeviceBuffer")
+
+
+def HDArrayReduceBufferNoAlloc(x, dtype, extent, strides, op, result, stream=None):
+    """Allocation-free reduction of a strided device box into the device double `result`."""
+    e, ep = _i64(extent)
+    s, sp = _i64(strides)
+    return _chk(lib().HDArrayReduceBufferNoAlloc(_ptr(x), dtype.encode(), len(extent), ep, sp, op,
+                                                 _ptr(result), stream), "HDArrayReduceBufferNoAlloc")
 
 
 def HDArrayGetCounters():
