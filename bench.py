@@ -388,8 +388,8 @@ def _events(torch, stream, fn, reps):
 
 def workload_stencil3d(H, torch, stream, args):
     import synthetic
-    n, nb, iters = 512, 37, 50
-    boxes = synthetic.kd_boxes(n, nb, stream=3)
+    n, nb, iters = args.n3, args.nb3, 50
+    boxes = synthetic.kd_boxes(n, nb, stream=3) if nb > 1 else [((0, 0, 0), (n, n, n))]
     work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
     x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
     H.HDArrayInit(ndev=nb)
@@ -418,7 +418,7 @@ def workload_stencil3d(H, torch, stream, args):
     algo = cells * 8 + 2 * xbytes
     hbm, src = peaks()
     H.HDArrayExit()
-    return {"workload": "3-D 7-point 512^3 FP32, 37 uneven manual partitions, 50 iterations per step",
+    return {"workload": "3-D 7-point %d^3 FP32, %d uneven manual partitions, 50 iterations per step" % (n, nb),
             "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9,
             "ms_per_step": ms, "us_per_iter": per * 1e3,
             "roofline": {"bound": "hbm", "kernel": "k_stencil3d<f32>", "achieved": algo / (per * 1e-3) / 1e9,
@@ -429,7 +429,7 @@ def workload_stencil3d(H, torch, stream, args):
 def workload_batch(H, torch, stream, args):
     import numpy as np
     import synthetic
-    insts = synthetic.jacobi_instances(512, stream=5)
+    insts = synthetic.jacobi_instances(args.ninst, stream=5)
     iters = 200
     ndev = max(p for _, _, p, _ in insts)
     H.HDArrayInit(ndev=ndev)
@@ -469,8 +469,8 @@ def workload_batch(H, torch, stream, args):
     per = ms / iters
     hbm, src = peaks()
     H.HDArrayExit()
-    return {"workload": "batch of 512 Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL parts, "
-                        "FP32), all instances in one launch per iteration, 200 iterations per step",
+    return {"workload": "batch of %d Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL parts, "
+                        "FP32), all instances in one launch per iteration, 200 iterations per step" % len(insts),
             "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9, "cells": cells,
             "ms_per_step": ms, "us_per_iter": per * 1e3,
             "roofline": {"bound": "hbm", "kernel": "k_jacobi2d<f32> (batched)",
@@ -556,7 +556,7 @@ def trmm_bf16x3(H, torch, stream, args, a64, b64):
     ij = np.stack([rng.integers(0, n, 256), rng.integers(0, m, 256)], 1)
     ij = np.concatenate([ij, [[0, 0], [1, 5], [127, 4095], [128, 1], [8191, 4095], [4095, 2048]]])
     ref = oracle.gemm_entries(np.tril(a.astype(np.float64)), b.astype(np.float64), None, 1.0, 0.0, ij)
-    mag = np.array([np.abs(np.tril(a[i:i + 1].astype(np.float64))[0]) @ np.abs(b[:, j].astype(np.float64))
+    mag = np.array([np.abs(a[i, :i + 1].astype(np.float64)) @ np.abs(b[:i + 1, j].astype(np.float64))
                     for i, j in ij])
     g = got[ij[:, 0], ij[:, 1]].astype(np.float64)
     flops = 2.0 * m * (n * (n + 1) / 2)
@@ -601,6 +601,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=8192,
                     help="grid side (default 8192; smaller only for profiling captures)")
+    ap.add_argument("--n3", type=int, default=512, help="3-D workload: cube side")
+    ap.add_argument("--nb3", type=int, default=37, help="3-D workload: number of boxes (1 = one box)")
+    ap.add_argument("--ninst", type=int, default=512, help="batch workload: number of instances")
     ap.add_argument("--workload", default="jacobi2d",
                     choices=["jacobi2d", "stencil3d", "batch", "trmm"],
                     help="jacobi2d is the benchmark line; the others print their own line")
