@@ -219,6 +219,12 @@ int HDArraySetStream(void *stream);
 /* HDARRAY_MODE_FUSED (default) or HDARRAY_MODE_PLAIN. */
 int HDArraySetMode(int mode);
 
+/* Tile-shape autotuning of the fused stencil launches (also enabled by HDARRAY_AUTOTUNE=1): the
+ * first time a stencil plan of a new (kernel, type, partition shape) is compiled in its fused form,
+ * the candidate tile shapes are timed on the GPU and the fastest is kept (in memory, and appended
+ * to the file named by HDARRAY_TUNE_CACHE if set).  on: 1 or 0. */
+int HDArraySetAutotune(int on);
+
 /* Batching: between Begin and End, HDArrayApplyKernel calls do their bookkeeping immediately
  * but their GPU work is deferred; End launches all of it, fused by kernel type into as few
  * launches as possible.  Calls inside one batch must be independent: an array defined by one

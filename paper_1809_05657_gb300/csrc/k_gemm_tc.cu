@@ -265,4 +265,219 @@ cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles,
     return cudaGetLastError();
 }
 
+
+
+// ==========================================================================================
+// Pre-split operand panels and the pipelined tensor-core GEMM.
+//
+// Panels: the bf16 hi and lo parts of A (per device, its 128-row tiles) and of B^T (256-column
+// tiles), each 128 x 64 (A) or 256 x 64 (B) tile stored contiguously in exactly the K-major
+// 128-byte-swizzled layout the MMA reads, so a K step of a CTA is four contiguous bulk copies.
+// A panel tile (mt, kt) part q sits at ((mt * nkt + kt) * 2 + q) * A_BYTES; a B panel tile
+// (nt, kt) part q at ((nt * nkt + kt) * 2 + q) * B_BYTES.
+// ==========================================================================================
+
+namespace {
+
+// One CTA per (tile, part pair): thread -> 16-byte chunk (row r, 8 consecutive k), both parts.
+__global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict__ jobs)
+{
+    const SplitJob J = jobs[blockIdx.y];
+    const int tiles_per_row = J.nkt;  // k tiles per row tile
+    const int tile = blockIdx.x;      // row tile * nkt + k tile
+    if (tile >= J.ntiles) return;
+    const int mt = tile / tiles_per_row, kt = tile - mt * tiles_per_row;
+    const int rows = J.rows_per_tile;  // 128 (A) or 256 (B)
+    const float *src = reinterpret_cast<const float *>(J.src);
+    uint8_t *hi = reinterpret_cast<uint8_t *>(J.dst) + (size_t)tile * 2 * rows * 128;
+    uint8_t *lo = hi + (size_t)rows * 128;
+    for (int q = threadIdx.x; q < rows * 8; q += blockDim.x) {
+        const int r = J.transpose ? (q & (rows - 1)) : (q >> 3);
+        const int c = J.transpose ? (q / rows) : (q & 7);
+        const int row = J.row0 + mt * rows + r;  // A: row i; B: column n
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int k = kt * 64 + c * 8 + e;
+            float v = 0.0f;
+            if (row < J.row_end && k < J.kend && (!J.lower || k <= row)) {
+                if (J.transpose) v = src[(int64_t)(k - J.lo0) * J.stride + (row - J.lo1)];  // B[k][n]
+                else v = src[(int64_t)(row - J.lo0) * J.stride + (k - J.lo1)];             // A[i][k]
+            }
+            split(v, h[e], l[e]);
+        }
+        uint4 H, L;
+        H.x = h[0] | ((uint32_t)h[1] << 16); H.y = h[2] | ((uint32_t)h[3] << 16);
+        H.z = h[4] | ((uint32_t)h[5] << 16); H.w = h[6] | ((uint32_t)h[7] << 16);
+        L.x = l[0] | ((uint32_t)l[1] << 16); L.y = l[2] | ((uint32_t)l[3] << 16);
+        L.z = l[4] | ((uint32_t)l[5] << 16); L.w = l[6] | ((uint32_t)l[7] << 16);
+        *reinterpret_cast<uint4 *>(hi + sw_off(r, c)) = H;
+        *reinterpret_cast<uint4 *>(lo + sw_off(r, c)) = L;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+constexpr int P_STAGES = 2;
+
+}  // namespace
+
+// Warp-specialised GEMM: warp 0 lane 0 streams panel tiles into a two-stage ring with bulk copies
+// (full barriers carry the byte count), warp 1 lane 0 issues the MMAs and commits each stage back
+// to its empty barrier and the final result to the done barrier, warps 4..7 read the accumulator
+// from tensor memory and write C.  Every wait is bounded.
+__global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *__restrict__ parts,
+                                                               const TcTile *__restrict__ tiles, float alpha,
+                                                               float beta, unsigned *err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], done;
+    __shared__ uint32_t taddr_s;
+    __shared__ int fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const TcTile tile = tiles[blockIdx.x];
+    const PanelPart P = parts[tile.part];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < P_STAGES; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = taddr_s;
+    const int nkt = (tile.kend + BK - 1) / BK;
+    const int mt = (tile.i0 - P.row0) / BM, nt = tile.j0 / BN;
+
+    if (warp == 0 && lane == 0) {  // producer
+        uint32_t ph[P_STAGES] = {0u, 0u};
+        for (int kt = 0; kt < nkt && !fail; kt++) {
+            const int s = kt % P_STAGES;
+            if (kt >= P_STAGES) {
+                if (!mbar_wait(smem_u32(&empty[s]), ph[s])) { fail = 1; break; }
+                ph[s] ^= 1u;
+            }
+            uint8_t *st = smem + s * STAGE_BYTES;
+            const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * 2) * A_BYTES;
+            const uint8_t *bp = reinterpret_cast<const uint8_t *>(P.bpanel) + (size_t)((nt * P.nkt_b + kt) * 2) * B_BYTES;
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_expect(fb, (uint32_t)STAGE_BYTES);
+            bulk_g2s(smem_u32(st), ap, 2 * A_BYTES, fb);                  // A hi, A lo
+            bulk_g2s(smem_u32(st + 2 * A_BYTES), bp, 2 * B_BYTES, fb);    // B hi, B lo
+        }
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        uint32_t ph[P_STAGES] = {0u, 0u};
+        int kt = 0;
+        for (; kt < nkt && !fail; kt++) {
+            const int s = kt % P_STAGES;
+            if (!mbar_wait(smem_u32(&full[s]), ph[s])) { fail = 1; break; }
+            ph[s] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_hi = st, a_lo = st + A_BYTES, b_hi = st + 2 * A_BYTES, b_lo = st + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; kk++) {
+                const uint32_t off = kk * 32;
+                mma_bf16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (kt > 0 || kk > 0) ? 1u : 0u);
+                mma_bf16(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
+                mma_bf16(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        // the done barrier completes when every MMA issued above has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
+    }
+    // everyone: wait for the accumulator (bounded; after a failure the MMAs already issued still
+    // complete before the tensor memory is released)
+    const bool ok = mbar_wait(smem_u32(&done), 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp >= 4 && ok && !fail && nkt > 0) {
+        const int lane_base = 32 * (warp & 3);
+        const int i = tile.i0 + lane_base + lane;
+        float *C = reinterpret_cast<float *>(P.c);
+        for (int cc = 0; cc < BN / 32; cc++) {
+            uint32_t r[32];
+            const uint32_t ta = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(cc * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                  "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                  "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (i < P.i1) {
+                float *crow = C + (int64_t)(i - P.clo0) * P.cs;
+#pragma unroll
+                for (int e = 0; e < 32; e++) {
+                    const int j = tile.j0 + cc * 32 + e;
+                    if (j < P.j1) {
+                        float *cp = crow + (j - P.clo1);
+                        const float acc = __uint_as_float(r[e]);
+                        *cp = beta == 0.0f ? alpha * acc : beta * *cp + alpha * acc;
+                    }
+                }
+            }
+        }
+    }
+    if (tid == 0 && (!ok || fail)) atomicOr(err, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s)
+{
+    if (njobs <= 0 || max_tiles <= 0) return cudaSuccess;
+    dim3 grid(max_tiles, njobs);
+    k_split_panel<<<grid, 256, 0, s>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
+                               float beta, unsigned *err, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    static bool attr = false;
+    const size_t sm = (size_t)P_STAGES * STAGE_BYTES + 1024;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3_panels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_gemm_bf16x3_panels<<<ntiles, 256, sm, s>>>(parts, tiles, alpha, beta, err);
+    return cudaGetLastError();
+}
+
 }  // namespace hda

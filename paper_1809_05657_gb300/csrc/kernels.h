@@ -157,6 +157,33 @@ struct TcTile {
     int32_t kend;
 };
 size_t gemm_tc_smem_bytes();
+
+// Pre-split bf16 hi/lo operand panels (see k_gemm_tc.cu for the layout) and the pipelined GEMM
+// that streams them with bulk copies.
+struct SplitJob {
+    const void *src;   // binary32 buffer
+    void *dst;         // panel
+    int64_t lo0, lo1, stride;  // buffer origin (row, col) and row stride (elements)
+    int32_t row0, row_end;     // A: rows of C's row tiles; B: columns of C's column tiles
+    int32_t kend;              // K extent
+    int32_t nkt, ntiles;       // k tiles per row tile, total tiles
+    int32_t rows_per_tile;     // 128 (A) or 256 (B)
+    int32_t transpose;         // 1 for B (stored as B^T)
+    int32_t lower;             // A lower triangular
+};
+struct PanelPart {
+    const void *apanel;  // this device's A panel
+    const void *bpanel;  // the B panel
+    void *c;
+    int64_t clo0, clo1, cs;
+    int32_t row0;        // first row of the device's row tiles
+    int32_t i1, j1;
+    int32_t nkt, nkt_b;  // k tiles per row tile in the A and B panels
+    int32_t pad;
+};
+cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s);
+cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
+                               float beta, unsigned *err, cudaStream_t s);
 cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles, float alpha, float beta,
                            unsigned *err, cudaStream_t s);
 

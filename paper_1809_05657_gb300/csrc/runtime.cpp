@@ -80,6 +80,12 @@ struct Ctx {
     int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per 8 rows with a plane ring)
+    int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
+    // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
+    bool autotune = false;
+    bool tuning = false;  // compile_plan is being called by the tuner
+    struct Shape { int variant, rows, warps, tile_z, fuse; };
+    std::map<std::string, Shape> tuned;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
     int last_error = 0;
@@ -733,7 +739,7 @@ int compile_plan(Plan &pl)
         const ArrStep *sx = nullptr;
         for (const ArrStep &st : pl.steps)
             if (st.a == X) sx = &st;
-        bool fused = !plain;
+        bool fused = !plain && g->fuse;
         Sten2DHost h;
         h.dtype = X->dtype;
         std::vector<std::pair<int, int>> dev_ranges;
@@ -800,7 +806,7 @@ int compile_plan(Plan &pl)
         const ArrStep *sx = nullptr;
         for (const ArrStep &st : pl.steps)
             if (st.a == X) sx = &st;
-        bool fused = !plain;
+        bool fused = !plain && g->fuse;
         Sten3DHost h;
         h.dtype = X->dtype;
         std::vector<std::pair<int, int>> dev_ranges;
@@ -985,6 +991,97 @@ int compile_plan(Plan &pl)
         else
             add(0, (int)gp.size(), max_rows, max_cols);
     }
+    // Panel path: when every device's column tiles start on 256-column boundaries, split the operands
+    // once into pre-tiled bf16 panels and stream them with bulk copies.  The bookkeeping guarantees
+    // that after this call's exchange every device holds all of B, so one B panel (from the first
+    // device with work) serves all devices.
+    bool panel_ok = !tt.empty();
+    for (const TcPart &t : tp) panel_ok = panel_ok && t.j1 > 0;
+    for (int p = 0; p < pt.nparts && panel_ok; p++)
+        if (!pt.box[p].empty() && pt.box[p].lo[1] % 256 != 0) panel_ok = false;
+    if (panel_ok && getenv("HDARRAY_GEMM_NO_PANELS") == nullptr) {
+        HDArray *A = pl.args[0], *B = pl.args[1];
+        const int64_t nk = A->n[1], nj = B->n[1];
+        std::vector<SplitJob> jobs;
+        std::vector<PanelPart> pp;
+        size_t total = 0;
+        int max_tiles = 0, first = -1;
+        std::vector<size_t> aoff;
+        for (int p = 0; p < pt.nparts; p++) {
+            const Box &W = pt.box[p];
+            if (W.empty()) continue;
+            if (first < 0) first = p;
+            const int64_t kend = (k.kind == K_TRMM) ? std::min<int64_t>(nk, W.hi[0]) : nk;
+            const int nkt = (int)((kend + 63) / 64), nmt = (int)((W.hi[0] - W.lo[0] + 127) / 128);
+            aoff.push_back(total);
+            total += (size_t)nmt * nkt * 2 * (128 * 64 * 2);
+            SplitJob J;
+            const DevBuf &ba = A->buf[p];
+            J.src = ba.ptr; J.dst = nullptr;
+            J.lo0 = ba.alloc.lo[0]; J.lo1 = ba.alloc.lo[1]; J.stride = ba.st[0];
+            J.row0 = (int32_t)W.lo[0]; J.row_end = (int32_t)W.hi[0]; J.kend = (int32_t)kend;
+            J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = 0;
+            J.lower = k.kind == K_TRMM ? 1 : 0;
+            jobs.push_back(J);
+            max_tiles = std::max(max_tiles, J.ntiles);
+            PanelPart q;
+            q.apanel = nullptr; q.bpanel = nullptr;
+            q.c = tp[pp.size()].c;
+            q.clo0 = tp[pp.size()].clo0; q.clo1 = tp[pp.size()].clo1; q.cs = tp[pp.size()].cs;
+            q.row0 = (int32_t)W.lo[0]; q.i1 = (int32_t)W.hi[0]; q.j1 = (int32_t)W.hi[1];
+            q.nkt = nkt; q.nkt_b = (int)((nk + 63) / 64); q.pad = 0;
+            pp.push_back(q);
+        }
+        const int nkt_b = (int)((nk + 63) / 64), nnt = (int)((nj + 255) / 256);
+        const size_t boff = total;
+        total += (size_t)nnt * nkt_b * 2 * (256 * 64 * 2);
+        {
+            SplitJob J;
+            const DevBuf &bb = B->buf[first];
+            J.src = bb.ptr; J.dst = nullptr;
+            J.lo0 = bb.alloc.lo[0]; J.lo1 = bb.alloc.lo[1]; J.stride = bb.st[0];
+            J.row0 = 0; J.row_end = (int32_t)nj; J.kend = (int32_t)nk;
+            J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = 256; J.transpose = 1; J.lower = 0;
+            jobs.push_back(J);
+            max_tiles = std::max(max_tiles, J.ntiles);
+        }
+        auto panels = std::make_shared<DevMem>();
+        if (cudaMalloc(&panels->ptr, total) != cudaSuccess) {
+            cudaGetLastError();
+            return HDARRAY_ERR_NOMEM;
+        }
+        panels->bytes = total;
+        char *base = (char *)panels->ptr;
+        for (size_t i = 0; i + 1 < jobs.size(); i++) jobs[i].dst = base + aoff[i];
+        jobs.back().dst = base + boff;
+        for (size_t i = 0; i < pp.size(); i++) {
+            pp[i].apanel = base + aoff[i];
+            pp[i].bpanel = base + boff;
+        }
+        // tiles index the PanelPart table in the same order as TcPart
+        std::vector<std::pair<const void *, size_t>> pb = {
+            {jobs.data(), (jobs.size() - 1) * sizeof(SplitJob)}, {&jobs.back(), sizeof(SplitJob)},
+            {pp.data(), pp.size() * sizeof(PanelPart)}, {tt.data(), tt.size() * sizeof(TcTile)}};
+        std::shared_ptr<DevMem> ptab;
+        std::vector<const char *> pa;
+        int rc2 = upload(pb, ptab, pa);
+        if (rc2) return rc2;
+        int amax = 0;
+        for (size_t i = 0; i + 1 < jobs.size(); i++) amax = std::max(amax, jobs[i].ntiles);
+        LaunchRec SA; SA.kind = L_SPLIT; SA.p0 = pa[0]; SA.n0 = (int64_t)(jobs.size() - 1); SA.n1 = amax; SA.n3 = 0;
+        LaunchRec SB; SB.kind = L_SPLIT; SB.p0 = pa[1]; SB.n0 = 1; SB.n1 = jobs.back().ntiles; SB.n3 = 1;
+        LaunchRec GM; GM.kind = L_GEMM_PANEL; GM.p0 = pa[2]; GM.p1 = pa[3]; GM.p2 = g->err_word;
+        GM.n0 = (int64_t)tt.size();
+        GM.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
+        GM.f1 = pl.scal.size() > 1 ? pl.scal[1] : 0.0;
+        pl.launches.push_back(SA);
+        pl.launches.push_back(SB);
+        pl.launches.push_back(GM);
+        pl.panels = panels;
+        pl.split_version[0] = pl.split_version[1] = ~0ull;
+        pl.extra_tables = ptab;
+        tt.clear();
+    }
     if (!tt.empty()) {
         LaunchRec L; L.kind = L_GEMM_TC;
         L.p0 = addr[4]; L.p1 = addr[5]; L.p2 = g->err_word; L.n0 = (int64_t)tt.size();
@@ -1016,6 +1113,12 @@ int run_plan(const std::shared_ptr<Plan> &pl)
 {
     if (g->host_only) return HDARRAY_OK;
     for (const LaunchRec &L : pl->launches) {
+        if (L.kind == L_SPLIT) {  // panels of an operand whose content has not changed are reused
+            const int which = (int)L.n3;
+            const uint64_t v = pl->args[which]->version;
+            if (!g->recording && pl->split_version[which] == v) continue;
+            pl->split_version[which] = v;
+        }
         int rc = issue_recorded(L);
         if (rc) return rc;
     }
@@ -1024,6 +1127,148 @@ int run_plan(const std::shared_ptr<Plan> &pl)
 }
 
 int flush_batch();
+
+// ------------------------------------------------------------------------------------------
+// Autotuner: tile shapes of the fused stencil launches
+// ------------------------------------------------------------------------------------------
+
+std::string tune_key(const Plan &pl)
+{
+    const Part &pt = g->parts[pl.part];
+    std::string k = pl.k->name + ":" + std::to_string(pl.args[0]->dtype) + ":" + std::to_string(pt.nparts);
+    for (const Box &b : pt.box) {
+        char buf[96];
+        snprintf(buf, sizeof(buf), ":%lld,%lld,%lld", (long long)(b.hi[0] - b.lo[0]), (long long)(b.hi[1] - b.lo[1]),
+                 (long long)(b.hi[2] - b.lo[2]));
+        k += buf;
+    }
+    return k;
+}
+
+void apply_shape(const Ctx::Shape &s, bool threed)
+{
+    g->fuse = s.fuse;
+    if (threed) {
+        g->tile_z = s.tile_z;
+    } else {
+        g->variant = s.variant;
+        g->tile_rows = s.rows;
+        g->warps_per_cta = s.warps;
+    }
+}
+
+Ctx::Shape current_shape() { return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse}; }
+
+const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
+
+void load_tune_file()
+{
+    static bool loaded = false;
+    if (loaded || !tune_file()) return;
+    loaded = true;
+    FILE *f = fopen(tune_file(), "r");
+    if (!f) return;
+    char key[4096];
+    Ctx::Shape s;
+    while (fscanf(f, "%4095s %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse) == 6)
+        g->tuned[key] = s;
+    fclose(f);
+}
+
+void save_tune(const std::string &key, const Ctx::Shape &s)
+{
+    if (!tune_file()) return;
+    FILE *f = fopen(tune_file(), "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse);
+    fclose(f);
+}
+
+float time_plan(const Plan &pl, int reps)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return 1e30f;
+    }
+    float best = 1e30f;
+    for (int r = 0; r < reps + 1; r++) {
+        cudaEventRecord(a, g->stream);
+        for (const LaunchRec &L : pl.launches)
+            if (issue(L, g->stream) != cudaSuccess) {
+                cudaGetLastError();
+                best = 1e30f;
+                r = reps + 1;
+                break;
+            }
+        cudaEventRecord(b, g->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r > 0 && ms < best) best = ms;  // the first run warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+int compile_plan(Plan &pl);
+
+// Compile a fused stencil plan with the best tile shape for its partition, timing the candidates
+// on the GPU the first time a shape key is seen.  Re-running the launch is harmless: it recomputes
+// Y from an unchanged X and copies the same halo values again.
+int compile_tuned(Plan &pl)
+{
+    const bool stencil = pl.k->kind == K_JACOBI2D || pl.k->kind == K_STENCIL3D;
+    if (!stencil || !g->autotune || g->recording || g->batching || g->tuning) return compile_plan(pl);
+    const bool threed = pl.k->kind == K_STENCIL3D;
+    load_tune_file();
+    const std::string key = tune_key(pl);
+    const Ctx::Shape saved = current_shape();
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) {
+        apply_shape(it->second, threed);
+        int rc = compile_plan(pl);
+        apply_shape(saved, threed);
+        return rc;
+    }
+    g->fuse = 1;  // probe: does this plan's exchange fit the tiles (its steady form)?
+    int rc = compile_plan(pl);
+    g->fuse = saved.fuse;
+    if (rc || !pl.fused) return rc ? rc : compile_plan(pl);  // tune on the steady form only
+    std::vector<Ctx::Shape> cands;
+    if (threed) {
+        for (int fu : {1, 0})
+            for (int tz : {16, 32, 64, 128}) cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu});
+    } else {
+        for (int fu : {1, 0})
+            for (int v : {0, 1})
+                for (int rows : {16, 32, 64})
+                    for (int w : {4, 8}) cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu});
+    }
+    g->tuning = true;
+    Ctx::Shape best = saved;
+    float best_ms = 1e30f;
+    for (const Ctx::Shape &c : cands) {
+        apply_shape(c, threed);
+        if (compile_plan(pl) != HDARRAY_OK) continue;
+        const float ms = time_plan(pl, 3);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    g->tuning = false;
+    apply_shape(best, threed);
+    rc = compile_plan(pl);
+    apply_shape(saved, threed);
+    g->tuned[key] = best;
+    save_tune(key, best);
+    if (trace())
+        fprintf(stderr, "hdarray: tuned %s -> variant %d rows %d warps %d tile_z %d fuse %d (%.1f us)\n",
+                key.c_str(), best.variant, best.rows, best.warps, best.tile_z, best.fuse, best_ms * 1e3);
+    return rc;
+}
 
 // ------------------------------------------------------------------------------------------
 // Applying a kernel
@@ -1185,7 +1430,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
         // a plan may be shared by signatures whose buffers moved: recompile when they did
         const std::string sig = epoch_sig(*pl);
         if (pl->compiled_sig != sig) {
-            rc = compile_plan(*pl);
+            rc = compile_tuned(*pl);
             if (rc) return rc;
             pl->compiled_sig = sig;
         }
@@ -1194,6 +1439,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
     for (ArrStep &st : pl->steps) {
         if (g->recording && !g->rec_pre.count(st.a)) g->rec_pre[st.a] = {st.a->cur, st.a->generation};
         st.a->cur = st.post;
+        if (st.defined) st.a->version++;
         if (st.used) st.a->last_moves = st.moves;
         for (const Move &m : st.moves) g->counters[1] += m.box.volume() * st.a->esize;
     }
@@ -1412,6 +1658,7 @@ int write_impl(HDArray *a, const void *uA, int part)
         }
     }
     a->cur = intern(a, std::move(s));
+    a->version++;
     return HDARRAY_OK;
 }
 
@@ -1685,6 +1932,10 @@ int init_impl(int ndev, unsigned flags)
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
         if (vv && (atoi(vv) == 0 || atoi(vv) == 1)) g->variant = atoi(vv);
+        const char *at = getenv("HDARRAY_AUTOTUNE");
+        g->autotune = at && atoi(at) != 0;
+        const char *fx = getenv("HDARRAY_FUSE_EXCHANGE");
+        if (fx) g->fuse = atoi(fx) != 0;
         const char *v3 = getenv("HDARRAY_STENCIL3D_VARIANT");
         if (v3 && (atoi(v3) == 0 || atoi(v3) == 1)) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
@@ -1719,6 +1970,10 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_GEMM_TC:
         return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
                               (unsigned *)L.p2, s);
+    case L_SPLIT: return launch_split_panels((const SplitJob *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_GEMM_PANEL:
+        return launch_gemm_panels((const PanelPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0,
+                                  (float)L.f1, (unsigned *)L.p2, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -2121,6 +2376,13 @@ int HDArraySetMode(int mode)
         for (auto &kv : g->memo) kv.second->compiled_sig.clear();
         g->batch_cache.clear();
     }
+    return HDARRAY_OK;
+}
+
+int HDArraySetAutotune(int on)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    g->autotune = on != 0;
     return HDARRAY_OK;
 }
 

@@ -66,7 +66,7 @@ struct Part {
 };
 
 // One kernel launch, recorded so that batches can merge it and graphs can replay it.
-enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC };
+enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL };
 struct LaunchRec {
     int kind = 0;
     int dtype = 0;
@@ -126,6 +126,9 @@ struct Plan {
     std::vector<CopyTask> copy_host;  // exchange tasks (batch merging)
     Sten2DHost s2;                    // stencil tables (batch merging)
     Sten3DHost s3;
+    std::shared_ptr<DevMem> panels;   // pre-split bf16 operand panels (tensor-core GEMM)
+    std::shared_ptr<DevMem> extra_tables;  // descriptor tables of the panel launches
+    uint64_t split_version[2] = {~0ull, ~0ull};  // content versions of A and B the panels hold
 };
 
 }  // namespace hda
@@ -142,6 +145,7 @@ struct HDArray {
     int cur = 0;
     uint64_t generation = 1;  // bumps when the state table is reset
     uint64_t epoch = 1;       // bumps when any device buffer moves
+    uint64_t version = 0;     // bumps whenever any element is (re)defined
     uint64_t uid = 0;
     std::vector<hda::Move> last_moves;
 };

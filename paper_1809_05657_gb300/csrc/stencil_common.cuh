@@ -61,21 +61,43 @@ struct Elem<DT_BF16> {
     __device__ static void store1(E *p, A a) { *p = __float2bfloat16_rn(a); }
 };
 
-// Copy a tile's receive segments (sender buffer -> own buffer), then order those stores before
-// the warp's loads of its own buffer.
+// Copy elements [first, total) step `stride` of a tile's receive segments (sender buffer -> own
+// buffer), all segments flattened into one index space and four element copies in flight per
+// thread, so a tile with several small faces pays about one memory round trip, not one per face.
+template <typename E>
+__device__ __forceinline__ void receive_flat(const Seg *__restrict__ segs, int seg0, int nseg, int first, int stride)
+{
+    int total = 0;
+    for (int s = 0; s < nseg; s++) total += segs[seg0 + s].n * segs[seg0 + s].m;
+    for (int base = first; base < total; base += 4 * stride) {
+        E v[4];
+        E *dst[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            dst[u] = nullptr;
+            int i = base + u * stride;
+            if (i >= total) continue;
+            int s = seg0;
+            while (i >= segs[s].n * segs[s].m) {
+                i -= segs[s].n * segs[s].m;
+                s++;
+            }
+            const Seg &g = segs[s];
+            const int o = i / g.n, k = i - o * g.n;
+            v[u] = reinterpret_cast<const E *>(g.src)[o * g.sso + k * g.ss];
+            dst[u] = reinterpret_cast<E *>(g.dst) + o * g.dso + k * g.ds;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (dst[u]) *dst[u] = v[u];
+    }
+}
+
+// The warp's receive phase, then __syncwarp orders the copies before the warp's loads.
 template <typename E>
 __device__ __forceinline__ void receive_segments(const Seg *__restrict__ segs, int seg0, int nseg, int lane)
 {
-    for (int s = 0; s < nseg; s++) {
-        const Seg g = segs[seg0 + s];
-        const E *src = reinterpret_cast<const E *>(g.src);
-        E *dst = reinterpret_cast<E *>(g.dst);
-        const int total = g.n * g.m;
-        for (int i = lane; i < total; i += 32) {
-            const int o = i / g.n, k = i - o * g.n;
-            dst[o * g.dso + k * g.ds] = src[o * g.sso + k * g.ss];
-        }
-    }
+    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, lane, 32);
     __syncwarp();
 }
 
@@ -141,16 +163,7 @@ __device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, boo
 template <typename E>
 __device__ __forceinline__ void receive_segments_cta(const Seg *__restrict__ segs, int seg0, int nseg)
 {
-    for (int s = 0; s < nseg; s++) {
-        const Seg g = segs[seg0 + s];
-        const E *src = reinterpret_cast<const E *>(g.src);
-        E *dst = reinterpret_cast<E *>(g.dst);
-        const int total = g.n * g.m;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            const int o = i / g.n, k = i - o * g.n;
-            dst[o * g.dso + k * g.ds] = src[o * g.sso + k * g.ss];
-        }
-    }
+    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
     __threadfence_block();
     __syncthreads();
 }

@@ -68,6 +68,7 @@ SIGNATURES = {
     "HDArrayNumDevices": (ctypes.c_int, []),
     "HDArraySetStream": (ctypes.c_int, [_P]),
     "HDArraySetMode": (ctypes.c_int, [ctypes.c_int]),
+    "HDArraySetAutotune": (ctypes.c_int, [ctypes.c_int]),
     "HDArrayBatchBegin": (ctypes.c_int, []),
     "HDArrayBatchEnd": (ctypes.c_int, []),
     "HDArrayGraphBegin": (ctypes.c_int, []),
@@ -269,6 +270,10 @@ def HDArraySetStream(stream=None):
 
 def HDArraySetMode(mode):
     return _chk(lib().HDArraySetMode(mode), "HDArraySetMode")
+
+
+def HDArraySetAutotune(on=True):
+    return _chk(lib().HDArraySetAutotune(1 if on else 0), "HDArraySetAutotune")
 
 
 def HDArrayBatchBegin():

@@ -531,9 +531,12 @@ def _bf16x3_bound(A, B, C0, alpha, beta, k):
     return (3 * 2.0 ** -16 + (k + 2) * 2.0 ** -24) * mag + 1e-30
 
 
+@pytest.mark.parametrize("panels", [True, False])
 @pytest.mark.parametrize("shape,P,lower", [((200, 300, 150), 2, False), ((512, 256, 512), 4, True),
                                             ((384, 520, 384), 3, True)])
-def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower):
+def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower, panels, monkeypatch):
+    if not panels:  # the fallback kernel that splits while loading
+        monkeypatch.setenv("HDARRAY_GEMM_NO_PANELS", "1")
     ni, nj, nk = shape
     if lower:
         a, b = synthetic.tri_gemm_inputs(ni, nj, stream=71, dtype="float")
@@ -550,7 +553,6 @@ def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower):
             ("part", "RA", ROW, (ni, nk), (0, 0), (ni, nk), P),
             ("part", "RB", ROW, (nk, nj), (0, 0), (nk, nj), P)]
     if lower:
-        rows = [p * ni // P + min(p, ni % P) * 0 for p in range(P + 1)]
         bx = oracle.partition_boxes(ROW, P, (ni, nj), (0, 0), (ni, nj))
         for p, (lo, hi) in enumerate(bx):
             r0, r1 = lo[0], hi[0]
@@ -567,3 +569,60 @@ def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower):
     assert (err <= 2 * bound).all(), float((err / bound).max())
     # the binary64 oracle's own result agrees with numpy to far better than the bound
     assert np.abs(orc.arrays["C"].G.astype(np.float64) - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_gemm_bf16x3_reuses_panels(gpu_lib):
+    """A second call with unchanged A and B reuses the split panels; changing B re-splits it."""
+    ni = nj = nk = 256
+    a = synthetic.to_storage(synthetic.normal(ni * nk, stream=75).reshape(ni, nk), "float")
+    b = synthetic.to_storage(synthetic.normal(nk * nj, stream=76).reshape(nk, nj), "float")
+    b2 = synthetic.to_storage(synthetic.normal(nk * nj, stream=77).reshape(nk, nj), "float")
+    gpu_lib(2)
+    A = H.HDArrayCreate("A", "float", None, ni, nk)
+    B = H.HDArrayCreate("B", "float", None, nk, nj)
+    C = H.HDArrayCreate("C", "float", None, ni, nj)
+    R = H.HDArrayPartition(ROW, (ni, nj), (0, 0), (ni, nj), 2)
+    H.HDArrayWrite(A, a, R)
+    H.HDArrayWrite(B, b, R)
+    out = []
+    for bb in (None, None, b2):
+        if bb is not None:
+            H.HDArrayWrite(B, bb, R)
+        H.HDArrayApplyKernel("gemm", R, A, B, C, 1.0, 0.0, ni, nj, nk)
+        got = np.zeros((ni, nj), np.float32)
+        H.HDArrayRead(C, got, R)
+        out.append(got)
+    for got, bb in zip(out, (b, b, b2)):
+        ref = a.astype(np.float64) @ bb.astype(np.float64)
+        assert (np.abs(got - ref) <= 2 * _bf16x3_bound(a, bb, 0 * got, 1.0, 0.0, nk)).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# execution choices must not change results: unfused exchange, autotuned tile shapes, variants
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("env", [{"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
+                                 {"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16"}])
+def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    dims, P = (260, 530), 6
+    x = synthetic.jacobi_field(dims, stream=81, dtype="float")
+    prog, last = jacobi_prog(dims, P, 7, BLOCK, "float", True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+
+
+@pytest.mark.parametrize("env", [{"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
+                                 {"HDARRAY_STENCIL3D_VARIANT": "0"}, {"HDARRAY_TILE_Z": "7"}])
+def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    n = 36
+    boxes = synthetic.kd_boxes(n, 7, stream=82, min_ext=6, max_ext=36)
+    x = synthetic.jacobi_field((n, n, n), stream=83, dtype="float")
+    prog, last = stencil3d_prog(n, boxes, 5, "float")
+    lib, orc, *_ = run_program(prog, len(boxes), {"B": x}, gpu_lib)
+    got = np.zeros((n, n, n), np.float32)
+    H.HDArrayRead(lib.arrays[last], got, lib.parts["D"])
+    assert np.array_equal(got, orc.arrays[last].G)
