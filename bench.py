@@ -134,6 +134,32 @@ def setup_jacobi(H, x, dtype, pingpong=True):
     return B, A, R, D, W
 
 
+def tune_setup(args):
+    """Autotuning of the stencil tile shapes (the library times candidates on first use); the
+    choices are appended to a per-run file whose lines are reported in the JSON."""
+    if args.no_autotune:
+        return None
+    path = os.path.join("/tmp", "hdarray_tune_%d.txt" % os.getpid())
+    if os.path.exists(path):
+        os.remove(path)
+    os.environ["HDARRAY_AUTOTUNE"] = "1"
+    os.environ["HDARRAY_TUNE_CACHE"] = path
+    return path
+
+
+def tune_report(path):
+    if not path or not os.path.exists(path):
+        return None
+    out = []
+    for line in open(path):
+        w = line.split()
+        if len(w) == 7:
+            key = w[0].split(":")
+            out.append({"kernel": key[0], "variant": int(w[1]), "rows": int(w[2]), "warps": int(w[3]),
+                        "tile_z": int(w[4]), "fused_exchange": int(w[5]), "variant3": int(w[6])})
+    return out
+
+
 def gpu_arm(args, rank, world):
     import numpy as np
     import torch
@@ -221,7 +247,7 @@ def gpu_arm(args, rank, world):
     extra = {}
     if rank == 0 and not args.quick:
         extra = extra_forms(H, torch, stream, args)
-    return dict(ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
+    return dict(tuned=None, ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
                 algo_bytes=algo_bytes, xbytes=xbytes, achieved=achieved, hbm=hbm, src=src,
                 clocks=clk.summary(), residual=res, extra=extra, e2e=e2e)
 
@@ -584,7 +610,9 @@ def run_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm}[args.workload]
+    tpath = tune_setup(args)
     out = fn(H, torch, stream, args)
+    out["autotuned"] = tune_report(tpath)
     out["steps"] = args.steps
     out["warmup"] = args.warmup
     print(json.dumps(out))
@@ -599,6 +627,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the comparison forms and e2e")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default tile shapes")
     ap.add_argument("--grid", type=int, default=8192,
                     help="grid side (default 8192; smaller only for profiling captures)")
     ap.add_argument("--n3", type=int, default=512, help="3-D workload: cube side")
@@ -623,7 +652,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    tpath = tune_setup(args)
     r = gpu_arm(args, rank, world)
+    r["tuned"] = tune_report(tpath)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -648,6 +679,7 @@ def main():
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "residual": r["residual"],
+            "autotuned": r["tuned"],
             "forms": r["extra"],
         }
         print(json.dumps(line))

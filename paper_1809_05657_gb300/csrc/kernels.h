@@ -88,6 +88,17 @@ cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3
                              int ntiles, const Seg *segs, int warps_per_cta, int variant,
                              cudaStream_t s);
 
+// Flat-block forms (binary32 / binary64): one CTA per block of a work box, the block and its halo
+// staged in shared memory, threads walking the block's cells in row-major order.  2-D tiles use
+// r0, r1, c0, c1 (cb unused); 3-D tiles use z0, z1, y, ny, x0, x1 (xb unused).
+constexpr int FLAT3D_STAGES = 6;
+size_t flat2d_smem(int dtype, int rows, int cols);
+size_t flat3d_smem(int dtype, int ny, int nx);
+cudaError_t launch_jacobi2d_flat(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                 const Seg *segs, size_t smem, cudaStream_t s);
+cudaError_t launch_stencil3d_flat(int dtype, const StenPart3D *parts, const StenTile3D *tiles, int ntiles,
+                                  const Seg *segs, size_t smem, cudaStream_t s);
+
 // ------------------------------------------------------------------------------------------
 // Element-wise residual R = (X - Y)^2 in double over boxes.
 // ------------------------------------------------------------------------------------------

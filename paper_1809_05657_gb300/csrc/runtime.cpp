@@ -84,7 +84,7 @@ struct Ctx {
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
     bool tuning = false;  // compile_plan is being called by the tuner
-    struct Shape { int variant, rows, warps, tile_z, fuse; };
+    struct Shape { int variant, rows, warps, tile_z, fuse, variant3; };
     std::map<std::string, Shape> tuned;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
@@ -616,6 +616,61 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     return exact && covered == need;
 }
 
+void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &I, std::vector<Seg> &out);
+
+// Flat-block tiles of one device's work box (2-D): blocks up to 256 columns wide and about
+// `cells` cells; the receive segments are the incoming cells on each block's four face strips.
+bool flat2d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
+                  const std::vector<Move> &recv, bool want_segs, int cells, Sten2DHost &h)
+{
+    const DevBuf &bx = X->buf[p], &by = Y->buf[p];
+    StenPart2D P;
+    P.x = bx.ptr; P.y = by.ptr;
+    P.xlo0 = bx.alloc.lo[0]; P.xlo1 = bx.alloc.lo[1]; P.xs = bx.st[0];
+    P.ylo0 = by.alloc.lo[0]; P.ylo1 = by.alloc.lo[1]; P.ys = by.st[0];
+    h.parts.push_back(P);
+    bool exact = true;
+    int64_t covered = 0, need = 0;
+    for (const Move &m : recv) {
+        need += m.box.volume();
+        if (box_overlaps(m.box, W)) exact = false;
+    }
+    const int64_t width = W.hi[1] - W.lo[1];
+    const int64_t nbx = (width + 255) / 256;
+    const int64_t bw = (width + nbx - 1) / nbx;  // balanced block widths
+    const int64_t br = std::max<int64_t>(1, std::min<int64_t>(W.hi[0] - W.lo[0], cells / std::max<int64_t>(1, bw)));
+    for (int64_t r = W.lo[0]; r < W.hi[0]; r += br) {
+        for (int64_t c = W.lo[1]; c < W.hi[1]; c += bw) {
+            StenTile2D t;
+            t.part = part_index;
+            t.r0 = (int32_t)r;
+            t.r1 = (int32_t)std::min<int64_t>(r + br, W.hi[0]);
+            t.c0 = (int32_t)c;
+            t.c1 = (int32_t)std::min<int64_t>(c + bw, W.hi[1]);
+            t.cb = t.c0;
+            t.seg0 = (int32_t)h.segs.size();
+            t.nseg = 0;
+            if (want_segs && exact) {
+                const Box strips[4] = {
+                    make_box(t.r0 - 1, t.c0, 0, t.r0, t.c1, 1), make_box(t.r1, t.c0, 0, t.r1 + 1, t.c1, 1),
+                    make_box(t.r0, t.c0 - 1, 0, t.r1, t.c0, 1), make_box(t.r0, t.c1, 0, t.r1, t.c1 + 1, 1)};
+                for (const Move &m : recv)
+                    for (int s = 0; s < 4; s++) {
+                        Box I = box_intersect(m.box, strips[s]);
+                        if (I.empty()) continue;
+                        const size_t before = h.segs.size();
+                        box_segments(X, X->buf[m.src], bx, I, h.segs);
+                        t.nseg += (int32_t)(h.segs.size() - before);
+                        covered += I.volume();
+                    }
+            }
+            h.smem = std::max(h.smem, flat2d_smem(X->dtype, t.r1 - t.r0, t.c1 - t.c0));
+            h.tiles.push_back(t);
+        }
+    }
+    return exact && covered == need;
+}
+
 // A receive segment for box I (at most two dimensions longer than one element) moved from buffer
 // src to buffer dst: the innermost long dimension is the inner run, the next one the outer run.
 void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &I, std::vector<Seg> &out)
@@ -653,7 +708,8 @@ void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const 
 // Tiles of the fused 3-D kernel for one device: (z chunk, x band, rows_per_tile rows); the
 // receive segments are the parts of the incoming faces on the tile's six face strips.
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
-                     const std::vector<Move> &recv, bool want_segs, int rows_per_tile, Sten3DHost &h)
+                     const std::vector<Move> &recv, bool want_segs, int rows_per_tile, Sten3DHost &h,
+                     int flat_cells = 0)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart3D P;
@@ -672,9 +728,17 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
         need += m.box.volume();
         if (box_overlaps(m.box, W)) exact = false;
     }
-    const int64_t xb0 = bx.alloc.lo[2] + align_down(W.lo[2] - bx.alloc.lo[2], VEC);
+    int64_t xb0 = bx.alloc.lo[2] + align_down(W.lo[2] - bx.alloc.lo[2], VEC);
+    int64_t band = BAND;
+    if (flat_cells > 0) {  // flat blocks: balanced widths up to 128, rows so that a plane has ~flat_cells
+        const int64_t width = W.hi[2] - W.lo[2];
+        const int64_t nbx = (width + 127) / 128;
+        band = (width + nbx - 1) / nbx;
+        xb0 = W.lo[2];
+        rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(W.hi[1] - W.lo[1], flat_cells / band));
+    }
     for (int64_t zc = W.lo[0]; zc < W.hi[0]; zc += ZC) {
-        for (int64_t xb = xb0; xb < W.hi[2]; xb += BAND) {
+        for (int64_t xb = xb0; xb < W.hi[2]; xb += band) {
             for (int64_t y = W.lo[1]; y < W.hi[1]; y += rows_per_tile) {
                 StenTile3D t;
                 t.part = part_index;
@@ -683,7 +747,7 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
                 t.y = (int32_t)y;
                 t.ny = (int32_t)std::min<int64_t>(rows_per_tile, W.hi[1] - y);
                 t.x0 = (int32_t)std::max<int64_t>(W.lo[2], xb);
-                t.x1 = (int32_t)std::min<int64_t>(W.hi[2], xb + BAND);
+                t.x1 = (int32_t)std::min<int64_t>(W.hi[2], xb + band);
                 t.xb = (int32_t)xb;
                 t.seg0 = (int32_t)h.segs.size();
                 t.nseg = 0;
@@ -704,6 +768,7 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
                         }
                     }
                 }
+                if (flat_cells > 0) h.smem = std::max(h.smem, flat3d_smem(X->dtype, t.ny, t.x1 - t.x0));
                 h.tiles.push_back(t);
             }
         }
@@ -753,7 +818,10 @@ int compile_plan(Plan &pl)
                 for (const Move &m : sx->moves)
                     if (m.dst == p) recv.push_back(m);
             int t0 = (int)h.tiles.size();
-            bool ok = jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h);
+            const bool flat = g->variant == 2 && X->dtype != DT_BF16;
+            h.flat = flat;
+            bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
+                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h);
             if (!ok) fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -778,9 +846,9 @@ int compile_plan(Plan &pl)
                 }
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
-                LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = g->warps_per_cta; L.n2 = g->variant;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->warps_per_cta; L.n2 = g->variant;
                 pl.launches.push_back(L);
             }
         } else {
@@ -789,9 +857,9 @@ int compile_plan(Plan &pl)
                 pl.launches.push_back(L);
             }
             if (!h.tiles.empty()) {
-                LaunchRec L; L.kind = L_JACOBI2D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = g->warps_per_cta; L.n2 = g->variant;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->warps_per_cta; L.n2 = g->variant;
                 pl.launches.push_back(L);
             }
         }
@@ -820,7 +888,10 @@ int compile_plan(Plan &pl)
                 for (const Move &m : sx->moves)
                     if (m.dst == p) recv.push_back(m);
             int t0 = (int)h.tiles.size();
-            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->variant3 == 1 ? 8 : 1, h))
+            const bool flat = g->variant3 == 2 && X->dtype != DT_BF16;
+            h.flat = flat;
+            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->variant3 == 1 ? 8 : 1, h,
+                                 flat ? g->tile_rows * 64 : 0))
                 fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -845,9 +916,9 @@ int compile_plan(Plan &pl)
                 }
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
-                LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = 8; L.n2 = g->variant3;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3;
                 pl.launches.push_back(L);
             }
         } else {
@@ -856,9 +927,9 @@ int compile_plan(Plan &pl)
                 pl.launches.push_back(L);
             }
             if (!h.tiles.empty()) {
-                LaunchRec L; L.kind = L_STENCIL3D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = 8; L.n2 = g->variant3;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3;
                 pl.launches.push_back(L);
             }
         }
@@ -1150,6 +1221,8 @@ void apply_shape(const Ctx::Shape &s, bool threed)
     g->fuse = s.fuse;
     if (threed) {
         g->tile_z = s.tile_z;
+        g->variant3 = s.variant3;
+        g->tile_rows = s.rows;
     } else {
         g->variant = s.variant;
         g->tile_rows = s.rows;
@@ -1157,7 +1230,10 @@ void apply_shape(const Ctx::Shape &s, bool threed)
     }
 }
 
-Ctx::Shape current_shape() { return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse}; }
+Ctx::Shape current_shape()
+{
+    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3};
+}
 
 const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
 
@@ -1170,7 +1246,8 @@ void load_tune_file()
     if (!f) return;
     char key[4096];
     Ctx::Shape s;
-    while (fscanf(f, "%4095s %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse) == 6)
+    while (fscanf(f, "%4095s %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
+                  &s.variant3) == 7)
         g->tuned[key] = s;
     fclose(f);
 }
@@ -1180,7 +1257,7 @@ void save_tune(const std::string &key, const Ctx::Shape &s)
     if (!tune_file()) return;
     FILE *f = fopen(tune_file(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse);
+    fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3);
     fclose(f);
 }
 
@@ -1237,14 +1314,22 @@ int compile_tuned(Plan &pl)
     g->fuse = saved.fuse;
     if (rc || !pl.fused) return rc ? rc : compile_plan(pl);  // tune on the steady form only
     std::vector<Ctx::Shape> cands;
+    const bool flat_ok = pl.args[0]->dtype != DT_BF16;
     if (threed) {
         for (int fu : {1, 0})
-            for (int tz : {16, 32, 64, 128}) cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu});
+            for (int tz : {16, 32, 64}) {
+                cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1});
+                if (flat_ok)
+                    for (int cells : {16, 32}) cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2});
+            }
     } else {
-        for (int fu : {1, 0})
+        for (int fu : {1, 0}) {
             for (int v : {0, 1})
                 for (int rows : {16, 32, 64})
-                    for (int w : {4, 8}) cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu});
+                    for (int w : {4, 8}) cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3});
+            if (flat_ok)
+                for (int cells : {16, 32, 64}) cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3});
+        }
     }
     g->tuning = true;
     Ctx::Shape best = saved;
@@ -1265,8 +1350,8 @@ int compile_tuned(Plan &pl)
     g->tuned[key] = best;
     save_tune(key, best);
     if (trace())
-        fprintf(stderr, "hdarray: tuned %s -> variant %d rows %d warps %d tile_z %d fuse %d (%.1f us)\n",
-                key.c_str(), best.variant, best.rows, best.warps, best.tile_z, best.fuse, best_ms * 1e3);
+        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d fuse %d (%.1f us)\n",
+                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.fuse, best_ms * 1e3);
     return rc;
 }
 
@@ -1479,13 +1564,15 @@ int flush_batch()
     if (it == g->batch_cache.end()) {
         // merge: all exchanges first, then every fused 2-D stencil of the same type, then the rest
         std::vector<CopyTask> copies;
-        std::map<int, Sten2DHost> sten;
+        std::map<std::pair<int, bool>, Sten2DHost> sten;
         std::vector<LaunchRec> rest;
         for (auto &p : plans) {
             if (p->k->kind == K_JACOBI2D && g->mode == HDARRAY_MODE_FUSED) {
                 copies.insert(copies.end(), p->copy_host.begin(), p->copy_host.end());
-                Sten2DHost &h = sten[p->s2.dtype];
+                Sten2DHost &h = sten[{p->s2.dtype, p->s2.flat}];
                 h.dtype = p->s2.dtype;
+                h.flat = p->s2.flat;
+                h.smem = std::max(h.smem, p->s2.smem);
                 const int pbase = (int)h.parts.size(), sbase = (int)h.segs.size();
                 h.parts.insert(h.parts.end(), p->s2.parts.begin(), p->s2.parts.end());
                 h.segs.insert(h.segs.end(), p->s2.segs.begin(), p->s2.segs.end());
@@ -1516,9 +1603,11 @@ int flush_batch()
         }
         int ai = 1;
         for (auto &kv : sten) {
-            LaunchRec L; L.kind = L_JACOBI2D; L.dtype = kv.first;
+            LaunchRec L; L.kind = kv.second.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = kv.second.dtype;
             L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2];
-            L.n0 = (int64_t)kv.second.tiles.size(); L.n1 = g->warps_per_cta; L.n2 = g->variant;
+            L.n0 = (int64_t)kv.second.tiles.size();
+            L.n1 = kv.second.flat ? (int64_t)kv.second.smem : g->warps_per_cta;
+            L.n2 = g->variant;
             ai += 3;
             if (L.n0 > 0) ls.push_back(L);
         }
@@ -1931,13 +2020,13 @@ int init_impl(int ndev, unsigned flags)
         const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
-        if (vv && (atoi(vv) == 0 || atoi(vv) == 1)) g->variant = atoi(vv);
+        if (vv && atoi(vv) >= 0 && atoi(vv) <= 2) g->variant = atoi(vv);
         const char *at = getenv("HDARRAY_AUTOTUNE");
         g->autotune = at && atoi(at) != 0;
         const char *fx = getenv("HDARRAY_FUSE_EXCHANGE");
         if (fx) g->fuse = atoi(fx) != 0;
         const char *v3 = getenv("HDARRAY_STENCIL3D_VARIANT");
-        if (v3 && (atoi(v3) == 0 || atoi(v3) == 1)) g->variant3 = atoi(v3);
+        if (v3 && atoi(v3) >= 0 && atoi(v3) <= 2) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
     }
@@ -1971,6 +2060,12 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
         return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
                               (unsigned *)L.p2, s);
     case L_SPLIT: return launch_split_panels((const SplitJob *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_FLAT2D:
+        return launch_jacobi2d_flat(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                                    (const Seg *)L.p2, (size_t)L.n1, s);
+    case L_FLAT3D:
+        return launch_stencil3d_flat(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
+                                     (const Seg *)L.p2, (size_t)L.n1, s);
     case L_GEMM_PANEL:
         return launch_gemm_panels((const PanelPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0,
                                   (float)L.f1, (unsigned *)L.p2, s);

@@ -66,7 +66,7 @@ struct Part {
 };
 
 // One kernel launch, recorded so that batches can merge it and graphs can replay it.
-enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL };
+enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL, L_FLAT2D, L_FLAT3D };
 struct LaunchRec {
     int kind = 0;
     int dtype = 0;
@@ -89,12 +89,16 @@ struct DevMem {
 // Host copies of a fused stencil plan's tables, kept so that a batch can concatenate them.
 struct Sten2DHost {
     int dtype = 0;
+    bool flat = false;  // flat-block tiles (k_jacobi2d_flat)
+    size_t smem = 0;    // dynamic shared memory per CTA of the flat form
     std::vector<StenPart2D> parts;
     std::vector<StenTile2D> tiles;
     std::vector<Seg> segs;
 };
 struct Sten3DHost {
     int dtype = 0;
+    bool flat = false;
+    size_t smem = 0;
     std::vector<StenPart3D> parts;
     std::vector<StenTile3D> tiles;
     std::vector<Seg> segs;

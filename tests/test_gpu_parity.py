@@ -601,28 +601,39 @@ def test_gemm_bf16x3_reuses_panels(gpu_lib):
 # execution choices must not change results: unfused exchange, autotuned tile shapes, variants
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("env", [{"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
-                                 {"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16"}])
-def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env):
+@pytest.mark.parametrize("env,dtype", [({"HDARRAY_FUSE_EXCHANGE": "0"}, "float"), ({"HDARRAY_AUTOTUNE": "1"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "2"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "2", "HDARRAY_TILE_ROWS": "1"}, "double"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "2", "HDARRAY_FUSE_EXCHANGE": "0"}, "float")])
+def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     dims, P = (260, 530), 6
-    x = synthetic.jacobi_field(dims, stream=81, dtype="float")
-    prog, last = jacobi_prog(dims, P, 7, BLOCK, "float", True)
+    x = synthetic.jacobi_field(dims, stream=81, dtype=dtype)
+    prog, last = jacobi_prog(dims, P, 7, BLOCK, dtype, True)
     lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
-    assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+    assert np.array_equal(read_all(lib, last, dims, dtype), orc.arrays[last].G)
 
 
-@pytest.mark.parametrize("env", [{"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
-                                 {"HDARRAY_STENCIL3D_VARIANT": "0"}, {"HDARRAY_TILE_Z": "7"}])
-def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env):
+def test_batch_flat_variant(gpu_lib, monkeypatch):
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "2")
+    test_batch_of_instances(gpu_lib)
+
+
+@pytest.mark.parametrize("env,dtype", [({"HDARRAY_FUSE_EXCHANGE": "0"}, "float"), ({"HDARRAY_AUTOTUNE": "1"}, "float"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "0"}, "float"), ({"HDARRAY_TILE_Z": "7"}, "float"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "2"}, "float"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "2", "HDARRAY_TILE_ROWS": "1"}, "double"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "2", "HDARRAY_TILE_Z": "5"}, "float")])
+def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     n = 36
     boxes = synthetic.kd_boxes(n, 7, stream=82, min_ext=6, max_ext=36)
-    x = synthetic.jacobi_field((n, n, n), stream=83, dtype="float")
-    prog, last = stencil3d_prog(n, boxes, 5, "float")
+    x = synthetic.jacobi_field((n, n, n), stream=83, dtype=dtype)
+    prog, last = stencil3d_prog(n, boxes, 5, dtype)
     lib, orc, *_ = run_program(prog, len(boxes), {"B": x}, gpu_lib)
-    got = np.zeros((n, n, n), np.float32)
+    got = np.zeros((n, n, n), NP[dtype])
     H.HDArrayRead(lib.arrays[last], got, lib.parts["D"])
     assert np.array_equal(got, orc.arrays[last].G)
