@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
             s = s + yp.v[k];
             s = s + zm.v[k];
             s = s + q[0].v[k];
-            out[k] = s / A(6);
+            out[k] = div6(s);
         }
         E *yrow = Yc + (int64_t)(z - zy) * zsy;
         if (full) {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
 // barrier of this step).  Stage layout: (8 + 2) rows x (32 chunks + 2 edge slots) x 16 bytes.
 // ------------------------------------------------------------------------------------------
 template <int DT, int NS>
-__global__ void __launch_bounds__(256) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
+__global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
                                                        const StenTile3D *__restrict__ tiles,
                                                        const Seg *__restrict__ segs)
 {
@@ -129,19 +129,28 @@ __global__ void __launch_bounds__(256) k_stencil3d_cta(const StenPart3D *__restr
     const bool needL = (t.xb >= t.x0) && (t.xb < t.x1);
     const bool needR = (t.xb + 32 * VEC - 1 >= t.x0) && (t.xb + 32 * VEC - 1 < t.x1);
 
-    auto issue_plane = [&](int zp) {  // every thread copies its share of plane zp
+    // This thread's share of every staged plane, fixed for the whole march: at most two 16-byte
+    // chunks (rows x 32 chunks over 256 threads) and possibly one band-end edge element.
+    const int nitems = nrows * 32;  // <= 320: thread t copies items t and t + 256
+    const int ch = threadIdx.x & 31, xc = t.xb + ch * VEC;
+    const bool chunk_ok = xc < t.x1 + 1 && xc + VEC > t.x0 - 1;
+    const int rr0 = threadIdx.x >> 5, rr1 = rr0 + 8;
+    const bool has0 = chunk_ok && threadIdx.x < nitems;
+    const bool has1 = chunk_ok && threadIdx.x + 256 < nitems;
+    const int64_t g0 = (int64_t)rr0 * ys + ch * VEC, g1 = (int64_t)rr1 * ys + ch * VEC;
+    const uint32_t so0 = (uint32_t)(rr0 * SLOTS + ch) * 16u, so1 = (uint32_t)(rr1 * SLOTS + ch) * 16u;
+    const int q = threadIdx.x;
+    const bool eL = q < ny && needL, eR = q >= 32 && q < 32 + ny && needR;
+    const int erow = eL ? q + 1 : q - 32 + 1;
+    const int64_t eoff = (int64_t)erow * ys + (eL ? -1 : 32 * VEC);
+    const uint32_t esoff = (uint32_t)(erow * SLOTS + (eL ? 32 : 33)) * 16u;
+    auto issue_plane = [&](int zp) {
         const int stage = (zp - t.z0 + 1) % NS;
-        const uint32_t sbase = ring_s + (uint32_t)(stage * STAGE) * 16u;
+        const uint32_t sb = ring_s + (uint32_t)(stage * STAGE) * 16u;
         const E *pz = xbase + (int64_t)(zp - P.xlo0) * zs;
-        for (int q = threadIdx.x; q < nrows * 32; q += blockDim.x) {
-            const int rr = q >> 5, ch = q & 31;
-            const int x = t.xb + ch * VEC;
-            if (x < t.x1 + 1 && x + VEC > t.x0 - 1) cpa16(sbase + (uint32_t)(rr * SLOTS + ch) * 16u, pz + rr * ys + ch * VEC);
-        }
-        const int q = threadIdx.x;  // band-end edges of the tile's own rows (1 .. ny)
-        if (q < ny && needL) edge_copy<DT>(sbase + (uint32_t)((q + 1) * SLOTS + 32) * 16u, pz + (q + 1) * ys - 1, true);
-        if (q >= 32 && q < 32 + ny && needR)
-            edge_copy<DT>(sbase + (uint32_t)((q - 32 + 1) * SLOTS + 33) * 16u, pz + (q - 32 + 1) * ys + 32 * VEC, false);
+        if (has0) cpa16(sb + so0, pz + g0);
+        if (has1) cpa16(sb + so1, pz + g1);
+        if (eL || eR) edge_copy<DT>(sb + esoff, pz + eoff, eL);
     };
 
     // prologue: planes z0-1 .. z0+NS-3
@@ -163,9 +172,10 @@ __global__ void __launch_bounds__(256) k_stencil3d_cta(const StenPart3D *__restr
         if (z - 2 + NS <= t.z1) issue_plane(z - 2 + NS);
         cpa_commit();
         if (mine) {
-            const uint4 *sm1 = smem + ((z - 1 - t.z0 + 1) % NS) * STAGE;
-            const uint4 *s0 = smem + ((z - t.z0 + 1) % NS) * STAGE;
-            const uint4 *sp1 = smem + ((z + 1 - t.z0 + 1) % NS) * STAGE;
+            const int k0 = z - t.z0;
+            const uint4 *sm1 = smem + (k0 % NS) * STAGE;
+            const uint4 *s0 = smem + ((k0 + 1) % NS) * STAGE;
+            const uint4 *sp1 = smem + ((k0 + 2) % NS) * STAGE;
             const int me = w + 1;  // my row in the staged planes
             Row<DT> c, ym, yp1, zm, zp;
             if (act) {
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(256) k_stencil3d_cta(const StenPart3D *__restr
                 s = s + yp1.v[k];
                 s = s + zm.v[k];
                 s = s + zp.v[k];
-                out[k] = s / A(6);
+                out[k] = div6(s);
             }
             if (full) {
                 *reinterpret_cast<typename EL::V *>(yp) = EL::pack(out);
