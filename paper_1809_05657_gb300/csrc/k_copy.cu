@@ -53,15 +53,26 @@ __device__ __forceinline__ void copy_task(const CopyTask &t)
             }
             for (; c < nch; c += 32) d[c] = s[c];
         }
-    } else {
+    } else {  // narrow rows: a thread per chunk, four copies in flight per thread
         const int total = nrows * nch;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            const int r = i / nch, c = i - r * nch;
-            const int row = t.row_begin + r;
-            const int o = row / t.n_mid, m = row - o * t.n_mid;
-            const T *s = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid);
-            T *d = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid);
-            d[c] = s[c];
+        const int step = blockDim.x;
+        for (int base = threadIdx.x; base < total; base += 4 * step) {
+            T v[4];
+            T *d[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                d[u] = nullptr;
+                const int i = base + u * step;
+                if (i >= total) continue;
+                const int r = i / nch, c = i - r * nch;
+                const int row = t.row_begin + r;
+                const int o = row / t.n_mid, m = row - o * t.n_mid;
+                v[u] = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid)[c];
+                d[u] = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid) + c;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (d[u]) *d[u] = v[u];
         }
     }
 }

@@ -344,6 +344,7 @@ int vec_for(std::initializer_list<int64_t> vals)
 }
 
 const int64_t TASK_BYTES = 256 * 1024;
+const int64_t TASK_ROWS = 1024;  // narrow rows (one-element faces) are split by count, not bytes
 
 // Append copy tasks moving box bx of array a from device buffer src to device buffer dst.
 void copy_tasks(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &bx,
@@ -366,7 +367,7 @@ void copy_tasks(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Bo
     if (t.vec < 2) t.vec = 2;
     t.pad = 0;
     const int64_t rows = vs.n_outer * vs.n_mid;
-    const int64_t per = std::max<int64_t>(1, TASK_BYTES / std::max<int64_t>(1, t.inner));
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(TASK_ROWS, TASK_BYTES / std::max<int64_t>(1, t.inner)));
     for (int64_t r = 0; r < rows; r += per) {
         t.row_begin = (int32_t)r;
         t.row_end = (int32_t)std::min(rows, r + per);

@@ -67,30 +67,41 @@ struct Elem<DT_BF16> {
 template <typename E>
 __device__ __forceinline__ void receive_flat(const Seg *__restrict__ segs, int seg0, int nseg, int first, int stride)
 {
-    int total = 0;
-    for (int s = 0; s < nseg; s++) total += segs[seg0 + s].n * segs[seg0 + s].m;
-    for (int base = first; base < total; base += 4 * stride) {
-        E v[4];
-        E *dst[4];
+    // segments in order; this thread's elements of each segment in batches of four loads, then
+    // four stores, and the batch carries over from one segment into the next
+    E v[4];
+    E *dst[4];
+    int nb = 0;
+    for (int s = 0; s < nseg; s++) {
+        const Seg g = segs[seg0 + s];
+        const int total = g.n * g.m;
+        const E *src = reinterpret_cast<const E *>(g.src);
+        E *d0 = reinterpret_cast<E *>(g.dst);
+        int o = first / g.n, k = first - (first / g.n) * g.n;
+        const int dof = stride / g.n, dk = stride - dof * g.n;
+        for (int i = first; i < total; i += stride) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            dst[u] = nullptr;
-            int i = base + u * stride;
-            if (i >= total) continue;
-            int s = seg0;
-            while (i >= segs[s].n * segs[s].m) {
-                i -= segs[s].n * segs[s].m;
-                s++;
+            for (int u = 0; u < 4; u++)
+                if (u == nb) {
+                    v[u] = src[o * g.sso + k * g.ss];
+                    dst[u] = d0 + o * g.dso + k * g.ds;
+                }
+            if (++nb == 4) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) *dst[u] = v[u];
+                nb = 0;
             }
-            const Seg &g = segs[s];
-            const int o = i / g.n, k = i - o * g.n;
-            v[u] = reinterpret_cast<const E *>(g.src)[o * g.sso + k * g.ss];
-            dst[u] = reinterpret_cast<E *>(g.dst) + o * g.dso + k * g.ds;
+            o += dof;
+            k += dk;
+            if (k >= g.n) {
+                k -= g.n;
+                o += 1;
+            }
         }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-            if (dst[u]) *dst[u] = v[u];
     }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+        if (u < nb) *dst[u] = v[u];
 }
 
 // The warp's receive phase, then __syncwarp orders the copies before the warp's loads.
