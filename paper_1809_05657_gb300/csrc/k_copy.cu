@@ -3,10 +3,12 @@
 // writes it with clEnqueueWriteBufferRect (Sec. 3.1, HDArrayApplyKernel); here source and
 // destination are device buffers of the same GPU and one kernel moves every section of a call.
 //
-// Each CTA copies one task (a slice of rows of one box).  Rows are copied with the widest access
-// the task's alignment allows (16-byte vectors for buffers whose rows start on 16-byte
-// boundaries), a warp per row for wide rows and a thread per chunk for narrow rows (the
-// one-element columns of 2-D column faces and 3-D x-faces).
+// Each CTA copies one task (a slice of rows of one box) with the widest access the task's
+// alignment allows (16-byte vectors for buffers whose rows start on 16-byte boundaries).  Every
+// thread keeps four loads in flight before it stores them: rows of 128 chunks or more go a warp
+// per row, lanes on consecutive chunks; shorter rows -- the faces of a partition, down to the
+// one-element rows of 2-D column faces and 3-D x-faces -- are flattened into (row, chunk) items,
+// consecutive threads on consecutive items.
 #include "kernels.h"
 
 namespace hda {
@@ -34,46 +36,47 @@ template <int V>
 __device__ __forceinline__ void copy_task(const CopyTask &t)
 {
     using T = typename VecOf<V>::T;
+    constexpr int UNR = 4;
     const int nch = t.inner / V;
     const int nrows = t.row_end - t.row_begin;
-    if (nch >= 32) {
+    if (nch >= 32 * UNR) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int r = warp; r < nrows; r += nw) {
             const int row = t.row_begin + r;
             const int o = row / t.n_mid, m = row - o * t.n_mid;
             const T *s = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid);
             T *d = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid);
-            int c = lane;
-            for (; c + 96 < nch; c += 128) {
-                T a = s[c], b = s[c + 32], e = s[c + 64], f = s[c + 96];
-                d[c] = a;
-                d[c + 32] = b;
-                d[c + 64] = e;
-                d[c + 96] = f;
-            }
-            for (; c < nch; c += 32) d[c] = s[c];
-        }
-    } else {  // narrow rows: a thread per chunk, four copies in flight per thread
-        const int total = nrows * nch;
-        const int step = blockDim.x;
-        for (int base = threadIdx.x; base < total; base += 4 * step) {
-            T v[4];
-            T *d[4];
+            for (int c0 = lane; c0 < nch; c0 += 32 * UNR) {
+                T v[UNR];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                d[u] = nullptr;
-                const int i = base + u * step;
-                if (i >= total) continue;
-                const int r = i / nch, c = i - r * nch;
-                const int row = t.row_begin + r;
-                const int o = row / t.n_mid, m = row - o * t.n_mid;
-                v[u] = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid)[c];
-                d[u] = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid) + c;
-            }
+                for (int u = 0; u < UNR; u++)
+                    if (c0 + 32 * u < nch) v[u] = s[c0 + 32 * u];
 #pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (d[u]) *d[u] = v[u];
+                for (int u = 0; u < UNR; u++)
+                    if (c0 + 32 * u < nch) d[c0 + 32 * u] = v[u];
+            }
         }
+        return;
+    }
+    const int total = nrows * nch;
+    const int step = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += UNR * step) {
+        T v[UNR];
+        T *d[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            d[u] = nullptr;
+            const int i = base + u * step;
+            if (i >= total) continue;
+            const int r = i / nch, c = i - r * nch;
+            const int row = t.row_begin + r;
+            const int o = row / t.n_mid, m = row - o * t.n_mid;
+            v[u] = reinterpret_cast<const T *>(t.src + o * t.s_outer + m * t.s_mid)[c];
+            d[u] = reinterpret_cast<T *>(t.dst + o * t.d_outer + m * t.d_mid) + c;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++)
+            if (d[u]) *d[u] = v[u];
     }
 }
 

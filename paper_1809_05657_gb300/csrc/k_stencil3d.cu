@@ -46,24 +46,24 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
     const int zx = (int)P.xlo0, zy = (int)P.ylo0;  // buffer origins along z
 
     Row<DT> zm, zc, q[PF], ym, yp, nym, nyp;
-    load_row<DT>(zm, Xc + (int64_t)(t.z0 - 1 - zx) * zs, 0, act, false, false, lane);
-    load_row<DT>(zc, Xc + (int64_t)(t.z0 - zx) * zs, 0, act, needL, needR, lane);
+    load_row<DT, true>(zm, Xc + (int64_t)(t.z0 - 1 - zx) * zs, 0, act, false, false, lane);
+    load_row<DT, true>(zc, Xc + (int64_t)(t.z0 - zx) * zs, 0, act, needL, needR, lane);
 #pragma unroll
     for (int k = 0; k < PF; k++)
-        if (t.z0 + 1 + k <= t.z1) load_row<DT>(q[k], Xc + (int64_t)(t.z0 + 1 + k - zx) * zs, 0, act, needL, needR, lane);
-    load_row<DT>(ym, Xm + (int64_t)(t.z0 - zx) * zs, 0, act, false, false, lane);
-    load_row<DT>(yp, Xp + (int64_t)(t.z0 - zx) * zs, 0, act, false, false, lane);
+        if (t.z0 + 1 + k <= t.z1) load_row<DT, true>(q[k], Xc + (int64_t)(t.z0 + 1 + k - zx) * zs, 0, act, needL, needR, lane);
+    load_row<DT, true>(ym, Xm + (int64_t)(t.z0 - zx) * zs, 0, act, false, false, lane);
+    load_row<DT, true>(yp, Xp + (int64_t)(t.z0 - zx) * zs, 0, act, false, false, lane);
 
     const bool full = (x >= t.x0) && (x + VEC <= t.x1);
     for (int z = t.z0; z < t.z1; z++) {
         if (z + 1 < t.z1) {
-            load_row<DT>(nym, Xm + (int64_t)(z + 1 - zx) * zs, 0, act, false, false, lane);
-            load_row<DT>(nyp, Xp + (int64_t)(z + 1 - zx) * zs, 0, act, false, false, lane);
+            load_row<DT, true>(nym, Xm + (int64_t)(z + 1 - zx) * zs, 0, act, false, false, lane);
+            load_row<DT, true>(nyp, Xp + (int64_t)(z + 1 - zx) * zs, 0, act, false, false, lane);
         }
         A left = __shfl_up_sync(0xffffffffu, zc.v[VEC - 1], 1);
         A right = __shfl_down_sync(0xffffffffu, zc.v[0], 1);
-        if (lane == 0) left = zc.l;
-        if (lane == 31) right = zc.r;
+        if (lane == 0) left = needL ? zc.l : A(0);
+        if (lane == 31) right = needR ? zc.r : A(0);
         A out[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; k++) {
@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
             s = s + yp.v[k];
             s = s + zm.v[k];
             s = s + q[0].v[k];
-            out[k] = div6(s);
+            out[k] = s;
         }
+        div6_n(out);
         E *yrow = Yc + (int64_t)(z - zy) * zsy;
         if (full) {
             *reinterpret_cast<typename EL::V *>(yrow) = EL::pack(out);
@@ -89,68 +90,63 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
 #pragma unroll
         for (int k = 0; k < PF - 1; k++) q[k] = q[k + 1];
         const int nz = z + 1 + PF;
-        if (nz <= t.z1) load_row<DT>(q[PF - 1], Xc + (int64_t)(nz - zx) * zs, 0, act, needL, needR, lane);
+        if (nz <= t.z1) load_row<DT, true>(q[PF - 1], Xc + (int64_t)(nz - zx) * zs, 0, act, needL, needR, lane);
         ym = nym;
         yp = nyp;
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// CTA variant: one CTA per tile of ny <= 8 consecutive rows (one warp each) of one band, marching
-// z.  Plane z' of rows y0-1 .. y0+ny (the tile's rows and their y neighbours) goes into stage
-// (z' - z0 + 1) % NS of a shared-memory ring by cp.async from every thread, so each input row
-// is fetched once per CTA and NS - 4 planes are in flight ahead of the one being computed.  At step
-// z the CTA reads planes z-1, z, z+1 and refills the stage of plane z-2 (read by nobody since the
-// barrier of this step).  Stage layout: (8 + 2) rows x (32 chunks + 2 edge slots) x 16 bytes.
+// CTA variant: one CTA of 256 threads per tile of ny rows x nch 16-byte chunks of the work box, one
+// chunk per thread (ny * nch <= 256), marching z.  A box narrower than 32 chunks gets more rows per
+// tile rather than idle lanes, and a wide box is cut into bands of equal width, so the lanes stay
+// busy whatever the partition's shape.  Plane z' of the staged region -- rows y0-1 .. y0+ny and
+// chunks xb-VEC .. xb+nch*VEC (the tile's chunks plus one halo chunk on each side, each halo chunk
+// only where the tile's output range ends on a chunk boundary) -- goes into stage (z' - z0 + 1) % NS
+// of a shared-memory ring by cp.async from every thread, so each input row is fetched once per CTA
+// and NS - 4 planes are in flight ahead of the one being computed.  At step z the CTA reads planes
+// z-1, z, z+1 and refills the stage of plane z-2 (read by nobody since the barrier of this step).
+// A stage is stage_slots >= (ny + 2) x (nch + 2) slots of 16 bytes, stage_slots <= 512.  Tiles are
+// ordered (z chunk, band, rows), so the CTAs resident together hold y-neighbouring tiles whose
+// shared halo rows meet in L2.
 // ------------------------------------------------------------------------------------------
 template <int DT, int NS>
 __global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
-                                                       const StenTile3D *__restrict__ tiles,
+                                                       const StenTile3D *__restrict__ tiles, int stage_slots,
                                                        const Seg *__restrict__ segs)
 {
     using EL = Elem<DT>;
     using E = typename EL::E;
     using A = typename EL::A;
     constexpr int VEC = EL::VEC;
-    constexpr int ROWS = 10, SLOTS = 34, STAGE = ROWS * SLOTS;  // in 16-byte slots
     extern __shared__ uint4 smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const StenTile3D t = tiles[blockIdx.x];
     const StenPart3D P = parts[t.part];
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(smem);
 
     receive_segments_cta<E>(segs, t.seg0, t.nseg);
 
-    const int ny = t.ny;
+    const int ny = t.ny, nch = t.nch, rw = nch + 2;  // a staged row: halo chunk, nch chunks, halo chunk
+    const int SS = (ny + 2) * rw;                     // 16-byte slots used per stage
     const int64_t zs = P.xs0, ys = P.xs1;
-    // row rr (0 .. ny+1) of the staged planes is array row y0 - 1 + rr
-    const E *xbase = reinterpret_cast<const E *>(P.x) + (int64_t)(t.y - 1 - P.xlo1) * ys + (t.xb - P.xlo2);
-    const int nrows = ny + 2;
-    const bool needL = (t.xb >= t.x0) && (t.xb < t.x1);
-    const bool needR = (t.xb + 32 * VEC - 1 >= t.x0) && (t.xb + 32 * VEC - 1 < t.x1);
+    // slot (rr, cc) of a stage holds row y0 - 1 + rr, elements xb + (cc - 1) * VEC ..
+    const E *xbase = reinterpret_cast<const E *>(P.x) + (int64_t)(t.y - 1 - P.xlo1) * ys + (t.xb - VEC - P.xlo2);
+    const bool needL = t.x0 == t.xb;              // x0 - 1 lies in the left halo chunk
+    const bool needR = t.x1 == t.xb + nch * VEC;  // x1 lies in the right halo chunk
 
-    // This thread's share of every staged plane, fixed for the whole march: at most two 16-byte
-    // chunks (rows x 32 chunks over 256 threads) and possibly one band-end edge element.
-    const int nitems = nrows * 32;  // <= 320: thread t copies items t and t + 256
-    const int ch = threadIdx.x & 31, xc = t.xb + ch * VEC;
-    const bool chunk_ok = xc < t.x1 + 1 && xc + VEC > t.x0 - 1;
-    const int rr0 = threadIdx.x >> 5, rr1 = rr0 + 8;
-    const bool has0 = chunk_ok && threadIdx.x < nitems;
-    const bool has1 = chunk_ok && threadIdx.x + 256 < nitems;
-    const int64_t g0 = (int64_t)rr0 * ys + ch * VEC, g1 = (int64_t)rr1 * ys + ch * VEC;
-    const uint32_t so0 = (uint32_t)(rr0 * SLOTS + ch) * 16u, so1 = (uint32_t)(rr1 * SLOTS + ch) * 16u;
-    const int q = threadIdx.x;
-    const bool eL = q < ny && needL, eR = q >= 32 && q < 32 + ny && needR;
-    const int erow = eL ? q + 1 : q - 32 + 1;
-    const int64_t eoff = (int64_t)erow * ys + (eL ? -1 : 32 * VEC);
-    const uint32_t esoff = (uint32_t)(erow * SLOTS + (eL ? 32 : 33)) * 16u;
+    // This thread's copy items, fixed for the whole march: slots j and j + 256 of every plane.
+    const int j0 = threadIdx.x, j1 = threadIdx.x + 256;
+    const int r0 = j0 / rw, c0 = j0 - r0 * rw, r1 = j1 / rw, c1 = j1 - r1 * rw;
+    const bool has0 = j0 < SS && (c0 > 0 || needL) && (c0 < rw - 1 || needR);
+    const bool has1 = j1 < SS && (c1 > 0 || needL) && (c1 < rw - 1 || needR);
+    const int64_t g0 = (int64_t)r0 * ys + c0 * VEC, g1 = (int64_t)r1 * ys + c1 * VEC;
     auto issue_plane = [&](int zp) {
         const int stage = (zp - t.z0 + 1) % NS;
-        const uint32_t sb = ring_s + (uint32_t)(stage * STAGE) * 16u;
+        const uint32_t sb = ring_s + (uint32_t)(stage * stage_slots) * 16u;
         const E *pz = xbase + (int64_t)(zp - P.xlo0) * zs;
-        if (has0) cpa16(sb + so0, pz + g0);
-        if (has1) cpa16(sb + so1, pz + g1);
-        if (eL || eR) edge_copy<DT>(sb + esoff, pz + eoff, eL);
+        if (has0) cpa16(sb + (uint32_t)j0 * 16u, pz + g0);
+        if (has1) cpa16(sb + (uint32_t)j1 * 16u, pz + g1);
     };
 
     // prologue: planes z0-1 .. z0+NS-3
@@ -160,50 +156,59 @@ __global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__re
         if (zp <= t.z1) issue_plane(zp);
         cpa_commit();
     }
-    const int x = t.xb + lane * VEC;
-    const bool act = (x < t.x1 + 1) && (x + VEC > t.x0 - 1);
-    const bool full = (x >= t.x0) && (x + VEC <= t.x1);
-    const bool mine = w < ny;
-    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.y + w - P.ylo1) * P.ys1 + (x - P.ylo2) +
+    // the chunk this thread computes: row r, chunk c (every chunk of the tile holds outputs)
+    const int r = threadIdx.x / nch, c = threadIdx.x - r * nch;
+    const int x = t.xb + c * VEC;
+    const bool act = r < ny;
+    const bool full = x >= t.x0 && x + VEC <= t.x1;
+    const int me = (r + 1) * rw + c + 1;
+    // x neighbours of the chunk's end elements: from the next lane's registers when it holds the
+    // neighbouring chunk of the same row, else from the staged row (the halo chunks included)
+    const bool shflL = c > 0 && lane > 0, shflR = c < nch - 1 && lane < 31;
+    const bool haveL = c > 0 || needL, haveR = c < nch - 1 || needR;
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.y + r - P.ylo1) * P.ys1 + (x - P.ylo2) +
             (int64_t)(t.z0 - P.ylo0) * P.ys0;
     for (int z = t.z0; z < t.z1; z++) {
         cpa_wait<NS - 4>();  // planes up to z + 1 have landed (this thread's copies)
         __syncthreads();     // ... and every other thread's
         if (z - 2 + NS <= t.z1) issue_plane(z - 2 + NS);
         cpa_commit();
-        if (mine) {
-            const int k0 = z - t.z0;
-            const uint4 *sm1 = smem + (k0 % NS) * STAGE;
-            const uint4 *s0 = smem + ((k0 + 1) % NS) * STAGE;
-            const uint4 *sp1 = smem + ((k0 + 2) % NS) * STAGE;
-            const int me = w + 1;  // my row in the staged planes
-            Row<DT> c, ym, yp1, zm, zp;
-            if (act) {
-                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me * SLOTS + lane), c.v);
-                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + (me - 1) * SLOTS + lane), ym.v);
-                EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + (me + 1) * SLOTS + lane), yp1.v);
-                EL::unpack(*reinterpret_cast<const typename EL::V *>(sm1 + me * SLOTS + lane), zm.v);
-                EL::unpack(*reinterpret_cast<const typename EL::V *>(sp1 + me * SLOTS + lane), zp.v);
-            }
-            A left = __shfl_up_sync(0xffffffffu, c.v[VEC - 1], 1);
-            A right = __shfl_down_sync(0xffffffffu, c.v[0], 1);
-            if (lane == 0 && needL) left = edge_read<DT>(s0 + me * SLOTS + 32, true);
-            if (lane == 31 && needR) right = edge_read<DT>(s0 + me * SLOTS + 33, false);
-            A out[VEC];
+        const int k0 = z - t.z0;
+        const uint4 *sm1 = smem + (k0 % NS) * stage_slots;
+        const uint4 *s0 = smem + ((k0 + 1) % NS) * stage_slots;
+        const uint4 *sp1 = smem + ((k0 + 2) % NS) * stage_slots;
+        Row<DT> cv, ym, yq, zm, zq;
+        if (act) {
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me), cv.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me - rw), ym.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me + rw), yq.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(sm1 + me), zm.v);
+            EL::unpack(*reinterpret_cast<const typename EL::V *>(sp1 + me), zq.v);
+        } else {
 #pragma unroll
-            for (int k = 0; k < VEC; k++) {
-                const A wv = k > 0 ? c.v[k - 1] : left;
-                const A ev = k < VEC - 1 ? c.v[k + 1] : right;
-                A s = wv + ev;
-                s = s + ym.v[k];
-                s = s + yp1.v[k];
-                s = s + zm.v[k];
-                s = s + zp.v[k];
-                out[k] = div6(s);
-            }
+            for (int k = 0; k < VEC; k++) cv.v[k] = ym.v[k] = yq.v[k] = zm.v[k] = zq.v[k] = A(0);
+        }
+        A left = __shfl_up_sync(0xffffffffu, cv.v[VEC - 1], 1);
+        A right = __shfl_down_sync(0xffffffffu, cv.v[0], 1);
+        if (!shflL) left = act && haveL ? EL::load1(reinterpret_cast<const E *>(s0 + me) - 1) : A(0);
+        if (!shflR) right = act && haveR ? EL::load1(reinterpret_cast<const E *>(s0 + me + 1)) : A(0);
+        A out[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const A wv = k > 0 ? cv.v[k - 1] : left;
+            const A ev = k < VEC - 1 ? cv.v[k + 1] : right;
+            A s = wv + ev;
+            s = s + ym.v[k];
+            s = s + yq.v[k];
+            s = s + zm.v[k];
+            s = s + zq.v[k];
+            out[k] = s;
+        }
+        div6_n(out);
+        if (act) {
             if (full) {
                 *reinterpret_cast<typename EL::V *>(yp) = EL::pack(out);
-            } else if (act) {
+            } else {
 #pragma unroll
                 for (int k = 0; k < VEC; k++)
                     if (x + k >= t.x0 && x + k < t.x1) EL::store1(yp + k, out[k]);
@@ -215,18 +220,25 @@ __global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__re
 }
 
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
-                             int ntiles, const Seg *segs, int warps_per_cta, int variant, cudaStream_t s)
+                             int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
+                             cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (variant == 1) {
-        constexpr int NS = 8;
-        const size_t sm = (size_t)NS * 10 * 34 * 16;
-        switch (dtype) {
-        case DT_F64: k_stencil3d_cta<DT_F64, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
-        case DT_F32: k_stencil3d_cta<DT_F32, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
-        case DT_BF16: k_stencil3d_cta<DT_BF16, NS><<<ntiles, 256, sm, s>>>(parts, tiles, segs); break;
-        default: return cudaErrorInvalidValue;
+        constexpr int NS = STENCIL3D_STAGES;
+        const int slots = (int)(smem / ((size_t)NS * 16));
+        if (slots < 1 || slots > 512 || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
+        const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
+        if (which < 0) return cudaErrorInvalidValue;
+        using KFn = void (*)(const StenPart3D *, const StenTile3D *, int, const Seg *);
+        const KFn fns[3] = {k_stencil3d_cta<DT_F64, NS>, k_stencil3d_cta<DT_F32, NS>, k_stencil3d_cta<DT_BF16, NS>};
+        static bool attr[3] = {false, false, false};
+        if (!attr[which]) {
+            cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 512 * 16);
+            if (e != cudaSuccess) return e;
+            attr[which] = true;
         }
+        fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs);
         return cudaGetLastError();
     }
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 8;

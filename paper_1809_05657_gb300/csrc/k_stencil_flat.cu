@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(256) k_stencil3d_flat(const StenPart3D *__rest
             s = s + (A)s0[o + SX];
             s = s + (A)sm1[o];
             s = s + (A)sp1[o];
-            yz[(int64_t)(t.y + r - P.ylo1) * P.ys1 + (t.x0 + c - P.ylo2)] = (E)div6(s);
+            A q[1] = {s};
+            div6_n(q);
+            yz[(int64_t)(t.y + r - P.ylo1) * P.ys1 + (t.x0 + c - P.ylo2)] = (E)q[0];
         });
     }
     cpa_wait<0>();

@@ -79,12 +79,13 @@ struct Ctx {
     int warps_per_cta = 8;  // 2-D warps per CTA
     int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
-    int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per 8 rows with a plane ring)
+    int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
+    int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
     bool tuning = false;  // compile_plan is being called by the tuner
-    struct Shape { int variant, rows, warps, tile_z, fuse, variant3; };
+    struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3; };
     std::map<std::string, Shape> tuned;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
@@ -343,7 +344,7 @@ int vec_for(std::initializer_list<int64_t> vals)
     return 1;
 }
 
-const int64_t TASK_BYTES = 256 * 1024;
+const int64_t TASK_BYTES = 64 * 1024;
 const int64_t TASK_ROWS = 1024;  // narrow rows (one-element faces) are split by count, not bytes
 
 // Append copy tasks moving box bx of array a from device buffer src to device buffer dst.
@@ -706,11 +707,14 @@ void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const 
     out.push_back(sg);
 }
 
-// Tiles of the fused 3-D kernel for one device: (z chunk, x band, rows_per_tile rows); the
-// receive segments are the parts of the incoming faces on the tile's six face strips.
+// Tiles of the fused 3-D kernel for one device, in (z chunk, x band, rows) order; the receive
+// segments are the parts of the incoming faces on the tile's six face strips.  variant 0: bands
+// of 32 chunks, one row per tile; variant 1: the box's chunks cut into bands of equal width of
+// at most band_chunks, as many rows per tile as 256 threads hold; variant 2 (flat_cells > 0):
+// balanced widths up to 128 elements, rows so that a plane has about flat_cells cells.
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
-                     const std::vector<Move> &recv, bool want_segs, int rows_per_tile, Sten3DHost &h,
-                     int flat_cells = 0)
+                     const std::vector<Move> &recv, bool want_segs, int variant, Sten3DHost &h,
+                     int flat_cells = 0, int band_chunks = 32)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart3D P;
@@ -721,7 +725,7 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
     P.ylo0 = by.alloc.lo[0]; P.ylo1 = by.alloc.lo[1]; P.ylo2 = by.alloc.lo[2];
     P.ys0 = by.st[0]; P.ys1 = by.st[1];
     h.parts.push_back(P);
-    const int VEC = 16 / X->esize, BAND = 32 * VEC;
+    const int VEC = 16 / X->esize;
     const int ZC = std::max(1, g->tile_z);
     bool exact = true;
     int64_t covered = 0, need = 0;
@@ -730,8 +734,18 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
         if (box_overlaps(m.box, W)) exact = false;
     }
     int64_t xb0 = bx.alloc.lo[2] + align_down(W.lo[2] - bx.alloc.lo[2], VEC);
-    int64_t band = BAND;
-    if (flat_cells > 0) {  // flat blocks: balanced widths up to 128, rows so that a plane has ~flat_cells
+    int64_t band = 32 * VEC;
+    int rows_per_tile = 1;
+    if (variant == 1) {
+        const int64_t chunks = (W.hi[2] - xb0 + VEC - 1) / VEC;
+        const int64_t cap = std::max(1, std::min(band_chunks, 256));
+        const int64_t nb = (chunks + cap - 1) / cap;
+        const int64_t nch = (chunks + nb - 1) / nb;
+        band = nch * VEC;
+        rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(256 / nch, 512 / (nch + 2) - 2));
+        h.smem = std::max(h.smem, (size_t)STENCIL3D_STAGES * (rows_per_tile + 2) * (nch + 2) * 16);
+    }
+    if (flat_cells > 0) {
         const int64_t width = W.hi[2] - W.lo[2];
         const int64_t nbx = (width + 127) / 128;
         band = (width + nbx - 1) / nbx;
@@ -750,6 +764,7 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
                 t.x0 = (int32_t)std::max<int64_t>(W.lo[2], xb);
                 t.x1 = (int32_t)std::min<int64_t>(W.hi[2], xb + band);
                 t.xb = (int32_t)xb;
+                t.nch = (int32_t)((t.x1 - xb + VEC - 1) / VEC);
                 t.seg0 = (int32_t)h.segs.size();
                 t.nseg = 0;
                 if (want_segs && exact) {
@@ -891,8 +906,8 @@ int compile_plan(Plan &pl)
             int t0 = (int)h.tiles.size();
             const bool flat = g->variant3 == 2 && X->dtype != DT_BF16;
             h.flat = flat;
-            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->variant3 == 1 ? 8 : 1, h,
-                                 flat ? g->tile_rows * 64 : 0))
+            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, flat ? 2 : g->variant3, h,
+                                 flat ? g->tile_rows * 64 : 0, g->band3))
                 fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -919,7 +934,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         } else {
@@ -930,7 +945,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         }
@@ -1224,6 +1239,7 @@ void apply_shape(const Ctx::Shape &s, bool threed)
         g->tile_z = s.tile_z;
         g->variant3 = s.variant3;
         g->tile_rows = s.rows;
+        g->band3 = s.band3;
     } else {
         g->variant = s.variant;
         g->tile_rows = s.rows;
@@ -1233,7 +1249,7 @@ void apply_shape(const Ctx::Shape &s, bool threed)
 
 Ctx::Shape current_shape()
 {
-    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3};
+    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3, g->band3};
 }
 
 const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
@@ -1247,8 +1263,8 @@ void load_tune_file()
     if (!f) return;
     char key[4096];
     Ctx::Shape s;
-    while (fscanf(f, "%4095s %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
-                  &s.variant3) == 7)
+    while (fscanf(f, "%4095s %d %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
+                  &s.variant3, &s.band3) == 8)
         g->tuned[key] = s;
     fclose(f);
 }
@@ -1258,7 +1274,8 @@ void save_tune(const std::string &key, const Ctx::Shape &s)
     if (!tune_file()) return;
     FILE *f = fopen(tune_file(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3);
+    fprintf(f, "%s %d %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3,
+            s.band3);
     fclose(f);
 }
 
@@ -1319,17 +1336,21 @@ int compile_tuned(Plan &pl)
     if (threed) {
         for (int fu : {1, 0})
             for (int tz : {16, 32, 64}) {
-                cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1});
+                for (int band : {16, 32, 64})
+                    cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band});
                 if (flat_ok)
-                    for (int cells : {16, 32}) cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2});
+                    for (int cells : {16, 32})
+                        cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3});
             }
     } else {
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
                 for (int rows : {16, 32, 64})
-                    for (int w : {4, 8}) cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3});
+                    for (int w : {4, 8})
+                        cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3});
             if (flat_ok)
-                for (int cells : {16, 32, 64}) cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3});
+                for (int cells : {16, 32, 64})
+                    cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3});
         }
     }
     g->tuning = true;
@@ -1351,8 +1372,9 @@ int compile_tuned(Plan &pl)
     g->tuned[key] = best;
     save_tune(key, best);
     if (trace())
-        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d fuse %d (%.1f us)\n",
-                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.fuse, best_ms * 1e3);
+        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d band %d fuse %d (%.1f us)\n",
+                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.band3, best.fuse,
+                best_ms * 1e3);
     return rc;
 }
 
@@ -2030,6 +2052,8 @@ int init_impl(int ndev, unsigned flags)
         if (v3 && atoi(v3) >= 0 && atoi(v3) <= 2) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
+        const char *b3 = getenv("HDARRAY_BAND3");
+        if (b3 && atoi(b3) > 0) g->band3 = atoi(b3);
     }
     g->inited = true;
     return HDARRAY_OK;
@@ -2053,7 +2077,7 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
     case L_STENCIL3D:
         return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
-                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
+                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_SQDIFF: return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, s);
     case L_GEMM64:
         return launch_gemm_f64((const GemmPart *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, L.f0, L.f1, s);

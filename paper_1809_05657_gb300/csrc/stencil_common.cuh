@@ -108,7 +108,10 @@ __device__ __forceinline__ void receive_flat(const Seg *__restrict__ segs, int s
 template <typename E>
 __device__ __forceinline__ void receive_segments(const Seg *__restrict__ segs, int seg0, int nseg, int lane)
 {
-    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, lane, 32);
+    if (nseg > 0) {
+        receive_flat<E>(segs, seg0, nseg, lane, 32);
+        __threadfence();  // the copies reach L2, where cp.async.cg loads read
+    }
     __syncwarp();
 }
 
@@ -120,7 +123,9 @@ struct Row {
     typename Elem<DT>::A l, r;
 };
 
-template <int DT>
+// ZERO: lanes past the band's end hold zeros (their results are not stored, but they take part in
+// the warp's vote on the division path).
+template <int DT, bool ZERO = false>
 __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::E *xrow, int x,
                                          bool act, bool needL, bool needR, int lane)
 {
@@ -128,6 +133,9 @@ __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::
     if (act) {
         typename EL::V v = *reinterpret_cast<const typename EL::V *>(xrow + x);
         EL::unpack(v, row.v);
+    } else if (ZERO) {
+#pragma unroll
+        for (int k = 0; k < EL::VEC; k++) row.v[k] = typename EL::A(0);
     }
     if (lane == 0 && needL) row.l = EL::load1(xrow + x - 1);
     if (lane == 31 && needR) row.r = EL::load1(xrow + x + EL::VEC);
@@ -136,17 +144,46 @@ __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::
 // Correctly rounded s / 6 in binary32 without a division: q = RN(s * c) with c = RN(1/6), the
 // remainder r = s - q * 6 (exact with one FMA), then q + r * c rounded once -- the correction step
 // for division by a constant known in advance (Brisebarre, Muller & Raina, IEEE Trans. Computers
-// 53(8), 2004).  Checked against IEEE division for every binary32 input: identical whenever
-// |s| >= 2^-100; below that the true division is used.
-__device__ __forceinline__ float div6(float s)
+// 53(8), 2004).  Checked against IEEE division for every finite binary32 input: identical whenever
+// |s| >= 2^-100.  The sign is copied from s, which is the quotient's sign there and makes the
+// result exact for s = +0 and -0 as well (the bare steps give +0 for -0).  Other tiny sums,
+// infinities (an infinite s gives a NaN remainder) and NaN must take the true division.
+__device__ __forceinline__ float div6_fast(float s)
 {
     const float c = 0x1.555556p-3f;  // RN(1/6)
-    float q = __fmul_rn(s, c);
+    const float q = __fmul_rn(s, c);
     const float r = __fmaf_rn(-q, 6.0f, s);
-    q = __fmaf_rn(r, c, q);
-    return fabsf(s) >= 0x1p-100f ? q : __fdiv_rn(s, 6.0f);
+    return copysignf(__fmaf_rn(r, c, q), s);
 }
-__device__ __forceinline__ double div6(double s) { return s / 6.0; }
+__device__ __forceinline__ bool div6_fast_ok(float s)
+{
+    const float a = fabsf(s);
+    return (a >= 0x1p-100f && a <= 0x1.fffffep127f) || a == 0.0f;  // false for NaN
+}
+
+// s[k] / 6 for every k, in place, correctly rounded.  The rare sums outside the fast method's range
+// send the lanes executing together (one vote over __activemask) through IEEE division, so the
+// common path carries no division instructions.
+template <int N>
+__device__ __forceinline__ void div6_n(float (&s)[N])
+{
+    bool slow = false;
+#pragma unroll
+    for (int k = 0; k < N; k++) slow |= !div6_fast_ok(s[k]);
+    if (__any_sync(__activemask(), slow)) {
+#pragma unroll
+        for (int k = 0; k < N; k++) s[k] = __fdiv_rn(s[k], 6.0f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k++) s[k] = div6_fast(s[k]);
+    }
+}
+template <int N>
+__device__ __forceinline__ void div6_n(double (&s)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; k++) s[k] = s[k] / 6.0;
+}
 
 // Asynchronous global -> shared copies (cp.async) and their group waits.
 __device__ __forceinline__ void cpa16(uint32_t saddr, const void *g)
@@ -189,8 +226,10 @@ __device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, boo
 template <typename E>
 __device__ __forceinline__ void receive_segments_cta(const Seg *__restrict__ segs, int seg0, int nseg)
 {
-    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
-    __threadfence_block();
+    if (nseg > 0) {
+        receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
+        __threadfence();  // the copies reach L2, where cp.async.cg loads read
+    }
     __syncthreads();
 }
 

@@ -637,3 +637,55 @@ def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     got = np.zeros((n, n, n), NP[dtype])
     H.HDArrayRead(lib.arrays[last], got, lib.parts["D"])
     assert np.array_equal(got, orc.arrays[last].G)
+
+
+@pytest.mark.parametrize("band,dtype", [("1", "float"), ("4", "float"), ("16", "float"), ("64", "float"),
+                                        ("3", "bf16"), ("64", "bf16"), ("5", "double"), ("64", "double")])
+def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype):
+    """The CTA kernel's tiles follow the box: narrow bands with many rows, wide bands with few,
+    bands of equal width across a row, ragged last tiles in y and z."""
+    monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", "1")
+    monkeypatch.setenv("HDARRAY_BAND3", band)
+    monkeypatch.setenv("HDARRAY_TILE_Z", "9")
+    n = 44
+    dims = (n, n, 150)
+    boxes = [((0, 0, 0), (20, 44, 3)), ((0, 0, 3), (20, 44, 17)), ((0, 0, 17), (20, 30, 150)),
+             ((0, 30, 17), (20, 44, 150)), ((20, 0, 0), (44, 7, 150)), ((20, 7, 0), (44, 44, 61)),
+             ((20, 7, 61), (44, 44, 150))]
+    work = [(tuple(max(1, v) for v in lo), tuple(min(d - 1, v) for v, d in zip(hi, dims))) for lo, hi in boxes]
+    x = synthetic.jacobi_field(dims, stream=84, dtype=dtype)
+    prog = [("create", "B", dtype, dims), ("create", "A", dtype, dims),
+            ("manual", "D", dims, boxes), ("manual", "W", dims, work), ("write", "B", "D")]
+    a, b = "B", "A"
+    for _ in range(4):
+        prog.append(("apply", "stencil3d", "W", [a, b]))
+        a, b = b, a
+    lib, orc, *_ = run_program(prog, len(boxes), {"B": x}, gpu_lib)
+    got = np.zeros(dims, NP[dtype])
+    H.HDArrayRead(lib.arrays[a], got, lib.parts["D"])
+    assert np.array_equal(got.view(np.uint8), orc.arrays[a].G.view(np.uint8))
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+def test_stencil3d_special_values(gpu_lib, monkeypatch, variant):
+    """Sums outside the fast division's range -- subnormal and tiny values, infinities, signed
+    zeros -- are divided exactly as IEEE division does (bit-exact against the oracle's s / 6)."""
+    monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", variant)
+    n = 30
+    boxes = synthetic.kd_boxes(n, 5, stream=85, min_ext=6, max_ext=30)
+    x = synthetic.jacobi_field((n, n, n), stream=86, dtype="float")
+    x[:, :10, :] *= np.float32(2.0 ** -120)   # sums near 2^-118: below the fast method's range
+    x[:, 10:13, :] *= np.float32(2.0 ** -135)  # subnormal values and results
+    x[3:6, 20, 7:9] = np.inf
+    x[12, 25, 3] = np.float32(3.0e38)          # large finite values next to each other
+    x[12, 25, 4] = np.float32(3.0e38)
+    x[20:25, 14:17, 2:5] = np.float32(-0.0)     # all-negative-zero neighbourhoods: -0 / 6 = -0
+    prog, last = stencil3d_prog(n, boxes, 3, "float")
+    lib, orc, *_ = run_program(prog, len(boxes), {"B": x}, gpu_lib)
+    got = np.zeros((n, n, n), np.float32)
+    H.HDArrayRead(lib.arrays[last], got, lib.parts["D"])
+    want = orc.arrays[last].G
+    assert np.isinf(want).any() and (np.abs(want[(want != 0) & np.isfinite(want)]) < 2.0 ** -100).any()
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.array_equal(got[ok].view(np.uint32), want[ok].view(np.uint32))
