@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
         }
         A left = __shfl_up_sync(0xffffffffu, zc.v[VEC - 1], 1);
         A right = __shfl_down_sync(0xffffffffu, zc.v[0], 1);
-        if (lane == 0) left = needL ? zc.l : A(0);
-        if (lane == 31) right = needR ? zc.r : A(0);
+        if (lane == 0) left = needL ? zc.l : A(1);
+        if (lane == 31) right = needR ? zc.r : A(1);
         A out[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; k++) {
@@ -97,27 +97,32 @@ __global__ void __launch_bounds__(256) k_stencil3d(const StenPart3D *__restrict_
 }
 
 // ------------------------------------------------------------------------------------------
-// CTA variant: one CTA of 256 threads per tile of ny rows x nch 16-byte chunks of the work box, one
-// chunk per thread (ny * nch <= 256), marching z.  A box narrower than 32 chunks gets more rows per
+// CTA variant: one CTA of T threads (256 or 512) per tile of ny rows x nch 16-byte chunks of the
+// work box, one chunk per thread (ny * nch <= T), marching z.  A box narrower than 32 chunks gets more rows per
 // tile rather than idle lanes, and a wide box is cut into bands of equal width, so the lanes stay
 // busy whatever the partition's shape.  Plane z' of the staged region -- rows y0-1 .. y0+ny and
 // chunks xb-VEC .. xb+nch*VEC (the tile's chunks plus one halo chunk on each side, each halo chunk
-// only where the tile's output range ends on a chunk boundary) -- goes into stage (z' - z0 + 1) % NS
-// of a shared-memory ring by cp.async from every thread, so each input row is fetched once per CTA
-// and NS - 4 planes are in flight ahead of the one being computed.  At step z the CTA reads planes
-// z-1, z, z+1 and refills the stage of plane z-2 (read by nobody since the barrier of this step).
-// A stage is stage_slots >= (ny + 2) x (nch + 2) slots of 16 bytes, stage_slots <= 512.  Tiles are
-// ordered (z chunk, band, rows), so the CTAs resident together hold y-neighbouring tiles whose
-// shared halo rows meet in L2.
+// only where the tile's output range ends on a chunk boundary) -- is entry e = z' - z0 + 1 of the
+// tile's plane sequence and goes into stage e % NS of a shared-memory ring by cp.async from every
+// thread, so each input row is fetched once per CTA.  A step computes two output planes z, z+1
+// from entries k .. k+3 (planes z-1 .. z+2, k = z - z0), after refilling the stages of entries k-2
+// and k-1 (read by nobody since the barrier of this step) with entries k+NS-2 and k+NS-1: NS - 4
+// planes stay in flight ahead of those being computed, and the barrier, the ring bookkeeping and
+// the centre plane z+1 (also plane z's upper neighbour) are shared by the two outputs.  A stage is
+// stage_slots >= (ny + 2) x (nch + 2) slots of 16 bytes, stage_slots <= 2T.  Tiles are ordered
+// (z chunk, band, rows), so the CTAs resident together hold y-neighbouring tiles whose shared halo
+// rows meet in L2.
 // ------------------------------------------------------------------------------------------
-template <int DT, int NS>
-__global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
+template <int DT, int NS, int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_cta(const StenPart3D *__restrict__ parts,
                                                        const StenTile3D *__restrict__ tiles, int stage_slots,
                                                        const Seg *__restrict__ segs)
 {
+    static_assert((NS & (NS - 1)) == 0 && NS >= 6, "ring depth: a power of two, at least 6");
     using EL = Elem<DT>;
     using E = typename EL::E;
     using A = typename EL::A;
+    using V = typename EL::V;
     constexpr int VEC = EL::VEC;
     extern __shared__ uint4 smem[];
     const int lane = threadIdx.x & 31;
@@ -129,33 +134,35 @@ __global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__re
 
     const int ny = t.ny, nch = t.nch, rw = nch + 2;  // a staged row: halo chunk, nch chunks, halo chunk
     const int SS = (ny + 2) * rw;                     // 16-byte slots used per stage
+    const int L = t.z1 - t.z0;                        // output planes; entries 0 .. L+1
     const int64_t zs = P.xs0, ys = P.xs1;
-    // slot (rr, cc) of a stage holds row y0 - 1 + rr, elements xb + (cc - 1) * VEC ..
-    const E *xbase = reinterpret_cast<const E *>(P.x) + (int64_t)(t.y - 1 - P.xlo1) * ys + (t.xb - VEC - P.xlo2);
     const bool needL = t.x0 == t.xb;              // x0 - 1 lies in the left halo chunk
     const bool needR = t.x1 == t.xb + nch * VEC;  // x1 lies in the right halo chunk
 
-    // This thread's copy items, fixed for the whole march: slots j and j + 256 of every plane.
-    const int j0 = threadIdx.x, j1 = threadIdx.x + 256;
+    // This thread's copy items, fixed for the whole march: slots j and j + T of every plane.
+    const int j0 = threadIdx.x, j1 = threadIdx.x + T;
     const int r0 = j0 / rw, c0 = j0 - r0 * rw, r1 = j1 / rw, c1 = j1 - r1 * rw;
     const bool has0 = j0 < SS && (c0 > 0 || needL) && (c0 < rw - 1 || needR);
     const bool has1 = j1 < SS && (c1 > 0 || needL) && (c1 < rw - 1 || needR);
+    // entry e's slot (rr, cc) holds row y0 - 1 + rr, elements xb + (cc - 1) * VEC .. of plane z0 - 1 + e
+    const E *src = reinterpret_cast<const E *>(P.x) + (int64_t)(t.z0 - 1 - P.xlo0) * zs +
+                   (int64_t)(t.y - 1 - P.xlo1) * ys + (t.xb - VEC - P.xlo2);
     const int64_t g0 = (int64_t)r0 * ys + c0 * VEC, g1 = (int64_t)r1 * ys + c1 * VEC;
-    auto issue_plane = [&](int zp) {
-        const int stage = (zp - t.z0 + 1) % NS;
-        const uint32_t sb = ring_s + (uint32_t)(stage * stage_slots) * 16u;
-        const E *pz = xbase + (int64_t)(zp - P.xlo0) * zs;
-        if (has0) cpa16(sb + (uint32_t)j0 * 16u, pz + g0);
-        if (has1) cpa16(sb + (uint32_t)j1 * 16u, pz + g1);
+    const uint32_t stage_bytes = (uint32_t)stage_slots * 16u;
+    int enext = 0;  // next entry to issue
+    auto issue = [&]() {
+        if (enext <= L + 1) {
+            const uint32_t sb = ring_s + (uint32_t)(enext & (NS - 1)) * stage_bytes;
+            if (has0) cpa16(sb + (uint32_t)j0 * 16u, src + g0);
+            if (has1) cpa16(sb + (uint32_t)j1 * 16u, src + g1);
+            src += zs;
+        }
+        enext++;
+        cpa_commit();  // one group per entry, empty past the end
     };
-
-    // prologue: planes z0-1 .. z0+NS-3
 #pragma unroll 1
-    for (int k = 0; k < NS - 1; k++) {
-        const int zp = t.z0 - 1 + k;
-        if (zp <= t.z1) issue_plane(zp);
-        cpa_commit();
-    }
+    for (int k = 0; k < NS - 2; k++) issue();  // entries 0 .. NS-3
+
     // the chunk this thread computes: row r, chunk c (every chunk of the tile holds outputs)
     const int r = threadIdx.x / nch, c = threadIdx.x - r * nch;
     const int x = t.xb + c * VEC;
@@ -168,53 +175,65 @@ __global__ void __launch_bounds__(256, 4) k_stencil3d_cta(const StenPart3D *__re
     const bool haveL = c > 0 || needL, haveR = c < nch - 1 || needR;
     E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.y + r - P.ylo1) * P.ys1 + (x - P.ylo2) +
             (int64_t)(t.z0 - P.ylo0) * P.ys0;
-    for (int z = t.z0; z < t.z1; z++) {
-        cpa_wait<NS - 4>();  // planes up to z + 1 have landed (this thread's copies)
-        __syncthreads();     // ... and every other thread's
-        if (z - 2 + NS <= t.z1) issue_plane(z - 2 + NS);
-        cpa_commit();
-        const int k0 = z - t.z0;
-        const uint4 *sm1 = smem + (k0 % NS) * stage_slots;
-        const uint4 *s0 = smem + ((k0 + 1) % NS) * stage_slots;
-        const uint4 *sp1 = smem + ((k0 + 2) % NS) * stage_slots;
-        Row<DT> cv, ym, yq, zm, zq;
+
+    auto ld = [&](int e, int off, A (&v)[VEC]) {  // chunk `me + off` of entry e
         if (act) {
-            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me), cv.v);
-            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me - rw), ym.v);
-            EL::unpack(*reinterpret_cast<const typename EL::V *>(s0 + me + rw), yq.v);
-            EL::unpack(*reinterpret_cast<const typename EL::V *>(sm1 + me), zm.v);
-            EL::unpack(*reinterpret_cast<const typename EL::V *>(sp1 + me), zq.v);
+            EL::unpack(*reinterpret_cast<const V *>(smem + (e & (NS - 1)) * stage_slots + me + off), v);
         } else {
 #pragma unroll
-            for (int k = 0; k < VEC; k++) cv.v[k] = ym.v[k] = yq.v[k] = zm.v[k] = zq.v[k] = A(0);
+            for (int k = 0; k < VEC; k++) v[k] = A(1);  // idle threads: sums of ones
         }
-        A left = __shfl_up_sync(0xffffffffu, cv.v[VEC - 1], 1);
-        A right = __shfl_down_sync(0xffffffffu, cv.v[0], 1);
-        if (!shflL) left = act && haveL ? EL::load1(reinterpret_cast<const E *>(s0 + me) - 1) : A(0);
-        if (!shflR) right = act && haveR ? EL::load1(reinterpret_cast<const E *>(s0 + me + 1)) : A(0);
+    };
+    // plane with centre cv (entry e), y neighbours from entry e, z neighbours zm and zq; stored at yq
+    auto plane = [&](int e, const A (&cv)[VEC], const A (&zm)[VEC], const A (&zq)[VEC], E *out_p) {
+        A ym[VEC], yq[VEC];
+        ld(e, -rw, ym);
+        ld(e, rw, yq);
+        A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
+        A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
+        const E *row = reinterpret_cast<const E *>(smem + (e & (NS - 1)) * stage_slots + me);
+        if (!shflL) left = act && haveL ? EL::load1(row - 1) : A(1);
+        if (!shflR) right = act && haveR ? EL::load1(row + VEC) : A(1);
         A out[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; k++) {
-            const A wv = k > 0 ? cv.v[k - 1] : left;
-            const A ev = k < VEC - 1 ? cv.v[k + 1] : right;
+            const A wv = k > 0 ? cv[k - 1] : left;
+            const A ev = k < VEC - 1 ? cv[k + 1] : right;
             A s = wv + ev;
-            s = s + ym.v[k];
-            s = s + yq.v[k];
-            s = s + zm.v[k];
-            s = s + zq.v[k];
+            s = s + ym[k];
+            s = s + yq[k];
+            s = s + zm[k];
+            s = s + zq[k];
             out[k] = s;
         }
         div6_n(out);
         if (act) {
             if (full) {
-                *reinterpret_cast<typename EL::V *>(yp) = EL::pack(out);
+                *reinterpret_cast<V *>(out_p) = EL::pack(out);
             } else {
 #pragma unroll
                 for (int k = 0; k < VEC; k++)
-                    if (x + k >= t.x0 && x + k < t.x1) EL::store1(yp + k, out[k]);
+                    if (x + k >= t.x0 && x + k < t.x1) EL::store1(out_p + k, out[k]);
             }
         }
-        yp += P.ys0;
+    };
+
+    for (int k = 0; k < L; k += 2) {
+        cpa_wait<NS - 6>();  // entries up to k + 3 have landed (this thread's copies)
+        __syncthreads();     // ... and every other thread's; the stages of k-2 and k-1 are free
+        issue();             // entry k + NS - 2
+        issue();             // entry k + NS - 1
+        A zm[VEC], cv[VEC], zq[VEC];
+        ld(k, 0, zm);
+        ld(k + 1, 0, cv);
+        ld(k + 2, 0, zq);
+        plane(k + 1, cv, zm, zq, yp);  // output plane z0 + k
+        if (k + 1 < L) {               // output plane z0 + k + 1: centre zq, below cv, above entry k+3
+            A zq2[VEC];
+            ld(k + 3, 0, zq2);
+            plane(k + 2, zq, cv, zq2, yp + P.ys0);
+        }
+        yp += 2 * P.ys0;
     }
     cpa_wait<0>();
 }
@@ -226,19 +245,22 @@ cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3
     if (ntiles <= 0) return cudaSuccess;
     if (variant == 1) {
         constexpr int NS = STENCIL3D_STAGES;
+        const int T = warps_per_cta == 16 ? 512 : 256;
         const int slots = (int)(smem / ((size_t)NS * 16));
-        if (slots < 1 || slots > 512 || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
-        const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
+        if (slots < 1 || slots > 2 * T || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
+        const int which = (dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1);
         if (which < 0) return cudaErrorInvalidValue;
         using KFn = void (*)(const StenPart3D *, const StenTile3D *, int, const Seg *);
-        const KFn fns[3] = {k_stencil3d_cta<DT_F64, NS>, k_stencil3d_cta<DT_F32, NS>, k_stencil3d_cta<DT_BF16, NS>};
-        static bool attr[3] = {false, false, false};
-        if (!attr[which]) {
-            cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 512 * 16);
+        const KFn fns[2][3] = {{k_stencil3d_cta<DT_F64, NS, 256>, k_stencil3d_cta<DT_F32, NS, 256>, k_stencil3d_cta<DT_BF16, NS, 256>},
+                               {k_stencil3d_cta<DT_F64, NS, 512>, k_stencil3d_cta<DT_F32, NS, 512>, k_stencil3d_cta<DT_BF16, NS, 512>}};
+        const int wt = T == 512 ? 1 : 0;
+        static bool attr[2][3] = {};
+        if (!attr[wt][which]) {
+            cudaError_t e = cudaFuncSetAttribute(fns[wt][which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 2 * T * 16);
             if (e != cudaSuccess) return e;
-            attr[which] = true;
+            attr[wt][which] = true;
         }
-        fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs);
+        fns[wt][which]<<<ntiles, T, smem, s>>>(parts, tiles, slots, segs);
         return cudaGetLastError();
     }
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 8;

@@ -66,7 +66,7 @@ cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D
 // row y, x in [x0, x1) inside a band of 32 vector chunks starting at xb, marching z over [z0, z1);
 // consecutive tiles are consecutive rows, so the rows y-1 and y+1 a warp reads were just read by
 // its neighbours in the same CTA.  CTA variant: a tile is ny rows x nch chunks from xb (one chunk
-// per thread of a 256-thread CTA), x in [x0, x1), marching z over [z0, z1).
+// per thread of a 256- or 512-thread CTA), x in [x0, x1), marching z over [z0, z1).
 // ------------------------------------------------------------------------------------------
 struct StenPart3D {
     const void *x;
@@ -81,14 +81,15 @@ struct StenTile3D {
     int32_t x0, x1;
     int32_t xb;
     int32_t seg0, nseg;
-    int32_t ny;   // rows: 1 for the per-warp variant, ny * nch <= 256 for the CTA variant
-    int32_t nch;  // 16-byte chunks per row from xb (CTA variant; (ny + 2) * (nch + 2) <= 512)
+    int32_t ny;   // rows: 1 for the per-warp variant, ny * nch <= threads for the CTA variant
+    int32_t nch;  // 16-byte chunks per row from xb (CTA variant; (ny + 2) * (nch + 2) <= 2 * threads)
 };
 // Plane-ring depth of the CTA variant; its dynamic shared memory is
 // STENCIL3D_STAGES * max over tiles of (ny + 2) * (nch + 2) * 16 bytes.
 constexpr int STENCIL3D_STAGES = 8;
 // variant 0: one warp per tile (a row), prefetch in registers (warps_per_cta tiles per CTA);
-// variant 1: one CTA per tile, planes prefetched into shared memory (cp.async), smem bytes as above.
+// variant 1: one CTA of 32 * warps_per_cta threads (8 or 16 warps) per tile, planes prefetched into
+// shared memory (cp.async), smem bytes as above.
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
                              int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
                              cudaStream_t s);

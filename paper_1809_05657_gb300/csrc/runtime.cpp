@@ -81,11 +81,12 @@ struct Ctx {
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
+    int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
     bool tuning = false;  // compile_plan is being called by the tuner
-    struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3; };
+    struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3, cta3; };
     std::map<std::string, Shape> tuned;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
@@ -710,11 +711,11 @@ void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const 
 // Tiles of the fused 3-D kernel for one device, in (z chunk, x band, rows) order; the receive
 // segments are the parts of the incoming faces on the tile's six face strips.  variant 0: bands
 // of 32 chunks, one row per tile; variant 1: the box's chunks cut into bands of equal width of
-// at most band_chunks, as many rows per tile as 256 threads hold; variant 2 (flat_cells > 0):
+// at most band_chunks, as many rows per tile as `threads` threads hold; variant 2 (flat_cells > 0):
 // balanced widths up to 128 elements, rows so that a plane has about flat_cells cells.
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                      const std::vector<Move> &recv, bool want_segs, int variant, Sten3DHost &h,
-                     int flat_cells = 0, int band_chunks = 32)
+                     int flat_cells = 0, int band_chunks = 32, int threads = 256)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart3D P;
@@ -737,12 +738,17 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
     int64_t band = 32 * VEC;
     int rows_per_tile = 1;
     if (variant == 1) {
+        // one chunk per thread; at most 2 * threads staged slots (two copy items per thread), and
+        // at most 704 with 512 threads so that two CTAs' rings fit on an SM; a band of nch chunks
+        // stages at least 3 (nch + 2) slots
+        threads = threads == 512 ? 512 : 256;
+        const int64_t slot_cap = threads == 512 ? 704 : 2 * threads;
         const int64_t chunks = (W.hi[2] - xb0 + VEC - 1) / VEC;
-        const int64_t cap = std::max(1, std::min(band_chunks, 256));
+        const int64_t cap = std::max<int64_t>(1, std::min<int64_t>({(int64_t)band_chunks, (int64_t)threads, slot_cap / 3 - 2}));
         const int64_t nb = (chunks + cap - 1) / cap;
         const int64_t nch = (chunks + nb - 1) / nb;
         band = nch * VEC;
-        rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(256 / nch, 512 / (nch + 2) - 2));
+        rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(threads / nch, slot_cap / (nch + 2) - 2));
         h.smem = std::max(h.smem, (size_t)STENCIL3D_STAGES * (rows_per_tile + 2) * (nch + 2) * 16);
     }
     if (flat_cells > 0) {
@@ -907,7 +913,7 @@ int compile_plan(Plan &pl)
             const bool flat = g->variant3 == 2 && X->dtype != DT_BF16;
             h.flat = flat;
             if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, flat ? 2 : g->variant3, h,
-                                 flat ? g->tile_rows * 64 : 0, g->band3))
+                                 flat ? g->tile_rows * 64 : 0, g->band3, g->cta3))
                 fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -934,7 +940,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         } else {
@@ -945,7 +951,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : 8; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         }
@@ -1240,6 +1246,7 @@ void apply_shape(const Ctx::Shape &s, bool threed)
         g->variant3 = s.variant3;
         g->tile_rows = s.rows;
         g->band3 = s.band3;
+        g->cta3 = s.cta3;
     } else {
         g->variant = s.variant;
         g->tile_rows = s.rows;
@@ -1249,7 +1256,7 @@ void apply_shape(const Ctx::Shape &s, bool threed)
 
 Ctx::Shape current_shape()
 {
-    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3, g->band3};
+    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3, g->band3, g->cta3};
 }
 
 const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
@@ -1263,8 +1270,8 @@ void load_tune_file()
     if (!f) return;
     char key[4096];
     Ctx::Shape s;
-    while (fscanf(f, "%4095s %d %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
-                  &s.variant3, &s.band3) == 8)
+    while (fscanf(f, "%4095s %d %d %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
+                  &s.variant3, &s.band3, &s.cta3) == 9)
         g->tuned[key] = s;
     fclose(f);
 }
@@ -1274,8 +1281,8 @@ void save_tune(const std::string &key, const Ctx::Shape &s)
     if (!tune_file()) return;
     FILE *f = fopen(tune_file(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3,
-            s.band3);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3,
+            s.band3, s.cta3);
     fclose(f);
 }
 
@@ -1337,20 +1344,21 @@ int compile_tuned(Plan &pl)
         for (int fu : {1, 0})
             for (int tz : {16, 32, 64}) {
                 for (int band : {16, 32, 64})
-                    cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band});
+                    for (int cta : {256, 512})
+                        cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band, cta});
                 if (flat_ok)
                     for (int cells : {16, 32})
-                        cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3});
+                        cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3});
             }
     } else {
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
                 for (int rows : {16, 32, 64})
                     for (int w : {4, 8})
-                        cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3});
+                        cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3});
             if (flat_ok)
                 for (int cells : {16, 32, 64})
-                    cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3});
+                    cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3});
         }
     }
     g->tuning = true;
@@ -1372,9 +1380,9 @@ int compile_tuned(Plan &pl)
     g->tuned[key] = best;
     save_tune(key, best);
     if (trace())
-        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d band %d fuse %d (%.1f us)\n",
-                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.band3, best.fuse,
-                best_ms * 1e3);
+        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d band %d cta %d fuse %d (%.1f us)\n",
+                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.band3, best.cta3,
+                best.fuse, best_ms * 1e3);
     return rc;
 }
 
@@ -2054,6 +2062,8 @@ int init_impl(int ndev, unsigned flags)
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
         const char *b3 = getenv("HDARRAY_BAND3");
         if (b3 && atoi(b3) > 0) g->band3 = atoi(b3);
+        const char *c3 = getenv("HDARRAY_CTA3");
+        if (c3 && (atoi(c3) == 256 || atoi(c3) == 512)) g->cta3 = atoi(c3);
     }
     g->inited = true;
     return HDARRAY_OK;

@@ -123,9 +123,9 @@ struct Row {
     typename Elem<DT>::A l, r;
 };
 
-// ZERO: lanes past the band's end hold zeros (their results are not stored, but they take part in
-// the warp's vote on the division path).
-template <int DT, bool ZERO = false>
+// FILL: lanes past the band's end hold ones (their results are not stored, but they take part in
+// the warp's vote on the division path, which a sum of ones keeps on the fast side).
+template <int DT, bool FILL = false>
 __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::E *xrow, int x,
                                          bool act, bool needL, bool needR, int lane)
 {
@@ -133,9 +133,9 @@ __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::
     if (act) {
         typename EL::V v = *reinterpret_cast<const typename EL::V *>(xrow + x);
         EL::unpack(v, row.v);
-    } else if (ZERO) {
+    } else if (FILL) {
 #pragma unroll
-        for (int k = 0; k < EL::VEC; k++) row.v[k] = typename EL::A(0);
+        for (int k = 0; k < EL::VEC; k++) row.v[k] = typename EL::A(1);
     }
     if (lane == 0 && needL) row.l = EL::load1(xrow + x - 1);
     if (lane == 31 && needR) row.r = EL::load1(xrow + x + EL::VEC);
@@ -145,20 +145,19 @@ __device__ __forceinline__ void load_row(Row<DT> &row, const typename Elem<DT>::
 // remainder r = s - q * 6 (exact with one FMA), then q + r * c rounded once -- the correction step
 // for division by a constant known in advance (Brisebarre, Muller & Raina, IEEE Trans. Computers
 // 53(8), 2004).  Checked against IEEE division for every finite binary32 input: identical whenever
-// |s| >= 2^-100.  The sign is copied from s, which is the quotient's sign there and makes the
-// result exact for s = +0 and -0 as well (the bare steps give +0 for -0).  Other tiny sums,
-// infinities (an infinite s gives a NaN remainder) and NaN must take the true division.
+// 2^-100 <= |s|.  Zero, tiny, infinite and NaN sums take the true division instead (the bare steps
+// give +0 for -0 and NaN for an infinity).
 __device__ __forceinline__ float div6_fast(float s)
 {
     const float c = 0x1.555556p-3f;  // RN(1/6)
     const float q = __fmul_rn(s, c);
     const float r = __fmaf_rn(-q, 6.0f, s);
-    return copysignf(__fmaf_rn(r, c, q), s);
+    return __fmaf_rn(r, c, q);
 }
+// 2^-100 <= |s| <= FLT_MAX, as one unsigned range test on the magnitude's bits
 __device__ __forceinline__ bool div6_fast_ok(float s)
 {
-    const float a = fabsf(s);
-    return (a >= 0x1p-100f && a <= 0x1.fffffep127f) || a == 0.0f;  // false for NaN
+    return (__float_as_uint(s) & 0x7fffffffu) - 0x0d800000u <= 0x71ffffffu;
 }
 
 // s[k] / 6 for every k, in place, correctly rounded.  The rare sums outside the fast method's range

@@ -639,13 +639,17 @@ def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     assert np.array_equal(got, orc.arrays[last].G)
 
 
-@pytest.mark.parametrize("band,dtype", [("1", "float"), ("4", "float"), ("16", "float"), ("64", "float"),
-                                        ("3", "bf16"), ("64", "bf16"), ("5", "double"), ("64", "double")])
-def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype):
+@pytest.mark.parametrize("band,dtype,cta", [("1", "float", "256"), ("4", "float", "256"), ("16", "float", "256"),
+                                            ("64", "float", "256"), ("3", "bf16", "256"), ("64", "bf16", "256"),
+                                            ("5", "double", "256"), ("64", "double", "256"), ("1", "float", "512"),
+                                            ("32", "float", "512"), ("512", "float", "512"), ("7", "bf16", "512"),
+                                            ("64", "double", "512")])
+def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype, cta):
     """The CTA kernel's tiles follow the box: narrow bands with many rows, wide bands with few,
-    bands of equal width across a row, ragged last tiles in y and z."""
+    bands of equal width across a row, ragged last tiles in y and z, with 256 or 512 threads."""
     monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", "1")
     monkeypatch.setenv("HDARRAY_BAND3", band)
+    monkeypatch.setenv("HDARRAY_CTA3", cta)
     monkeypatch.setenv("HDARRAY_TILE_Z", "9")
     n = 44
     dims = (n, n, 150)
