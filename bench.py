@@ -153,11 +153,11 @@ def tune_report(path):
     out = []
     for line in open(path):
         w = line.split()
-        if len(w) == 9:
+        if len(w) == 10:
             key = w[0].split(":")
             out.append({"kernel": key[0], "variant": int(w[1]), "rows": int(w[2]), "warps": int(w[3]),
                         "tile_z": int(w[4]), "fused_exchange": int(w[5]), "variant3": int(w[6]),
-                        "band3": int(w[7]), "cta3": int(w[8])})
+                        "band3": int(w[7]), "cta3": int(w[8]), "band2": int(w[9])})
     return out
 
 

@@ -187,10 +187,152 @@ __global__ void __launch_bounds__(256) k_jacobi2d_async(const StenPart2D *__rest
     cpa_wait<0>();
 }
 
+// ------------------------------------------------------------------------------------------
+// Packed-stream variant for partitions of any width: one CTA of 256 threads per tile of a column
+// band of nch 16-byte chunks (nch <= 32) and ns * sl rows, cut into ns streams of sl consecutive
+// rows (ns * nch <= 256, one chunk per thread), all streams marching down their rows in step.  A
+// narrow band (the column partitions of a small instance) so keeps every lane busy with several
+// row streams instead of idling most of a warp.  Entry e of a stream is its row r_s - 1 + e
+// (e = 0 .. len_s + 1; r_s its first row); entry e of every stream -- nch chunks plus one halo chunk
+// on each side, each halo chunk only where the band's output range ends on a chunk boundary -- goes
+// into stage e % NS of a shared-memory ring by cp.async.  A step computes output rows r_s + k and
+// r_s + k + 1 from entries k .. k+3 after refilling the stages of entries k-2, k-1 (free since the
+// barrier of this step) with entries k+NS-2, k+NS-1.  A stage is stage_slots >= ns * (nch + 2)
+// slots of 16 bytes, at most 512.
+// ------------------------------------------------------------------------------------------
+template <int DT, int NS>
+__global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__restrict__ parts,
+                                                        const StenTile2D *__restrict__ tiles, int stage_slots,
+                                                        const Seg *__restrict__ segs)
+{
+    static_assert((NS & (NS - 1)) == 0 && NS >= 6, "ring depth: a power of two, at least 6");
+    using EL = Elem<DT>;
+    using E = typename EL::E;
+    using A = typename EL::A;
+    using V = typename EL::V;
+    constexpr int VEC = EL::VEC;
+    extern __shared__ uint4 smem[];
+    const int lane = threadIdx.x & 31;
+    const StenTile2D t = tiles[blockIdx.x];
+    const StenPart2D P = parts[t.part];
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(smem);
+
+    receive_segments_cta<E>(segs, t.seg0, t.nseg);
+
+    const int nch = t.nch, rw = nch + 2, G = t.ns, SL = t.sl;
+    const int SS = G * rw;                        // 16-byte slots used per stage
+    const bool needL = t.c0 == t.cb;              // c0 - 1 lies in the left halo chunk
+    const bool needR = t.c1 == t.cb + nch * VEC;  // c1 lies in the right halo chunk
+
+    // This thread's copy items: slots j and j + 256 of every entry, (stream, chunk) = divmod(j, rw),
+    // each loaded while its stream has rows left (entries 0 .. len + 1).
+    const int j0 = threadIdx.x, j1 = threadIdx.x + 256;
+    const int s0 = j0 / rw, q0 = j0 - s0 * rw, s1 = j1 / rw, q1 = j1 - s1 * rw;
+    const bool has0 = j0 < SS && (q0 > 0 || needL) && (q0 < rw - 1 || needR);
+    const bool has1 = j1 < SS && (q1 > 0 || needL) && (q1 < rw - 1 || needR);
+    const int last0 = min(SL, t.r1 - t.r0 - s0 * SL) + 1, last1 = min(SL, t.r1 - t.r0 - s1 * SL) + 1;
+    const int64_t xs = P.xs;
+    const E *xrow = reinterpret_cast<const E *>(P.x) + (t.cb - VEC - P.xlo1);  // column of slot 0, row 0
+    const E *src0 = xrow + (int64_t)(t.r0 + s0 * SL - 1 - P.xlo0) * xs + q0 * VEC;
+    const E *src1 = xrow + (int64_t)(t.r0 + s1 * SL - 1 - P.xlo0) * xs + q1 * VEC;
+    const uint32_t stage_bytes = (uint32_t)stage_slots * 16u;
+    int enext = 0;  // next entry to issue
+    auto issue = [&]() {
+        const uint32_t sb = ring_s + (uint32_t)(enext & (NS - 1)) * stage_bytes;
+        if (has0 && enext <= last0) cpa16(sb + (uint32_t)j0 * 16u, src0);
+        if (has1 && enext <= last1) cpa16(sb + (uint32_t)j1 * 16u, src1);
+        src0 += xs;
+        src1 += xs;
+        enext++;
+        cpa_commit();  // one group per entry
+    };
+#pragma unroll 1
+    for (int k = 0; k < NS - 2; k++) issue();  // entries 0 .. NS-3
+
+    // the chunk this thread computes: stream s, chunk c
+    const int s = threadIdx.x / nch, c = threadIdx.x - s * nch;
+    const int x = t.cb + c * VEC;
+    const bool act = s < G;
+    const int len = act ? min(SL, t.r1 - t.r0 - s * SL) : 0;  // output rows of this stream
+    const bool full = x >= t.c0 && x + VEC <= t.c1;
+    const int me = s * rw + c + 1;
+    const bool shflL = c > 0 && lane > 0, shflR = c < nch - 1 && lane < 31;
+    const bool haveL = c > 0 || needL, haveR = c < nch - 1 || needR;
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.r0 + s * SL - P.ylo0) * P.ys + (x - P.ylo1);
+
+    auto ld = [&](int e, A (&v)[VEC]) {  // this thread's chunk of entry e
+        if (act) EL::unpack(*reinterpret_cast<const V *>(smem + (e & (NS - 1)) * stage_slots + me), v);
+    };
+    // one output row: centre cv (entry e), rows above / below up and dn; stored at out_p if `store`
+    auto row = [&](int e, const A (&up)[VEC], const A (&cv)[VEC], const A (&dn)[VEC], E *out_p, bool store) {
+        A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
+        A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
+        const E *sr = reinterpret_cast<const E *>(smem + (e & (NS - 1)) * stage_slots + me);
+        if (!shflL && act && haveL) left = EL::load1(sr - 1);
+        if (!shflR && act && haveR) right = EL::load1(sr + VEC);
+        A out[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const A w = k > 0 ? cv[k - 1] : left;
+            const A ev = k < VEC - 1 ? cv[k + 1] : right;
+            A sum = w + ev;
+            sum = sum + up[k];
+            sum = sum + dn[k];
+            out[k] = sum * A(0.25);
+        }
+        if (store) {
+            if (full) {
+                *reinterpret_cast<V *>(out_p) = EL::pack(out);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; k++)
+                    if (x + k >= t.c0 && x + k < t.c1) EL::store1(out_p + k, out[k]);
+            }
+        }
+    };
+
+    for (int k = 0; k < SL; k += 2) {
+        cpa_wait<NS - 6>();  // entries up to k + 3 have landed (this thread's copies)
+        __syncthreads();     // ... and every other thread's; the stages of k-2 and k-1 are free
+        issue();             // entry k + NS - 2
+        issue();             // entry k + NS - 1
+        A up[VEC], cv[VEC], dn[VEC];
+        ld(k, up);
+        ld(k + 1, cv);
+        ld(k + 2, dn);
+        row(k + 1, up, cv, dn, yp, k < len);  // output row r_s + k
+        if (k + 1 < SL) {                     // output row r_s + k + 1
+            A dn2[VEC];
+            ld(k + 3, dn2);
+            row(k + 2, cv, dn, dn2, yp + P.ys, k + 1 < len);
+        }
+        yp += 2 * P.ys;
+    }
+    cpa_wait<0>();
+}
+
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
-                            int ntiles, const Seg *segs, int warps_per_cta, int variant, cudaStream_t s)
+                            int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
+                            cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (variant == 3) {
+        constexpr int NS = JACOBI2D_STAGES;
+        const int slots = (int)(smem / ((size_t)NS * 16));
+        if (slots < 1 || slots > 512 || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
+        const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
+        if (which < 0) return cudaErrorInvalidValue;
+        using KFn = void (*)(const StenPart2D *, const StenTile2D *, int, const Seg *);
+        const KFn fns[3] = {k_jacobi2d_cta<DT_F64, NS>, k_jacobi2d_cta<DT_F32, NS>, k_jacobi2d_cta<DT_BF16, NS>};
+        static bool attr[3] = {false, false, false};
+        if (!attr[which]) {
+            cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 512 * 16);
+            if (e != cudaSuccess) return e;
+            attr[which] = true;
+        }
+        fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs);
+        return cudaGetLastError();
+    }
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 4;
     const int grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const int block = 32 * warps_per_cta;

@@ -48,6 +48,7 @@ struct StenTile2D {
     int32_t c0, c1;
     int32_t cb;
     int32_t seg0, nseg;
+    int32_t nch, ns, sl;  // packed-stream variant: chunks per row, streams, rows per stream
 };
 struct Seg {  // dst[o * dso + k * ds] = src[o * sso + k * ss], k < n, o < m (element strides)
     const void *src;
@@ -56,9 +57,13 @@ struct Seg {  // dst[o * dso + k * ds] = src[o * sso + k * ss], k < n, o < m (el
     int64_t sso, dso;  // outer strides
     int32_t n, m;
 };
-// variant 0: prefetched rows in registers; variant 1: in shared memory via cp.async.
+// variant 0: a warp per tile, prefetched rows in registers; variant 1: a warp per tile, rows in
+// shared memory via cp.async (warps_per_cta tiles per CTA); variant 3: a CTA per tile of ns row
+// streams x nch chunks, rows in a shared-memory ring of JACOBI2D_STAGES stages of smem / (16 *
+// JACOBI2D_STAGES) >= ns * (nch + 2) slots (at most 512).
+constexpr int JACOBI2D_STAGES = 8;
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
-                            int ntiles, const Seg *segs, int warps_per_cta, int variant,
+                            int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
                             cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------

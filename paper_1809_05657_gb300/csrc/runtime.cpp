@@ -80,13 +80,14 @@ struct Ctx {
     int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
+    int band2 = 32;         // 2-D packed-stream variant: most 16-byte chunks per band
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
     bool tuning = false;  // compile_plan is being called by the tuner
-    struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3, cta3; };
+    struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3, cta3, band2; };
     std::map<std::string, Shape> tuned;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
@@ -548,8 +549,47 @@ std::string epoch_sig(const Plan &pl)
 // Tiles of the fused Jacobi kernel for one device.  Returns false if the device's incoming
 // sections are not exactly the halo strips of its tiles (then the exchange runs as a separate
 // copy launch).
+// Receive segments of a 2-D tile: the parts of the incoming moves on its four face strips.
+void tile2d_segments(const HDArray *X, const DevBuf &bx, StenTile2D &t, const std::vector<Move> &recv,
+                     Sten2DHost &h, int64_t &covered)
+{
+    const Box strips[4] = {
+        make_box(t.r0 - 1, t.c0, 0, t.r0, t.c1, 1), make_box(t.r1, t.c0, 0, t.r1 + 1, t.c1, 1),
+        make_box(t.r0, t.c0 - 1, 0, t.r1, t.c0, 1), make_box(t.r0, t.c1, 0, t.r1, t.c1 + 1, 1)};
+    for (const Move &m : recv) {
+        const DevBuf &src = X->buf[m.src];
+        for (int s = 0; s < 4; s++) {
+            Box I = box_intersect(m.box, strips[s]);
+            if (I.empty()) continue;
+            Seg sg;
+            sg.src = src.ptr + elem_off(src, I.lo) * X->esize;
+            sg.dst = bx.ptr + elem_off(bx, I.lo) * X->esize;
+            if (s < 2) {  // a row run
+                sg.n = (int32_t)(I.hi[1] - I.lo[1]);
+                sg.ss = 1;
+                sg.ds = 1;
+            } else {      // a column run
+                sg.n = (int32_t)(I.hi[0] - I.lo[0]);
+                sg.ss = src.st[0];
+                sg.ds = bx.st[0];
+            }
+            sg.m = 1;
+            sg.sso = 0;
+            sg.dso = 0;
+            covered += I.volume();
+            h.segs.push_back(sg);
+            t.nseg++;
+        }
+    }
+}
+
+// Tiles of the fused 2-D kernel for one device.  Warp variants (0, 1): column bands of 32 chunks
+// x tile_rows rows, a warp each.  Packed-stream variant (3): the box's chunks cut into bands of
+// equal width of at most band_chunks (<= 32); per band, tiles of ns streams x sl rows with
+// ns = min(256 / nch, 512 / (nch + 2)) and sl about tile_rows, balanced over the band's rows.
 bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
-                  const std::vector<Move> &recv, bool want_segs, Sten2DHost &h)
+                  const std::vector<Move> &recv, bool want_segs, Sten2DHost &h, int variant = 1,
+                  int band_chunks = 32)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart2D P;
@@ -562,7 +602,7 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     P.ylo1 = by.alloc.lo[1];
     P.ys = by.st[0];
     h.parts.push_back(P);
-    const int VEC = 16 / X->esize, BAND = 32 * VEC;
+    const int VEC = 16 / X->esize;
     const int H = std::max(1, g->tile_rows);
     bool exact = true;
     int64_t covered = 0, need = 0;
@@ -572,48 +612,53 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     }
     // bands start on 16-byte chunks of X's buffer (Y's buffer has the same phase, checked by the caller)
     const int64_t cb0 = bx.alloc.lo[1] + align_down(W.lo[1] - bx.alloc.lo[1], VEC);
+    auto add = [&](StenTile2D &t) {
+        t.part = part_index;
+        t.seg0 = (int32_t)h.segs.size();
+        t.nseg = 0;
+        if (want_segs && exact) tile2d_segments(X, bx, t, recv, h, covered);
+        h.tiles.push_back(t);
+    };
+    if (variant == 3) {
+        const int64_t chunks = (W.hi[1] - cb0 + VEC - 1) / VEC;
+        const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(band_chunks, 32));
+        const int64_t nb = (chunks + cap - 1) / cap;
+        const int64_t nch = (chunks + nb - 1) / nb;
+        const int64_t G = std::min<int64_t>(256 / nch, 512 / (nch + 2));
+        const int64_t R = W.hi[0] - W.lo[0];
+        const int64_t ntr = (R + G * H - 1) / (G * H);     // tiles down the band
+        const int64_t sl = (R + ntr * G - 1) / (ntr * G);  // balanced stream length
+        h.smem = std::max(h.smem, (size_t)JACOBI2D_STAGES * G * (nch + 2) * 16);
+        for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += G * sl) {
+            for (int64_t b = 0; b < nb; b++) {
+                const int64_t cb = cb0 + b * nch * VEC;
+                StenTile2D t;
+                t.r0 = (int32_t)rb;
+                t.r1 = (int32_t)std::min<int64_t>(rb + G * sl, W.hi[0]);
+                t.c0 = (int32_t)std::max<int64_t>(W.lo[1], cb);
+                t.c1 = (int32_t)std::min<int64_t>(W.hi[1], cb + nch * VEC);
+                t.cb = (int32_t)cb;
+                t.nch = (int32_t)((t.c1 - cb + VEC - 1) / VEC);
+                t.sl = (int32_t)sl;
+                t.ns = (int32_t)((t.r1 - t.r0 + sl - 1) / sl);  // every stream has rows
+                add(t);
+            }
+        }
+        return exact && covered == need;
+    }
+    const int BAND = 32 * VEC;
     for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += H) {
         for (int64_t cb = cb0; cb < W.hi[1]; cb += BAND) {
             StenTile2D t;
-            t.part = part_index;
             t.r0 = (int32_t)rb;
             t.r1 = (int32_t)std::min<int64_t>(rb + H, W.hi[0]);
             t.c0 = (int32_t)std::max<int64_t>(W.lo[1], cb);
             t.c1 = (int32_t)std::min<int64_t>(W.hi[1], cb + BAND);
             t.cb = (int32_t)cb;
-            t.seg0 = (int32_t)h.segs.size();
-            t.nseg = 0;
-            if (want_segs && exact) {
-                const Box strips[4] = {
-                    make_box(t.r0 - 1, t.c0, 0, t.r0, t.c1, 1), make_box(t.r1, t.c0, 0, t.r1 + 1, t.c1, 1),
-                    make_box(t.r0, t.c0 - 1, 0, t.r1, t.c0, 1), make_box(t.r0, t.c1, 0, t.r1, t.c1 + 1, 1)};
-                for (const Move &m : recv) {
-                    const DevBuf &src = X->buf[m.src];
-                    for (int s = 0; s < 4; s++) {
-                        Box I = box_intersect(m.box, strips[s]);
-                        if (I.empty()) continue;
-                        Seg sg;
-                        sg.src = src.ptr + elem_off(src, I.lo) * X->esize;
-                        sg.dst = bx.ptr + elem_off(bx, I.lo) * X->esize;
-                        if (s < 2) {  // a row run
-                            sg.n = (int32_t)(I.hi[1] - I.lo[1]);
-                            sg.ss = 1;
-                            sg.ds = 1;
-                        } else {      // a column run
-                            sg.n = (int32_t)(I.hi[0] - I.lo[0]);
-                            sg.ss = src.st[0];
-                            sg.ds = bx.st[0];
-                        }
-                        sg.m = 1;
-                        sg.sso = 0;
-                        sg.dso = 0;
-                        covered += I.volume();
-                        h.segs.push_back(sg);
-                        t.nseg++;
-                    }
-                }
-            }
-            h.tiles.push_back(t);
+            t.nch = 32;
+            t.ns = 1;
+            t.sl = t.r1 - t.r0;
+            add(t);
         }
     }
     return exact && covered == need;
@@ -645,6 +690,7 @@ bool flat2d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     for (int64_t r = W.lo[0]; r < W.hi[0]; r += br) {
         for (int64_t c = W.lo[1]; c < W.hi[1]; c += bw) {
             StenTile2D t;
+            t.nch = 0; t.ns = 0; t.sl = 0;
             t.part = part_index;
             t.r0 = (int32_t)r;
             t.r1 = (int32_t)std::min<int64_t>(r + br, W.hi[0]);
@@ -842,8 +888,10 @@ int compile_plan(Plan &pl)
             int t0 = (int)h.tiles.size();
             const bool flat = g->variant == 2 && X->dtype != DT_BF16;
             h.flat = flat;
+            h.variant = flat ? 2 : g->variant == 2 ? 1 : g->variant;
+            h.warps = g->warps_per_cta;
             bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
-                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h);
+                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2);
             if (!ok) fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -870,7 +918,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->warps_per_cta; L.n2 = g->variant;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         } else {
@@ -881,7 +929,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->warps_per_cta; L.n2 = g->variant;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         }
@@ -1251,12 +1299,13 @@ void apply_shape(const Ctx::Shape &s, bool threed)
         g->variant = s.variant;
         g->tile_rows = s.rows;
         g->warps_per_cta = s.warps;
+        g->band2 = s.band2;
     }
 }
 
 Ctx::Shape current_shape()
 {
-    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3, g->band3, g->cta3};
+    return Ctx::Shape{g->variant, g->tile_rows, g->warps_per_cta, g->tile_z, g->fuse, g->variant3, g->band3, g->cta3, g->band2};
 }
 
 const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
@@ -1270,8 +1319,8 @@ void load_tune_file()
     if (!f) return;
     char key[4096];
     Ctx::Shape s;
-    while (fscanf(f, "%4095s %d %d %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
-                  &s.variant3, &s.band3, &s.cta3) == 9)
+    while (fscanf(f, "%4095s %d %d %d %d %d %d %d %d %d", key, &s.variant, &s.rows, &s.warps, &s.tile_z, &s.fuse,
+                  &s.variant3, &s.band3, &s.cta3, &s.band2) == 10)
         g->tuned[key] = s;
     fclose(f);
 }
@@ -1281,8 +1330,8 @@ void save_tune(const std::string &key, const Ctx::Shape &s)
     if (!tune_file()) return;
     FILE *f = fopen(tune_file(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse, s.variant3,
-            s.band3, s.cta3);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", key.c_str(), s.variant, s.rows, s.warps, s.tile_z, s.fuse,
+            s.variant3, s.band3, s.cta3, s.band2);
     fclose(f);
 }
 
@@ -1345,20 +1394,27 @@ int compile_tuned(Plan &pl)
             for (int tz : {16, 32, 64}) {
                 for (int band : {16, 32, 64})
                     for (int cta : {256, 512})
-                        cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band, cta});
+                        cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band, cta, saved.band2});
                 if (flat_ok)
                     for (int cells : {16, 32})
-                        cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3});
+                        cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3,
+                                                   saved.band2});
             }
     } else {
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
                 for (int rows : {16, 32, 64})
                     for (int w : {4, 8})
-                        cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3});
+                        cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
+                                                   saved.band2});
+            for (int band : {8, 16, 32})
+                for (int rows : {16, 32, 64})
+                    cands.push_back(Ctx::Shape{3, rows, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
+                                               band});
             if (flat_ok)
                 for (int cells : {16, 32, 64})
-                    cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3});
+                    cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
+                                               saved.band2});
         }
     }
     g->tuning = true;
@@ -1380,9 +1436,9 @@ int compile_tuned(Plan &pl)
     g->tuned[key] = best;
     save_tune(key, best);
     if (trace())
-        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d band %d cta %d fuse %d (%.1f us)\n",
-                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.band3, best.cta3,
-                best.fuse, best_ms * 1e3);
+        fprintf(stderr, "hdarray: tuned %s -> variant %d/%d rows %d warps %d tile_z %d band %d/%d cta %d fuse %d (%.1f us)\n",
+                key.c_str(), best.variant, best.variant3, best.rows, best.warps, best.tile_z, best.band2, best.band3,
+                best.cta3, best.fuse, best_ms * 1e3);
     return rc;
 }
 
@@ -1595,14 +1651,16 @@ int flush_batch()
     if (it == g->batch_cache.end()) {
         // merge: all exchanges first, then every fused 2-D stencil of the same type, then the rest
         std::vector<CopyTask> copies;
-        std::map<std::pair<int, bool>, Sten2DHost> sten;
+        std::map<std::tuple<int, int, int>, Sten2DHost> sten;  // (dtype, variant, warps)
         std::vector<LaunchRec> rest;
         for (auto &p : plans) {
             if (p->k->kind == K_JACOBI2D && g->mode == HDARRAY_MODE_FUSED) {
                 copies.insert(copies.end(), p->copy_host.begin(), p->copy_host.end());
-                Sten2DHost &h = sten[{p->s2.dtype, p->s2.flat}];
+                Sten2DHost &h = sten[std::make_tuple(p->s2.dtype, p->s2.variant, p->s2.warps)];
                 h.dtype = p->s2.dtype;
                 h.flat = p->s2.flat;
+                h.variant = p->s2.variant;
+                h.warps = p->s2.warps;
                 h.smem = std::max(h.smem, p->s2.smem);
                 const int pbase = (int)h.parts.size(), sbase = (int)h.segs.size();
                 h.parts.insert(h.parts.end(), p->s2.parts.begin(), p->s2.parts.end());
@@ -1637,8 +1695,9 @@ int flush_batch()
             LaunchRec L; L.kind = kv.second.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = kv.second.dtype;
             L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2];
             L.n0 = (int64_t)kv.second.tiles.size();
-            L.n1 = kv.second.flat ? (int64_t)kv.second.smem : g->warps_per_cta;
-            L.n2 = g->variant;
+            L.n1 = kv.second.flat ? (int64_t)kv.second.smem : kv.second.warps;
+            L.n2 = kv.second.variant;
+            L.n3 = (int64_t)kv.second.smem;
             ai += 3;
             if (L.n0 > 0) ls.push_back(L);
         }
@@ -2051,7 +2110,9 @@ int init_impl(int ndev, unsigned flags)
         const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
-        if (vv && atoi(vv) >= 0 && atoi(vv) <= 2) g->variant = atoi(vv);
+        if (vv && atoi(vv) >= 0 && atoi(vv) <= 3) g->variant = atoi(vv);
+        const char *b2 = getenv("HDARRAY_BAND2");
+        if (b2 && atoi(b2) > 0) g->band2 = atoi(b2);
         const char *at = getenv("HDARRAY_AUTOTUNE");
         g->autotune = at && atoi(at) != 0;
         const char *fx = getenv("HDARRAY_FUSE_EXCHANGE");
@@ -2084,7 +2145,7 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_COPY: return launch_copy((const CopyTask *)L.p0, (int)L.n0, s);
     case L_JACOBI2D:
         return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
-                               (const Seg *)L.p2, (int)L.n1, (int)L.n2, s);
+                               (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_STENCIL3D:
         return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
                                 (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);

@@ -605,7 +605,11 @@ def test_gemm_bf16x3_reuses_panels(gpu_lib):
                                        ({"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16"}, "float"),
                                        ({"HDARRAY_JACOBI_VARIANT": "2"}, "float"),
                                        ({"HDARRAY_JACOBI_VARIANT": "2", "HDARRAY_TILE_ROWS": "1"}, "double"),
-                                       ({"HDARRAY_JACOBI_VARIANT": "2", "HDARRAY_FUSE_EXCHANGE": "0"}, "float")])
+                                       ({"HDARRAY_JACOBI_VARIANT": "2", "HDARRAY_FUSE_EXCHANGE": "0"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "3"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_BAND2": "3", "HDARRAY_TILE_ROWS": "5"}, "double"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "7"}, "bf16"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_FUSE_EXCHANGE": "0"}, "float")])
 def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -619,6 +623,26 @@ def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env, dtype):
 def test_batch_flat_variant(gpu_lib, monkeypatch):
     monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "2")
     test_batch_of_instances(gpu_lib)
+
+
+def test_batch_packed_variant(gpu_lib, monkeypatch):
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "3")
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", "9")
+    test_batch_of_instances(gpu_lib)
+
+
+@pytest.mark.parametrize("dims,P,ptype,dtype,band", [((150, 70), 7, COL, "float", "32"), ((150, 70), 7, COL, "bf16", "32"),
+                                                     ((300, 45), 11, COL, "double", "32"), ((64, 900), 9, ROW, "float", "8"),
+                                                     ((97, 131), 16, COL, "float", "2")])
+def test_jacobi2d_packed_narrow(gpu_lib, monkeypatch, dims, P, ptype, dtype, band):
+    """Packed row streams on partitions a few elements wide or a few rows high."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "3")
+    monkeypatch.setenv("HDARRAY_BAND2", band)
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", "6")
+    x = synthetic.jacobi_field(dims, stream=87, dtype=dtype)
+    prog, last = jacobi_prog(dims, P, 5, ptype, dtype, True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, dtype), orc.arrays[last].G)
 
 
 @pytest.mark.parametrize("env,dtype", [({"HDARRAY_FUSE_EXCHANGE": "0"}, "float"), ({"HDARRAY_AUTOTUNE": "1"}, "float"),
