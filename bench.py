@@ -46,9 +46,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, or None when the
-    kernel source changed since the capture."""
+def profiled_traffic(variant):
+    """DRAM bytes per launch of the fused kernel variant `variant` from the committed ncu summary,
+    or None when the kernel source changed since the capture or the variant was not captured."""
     try:
         txt = open(PROFILE).read()
         sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
@@ -59,9 +59,26 @@ def profiled_traffic():
                 vals[k.strip()] = v.strip()
         if vals.get("kernel_source_sha256_16") != sha:
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_launch_v%d" % variant])
     except Exception:
         return None
+
+
+KERNEL_NAMES_2D = {0: "k_jacobi2d<f32,6> (register ring)", 1: "k_jacobi2d_async<f32,8> (cp.async ring)",
+                   2: "k_jacobi2d_flat<f32>", 3: "k_jacobi2d_cta<f32,8> (packed row streams)"}
+
+
+def jacobi_variant(tuned):
+    """The 2-D kernel variant the default workload ran: the tuner's choice, else the environment's
+    or the library default."""
+    for t in tuned or []:
+        if t.get("kernel") == "jacobi2d":
+            return int(t["variant"])
+    try:
+        v = int(os.environ.get("HDARRAY_JACOBI_VARIANT", "1"))
+        return v if v in KERNEL_NAMES_2D else 1
+    except ValueError:
+        return 1
 
 
 class ClockSampler:
@@ -660,7 +677,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     if rank == 0:
-        traffic = profiled_traffic()
+        variant = jacobi_variant(r["tuned"])
+        traffic = profiled_traffic(variant)
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
@@ -669,7 +687,7 @@ def main():
             "config": {"workload": WORKLOAD, "grid": [N, N], "logical_devices": P,
                        "iterations_per_step": ITERS, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs 2 x 268 MB > 129 MB L2 (no flush)"},
-            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d<f32> (fused exchange + stencil)",
+            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES_2D[variant] + ", fused exchange + stencil",
                          "achieved": r["achieved"], "peak": r["hbm"], "unit": "GB/s",
                          "frac": r["achieved"] / r["hbm"], "peak_source": r["src"],
                          "traffic": traffic, "algo_bytes_per_launch": r["algo_bytes"],
