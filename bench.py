@@ -470,6 +470,43 @@ def workload_stencil3d(H, torch, stream, args):
                          "algo_bytes_per_launch": algo}}
 
 
+def workload_conv2d(H, torch, stream, args):
+    """The 2-D convolution of Sec. 5 (eight neighbours and the centre, seeded weights) on the
+    8192^2 binary32 grid, BLOCK 4 x 4; no dependency between iterations, so the halo moves once."""
+    import numpy as np
+    import synthetic
+    N, P, iters = args.grid, 16, 100
+    x = synthetic.jacobi_field((N, N), stream=6, dtype="float")
+    w = [float(v) for v in synthetic.normal(9, stream=6)]
+    H.HDArrayInit(ndev=P)
+    H.HDArraySetStream(stream.cuda_stream)
+    X = H.HDArrayCreate("X", "float", None, N, N)
+    Y = H.HDArrayCreate("Y", "float", None, N, N)
+    D = H.HDArrayPartition(H.BLOCK, (N, N), (0, 0), (N, N), P)
+    W = H.HDArrayPartition(H.BLOCK, (N, N), (1, 1), (N - 1, N - 1), P)
+    H.HDArrayWrite(X, torch.from_numpy(x).pin_memory(), D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("conv2d", W, X, Y, *w)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("conv2d", W, X, Y, *w)
+    H.HDArrayApplyKernel("conv2d", W, X, Y, *w)
+    gid = H.HDArrayGraphEnd()
+    for _ in range(args.warmup):
+        H.HDArrayGraphLaunch(gid, iters // 2)
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
+    cells = (N - 2) * (N - 2)
+    per = ms / iters
+    hbm, src = peaks()
+    H.HDArrayExit()
+    return {"workload": "2-D convolution (3 x 3 weights) %d^2 FP32, BLOCK 4x4 = 16 logical devices, "
+                        "%d iterations per step" % (N, iters),
+            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9,
+            "ms_per_step": ms, "us_per_iter": per * 1e3,
+            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d_cta<f32,8,OP_CONV> (packed row streams)",
+                         "achieved": cells * 8 / (per * 1e-3) / 1e9, "peak": hbm,
+                         "frac": cells * 8 / (per * 1e-3) / 1e9 / hbm, "peak_source": src}}
+
+
 def workload_batch(H, torch, stream, args):
     import numpy as np
     import synthetic
@@ -627,7 +664,8 @@ def run_workload(args):
     build_library()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm}[args.workload]
+    fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
+          "conv2d": workload_conv2d}[args.workload]
     tpath = tune_setup(args)
     out = fn(H, torch, stream, args)
     out["autotuned"] = tune_report(tpath)
@@ -652,7 +690,7 @@ def main():
     ap.add_argument("--nb3", type=int, default=37, help="3-D workload: number of boxes (1 = one box)")
     ap.add_argument("--ninst", type=int, default=512, help="batch workload: number of instances")
     ap.add_argument("--workload", default="jacobi2d",
-                    choices=["jacobi2d", "stencil3d", "batch", "trmm"],
+                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d"],
                     help="jacobi2d is the benchmark line; the others print their own line")
     args = ap.parse_args()
     global N, CELLS

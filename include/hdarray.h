@@ -115,6 +115,9 @@ int HDArrayPartition(PART_T type, int dim, ...);
  *   "jacobi2d"  (HDArray_t *X, HDArray_t *Y)               Y = 4-neighbour mean of X (Sec. 5)
  *   "copy"      (HDArray_t *X, HDArray_t *Y)               Y = X          (Sec. 5, kernel 2)
  *   "stencil3d" (HDArray_t *X, HDArray_t *Y)               Y = 6-neighbour mean of X (3-D)
+ *   "conv2d"    (HDArray_t *X, HDArray_t *Y, double w0 .. w8)  Y = 3 x 3 convolution of X
+ *               (Sec. 5, eight neighbours): Y[i][j] = sum_{a,b=0..2} w[3a+b] X[i+a-1][j+b-1],
+ *               summed in that order, each product rounded, in X's arithmetic precision
  *   "sqdiff"    (HDArray_t *X, HDArray_t *Y, HDArray_t *R) R = (X - Y)^2 in double
  *   "gemm"      (A, B, C, double alpha, double beta, int ni, int nj, int nk)   (Listing 3)
  *   "trmm"      (A, B, C, double alpha, double beta)       the same with A lower triangular

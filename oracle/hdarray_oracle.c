@@ -426,6 +426,45 @@ int orc_jacobi2d(int prec, int64_t n0, int64_t n1, const void *B, void *A, const
     return 0;
 }
 
+/* 2-D convolution (Sec. 5: the Jacobi pattern plus the four diagonal neighbours, no dependency
+ * between iterations).  The paper prints no coefficients, so the nine weights are arguments:
+ *   A[i][j] = sum over a, b in 0..2 of w[3a + b] * B[i+a-1][j+b-1],
+ * accumulated in that order starting from the first product, every product and sum rounded to
+ * the arithmetic precision (binary64, or binary32 for float and bfloat16 storage, the weights
+ * rounded to it first; bfloat16 results rounded to nearest even on the store).
+ * Returns -1 if a work element lacks a neighbour inside the array. */
+int orc_conv2d(int prec, int64_t n0, int64_t n1, const void *B, void *A, const uint8_t *work, const double *w)
+{
+    for (int64_t i = 0; i < n0; i++)
+        for (int64_t j = 0; j < n1; j++)
+            if (work[i * n1 + j] && (i == 0 || j == 0 || i == n0 - 1 || j == n1 - 1)) return -1;
+    float wf[9];
+    for (int k = 0; k < 9; k++) wf[k] = (float)w[k];
+    for (int64_t i = 1; i + 1 < n0; i++) {
+        for (int64_t j = 1; j + 1 < n1; j++) {
+            const int64_t c = i * n1 + j;
+            if (!work[c]) continue;
+            if (prec == 0) {
+                const double *b = (const double *)B;
+                double s = w[0] * b[c - n1 - 1];
+                for (int k = 1; k < 9; k++) s = s + w[k] * b[c + (k / 3 - 1) * n1 + (k % 3 - 1)];
+                ((double *)A)[c] = s;
+            } else if (prec == 1) {
+                const float *b = (const float *)B;
+                float s = wf[0] * b[c - n1 - 1];
+                for (int k = 1; k < 9; k++) s = s + wf[k] * b[c + (k / 3 - 1) * n1 + (k % 3 - 1)];
+                ((float *)A)[c] = s;
+            } else {
+                const uint16_t *b = (const uint16_t *)B;
+                float s = wf[0] * orc_bf16_to_f32(b[c - n1 - 1]);
+                for (int k = 1; k < 9; k++) s = s + wf[k] * orc_bf16_to_f32(b[c + (k / 3 - 1) * n1 + (k % 3 - 1)]);
+                ((uint16_t *)A)[c] = orc_f32_to_bf16(s);
+            }
+        }
+    }
+    return 0;
+}
+
 /* 3-D 7-point analogue of the Jacobi step: the mean of the six face neighbours,
  * summed in the order x-1, x+1, y-1, y+1, z-1, z+1 (x = dimension 2, innermost; z = dimension 0),
  * then divided by 6 with one correctly rounded division. */

@@ -59,6 +59,7 @@ def lib():
             "orc_bf16_to_f32_array": (None, [i64, P, P]),
             "orc_jacobi2d": (i32, [i32, i64, i64, P, P, P]),
             "orc_stencil3d": (i32, [i32, i64, i64, i64, P, P, P]),
+            "orc_conv2d": (i32, [i32, i64, i64, P, P, P, P]),
             "orc_copy": (None, [i32, i64, P, P, P]),
             "orc_sqdiff": (None, [i32, i64, P, P, P, P]),
             "orc_gemm": (None, [i64, i64, i64, ctypes.c_double, ctypes.c_double, P, P, P, P]),
@@ -171,6 +172,16 @@ def _run_jacobi2d(o, arrs, work, scal):
         raise ValueError("jacobi2d: work element on the array border")
 
 
+def _run_conv2d(o, arrs, work, scal):
+    X, Y = arrs
+    w = np.ascontiguousarray(np.array(scal, dtype=np.float64))
+    if w.size != 9:
+        raise ValueError("conv2d: nine weights")
+    rc = lib().orc_conv2d(X.prec, X.dims[0], X.dims[1], _p(X.G), _p(Y.G), _p(work), _p(w))
+    if rc != 0:
+        raise ValueError("conv2d: work element on the array border")
+
+
 def _run_stencil3d(o, arrs, work, scal):
     X, Y = arrs
     rc = lib().orc_stencil3d(X.prec, X.dims[0], X.dims[1], X.dims[2], _p(X.G), _p(Y.G), _p(work))
@@ -226,8 +237,9 @@ KERNELS = {
     "trmm": KernelSpec(3, {0: [(0, ALL)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_gemm, nscal=2),
     # The communication step alone (use at zero offsets or absolute sections, no definition).
     "exchange": KernelSpec(1, {0: [(0, 0, 0)]}, {}, None),
-    # Sec. 5, 2-D convolution: the Jacobi offsets plus the four diagonals (sets only).
-    "conv2d": KernelSpec(2, {0: _C2 + [(0, 0)]}, {1: [(0, 0)]}, None),
+    # Sec. 5, 2-D convolution: the Jacobi offsets plus the four diagonals and the centre, nine
+    # weights as scalars.  Arguments (X, Y, w0 .. w8).
+    "conv2d": KernelSpec(2, {0: _C2 + [(0, 0)]}, {1: [(0, 0)]}, _run_conv2d, nscal=9),
 }
 
 

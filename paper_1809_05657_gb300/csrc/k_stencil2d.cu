@@ -199,11 +199,32 @@ __global__ void __launch_bounds__(256) k_jacobi2d_async(const StenPart2D *__rest
 // r_s + k + 1 from entries k .. k+3 after refilling the stages of entries k-2, k-1 (free since the
 // barrier of this step) with entries k+NS-2, k+NS-1.  A stage is stage_slots >= ns * (nch + 2)
 // slots of 16 bytes, at most 512.
+//
+// OP selects the point operation on the 3 x 3 neighbourhood: OP_JACOBI, the Jacobi step above;
+// OP_CONV, the 2-D convolution of Sec. 5 (eight neighbours and the centre) with the weights w[9]:
+//   Y[i][j] = sum over a, b in 0..2 of w[3a + b] * X[i+a-1][j+b-1],
+// accumulated in that row-major order, each product rounded (no fused multiply-add), in the
+// arithmetic precision (binary32 for bfloat16 storage; weights rounded to it).
 // ------------------------------------------------------------------------------------------
-template <int DT, int NS>
+constexpr int OP_JACOBI = 0, OP_CONV = 1;
+
+template <typename A>
+__device__ __forceinline__ A mul_rn(A a, A b);
+template <>
+__device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename A>
+__device__ __forceinline__ A add_rn(A a, A b);
+template <>
+__device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+template <>
+__device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+
+template <int DT, int NS, int OP>
 __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__restrict__ parts,
                                                         const StenTile2D *__restrict__ tiles, int stage_slots,
-                                                        const Seg *__restrict__ segs)
+                                                        const Seg *__restrict__ segs, const double *__restrict__ wts)
 {
     static_assert((NS & (NS - 1)) == 0 && NS >= 6, "ring depth: a power of two, at least 6");
     using EL = Elem<DT>;
@@ -216,6 +237,9 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
     const StenTile2D t = tiles[blockIdx.x];
     const StenPart2D P = parts[t.part];
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(smem);
+    A w[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) w[k] = OP == OP_CONV ? (A)wts[k] : A(0);
 
     receive_segments_cta<E>(segs, t.seg0, t.nseg);
 
@@ -263,22 +287,49 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
     auto ld = [&](int e, A (&v)[VEC]) {  // this thread's chunk of entry e
         if (act) EL::unpack(*reinterpret_cast<const V *>(smem + (e & (NS - 1)) * stage_slots + me), v);
     };
-    // one output row: centre cv (entry e), rows above / below up and dn; stored at out_p if `store`
-    auto row = [&](int e, const A (&up)[VEC], const A (&cv)[VEC], const A (&dn)[VEC], E *out_p, bool store) {
-        A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
-        A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
+    // the elements left and right of this thread's chunk of entry e (v holds the chunk)
+    auto ends = [&](int e, const A (&v)[VEC], A &left, A &right) {
+        left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
+        right = __shfl_down_sync(0xffffffffu, v[0], 1);
         const E *sr = reinterpret_cast<const E *>(smem + (e & (NS - 1)) * stage_slots + me);
         if (!shflL && act && haveL) left = EL::load1(sr - 1);
         if (!shflR && act && haveR) right = EL::load1(sr + VEC);
+    };
+    // one output row from the entries e-1, e, e+1 (rows above, centre, below); stored at out_p
+    auto row = [&](int e, const A (&up)[VEC], const A (&cv)[VEC], const A (&dn)[VEC], E *out_p, bool store) {
         A out[VEC];
+        A cl, cr;
+        ends(e, cv, cl, cr);
+        if (OP == OP_JACOBI) {
 #pragma unroll
-        for (int k = 0; k < VEC; k++) {
-            const A w = k > 0 ? cv[k - 1] : left;
-            const A ev = k < VEC - 1 ? cv[k + 1] : right;
-            A sum = w + ev;
-            sum = sum + up[k];
-            sum = sum + dn[k];
-            out[k] = sum * A(0.25);
+            for (int k = 0; k < VEC; k++) {
+                const A wv = k > 0 ? cv[k - 1] : cl;
+                const A ev = k < VEC - 1 ? cv[k + 1] : cr;
+                A sum = wv + ev;
+                sum = sum + up[k];
+                sum = sum + dn[k];
+                out[k] = sum * A(0.25);
+            }
+        } else {
+            A ul, ur, dl, dr;
+            ends(e - 1, up, ul, ur);
+            ends(e + 1, dn, dl, dr);
+#pragma unroll
+            for (int k = 0; k < VEC; k++) {
+                const A r0[3] = {k > 0 ? up[k - 1] : ul, up[k], k < VEC - 1 ? up[k + 1] : ur};
+                const A r1[3] = {k > 0 ? cv[k - 1] : cl, cv[k], k < VEC - 1 ? cv[k + 1] : cr};
+                const A r2[3] = {k > 0 ? dn[k - 1] : dl, dn[k], k < VEC - 1 ? dn[k + 1] : dr};
+                A sum = mul_rn(w[0], r0[0]);
+                sum = add_rn(sum, mul_rn(w[1], r0[1]));
+                sum = add_rn(sum, mul_rn(w[2], r0[2]));
+                sum = add_rn(sum, mul_rn(w[3], r1[0]));
+                sum = add_rn(sum, mul_rn(w[4], r1[1]));
+                sum = add_rn(sum, mul_rn(w[5], r1[2]));
+                sum = add_rn(sum, mul_rn(w[6], r2[0]));
+                sum = add_rn(sum, mul_rn(w[7], r2[1]));
+                sum = add_rn(sum, mul_rn(w[8], r2[2]));
+                out[k] = sum;
+            }
         }
         if (store) {
             if (full) {
@@ -311,28 +362,36 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
     cpa_wait<0>();
 }
 
+cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                 const Seg *segs, const double *weights, size_t smem, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    constexpr int NS = JACOBI2D_STAGES;
+    const int slots = (int)(smem / ((size_t)NS * 16));
+    if (slots < 1 || slots > 512 || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
+    const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
+    if (which < 0 || (op != OP_JACOBI && op != OP_CONV) || (op == OP_CONV && !weights)) return cudaErrorInvalidValue;
+    using KFn = void (*)(const StenPart2D *, const StenTile2D *, int, const Seg *, const double *);
+    const KFn fns[2][3] = {{k_jacobi2d_cta<DT_F64, NS, OP_JACOBI>, k_jacobi2d_cta<DT_F32, NS, OP_JACOBI>,
+                            k_jacobi2d_cta<DT_BF16, NS, OP_JACOBI>},
+                           {k_jacobi2d_cta<DT_F64, NS, OP_CONV>, k_jacobi2d_cta<DT_F32, NS, OP_CONV>,
+                            k_jacobi2d_cta<DT_BF16, NS, OP_CONV>}};
+    static bool attr[2][3] = {};
+    if (!attr[op][which]) {
+        cudaError_t e = cudaFuncSetAttribute(fns[op][which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 512 * 16);
+        if (e != cudaSuccess) return e;
+        attr[op][which] = true;
+    }
+    fns[op][which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs, weights);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
                             int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
                             cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    if (variant == 3) {
-        constexpr int NS = JACOBI2D_STAGES;
-        const int slots = (int)(smem / ((size_t)NS * 16));
-        if (slots < 1 || slots > 512 || smem != (size_t)NS * slots * 16) return cudaErrorInvalidValue;
-        const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
-        if (which < 0) return cudaErrorInvalidValue;
-        using KFn = void (*)(const StenPart2D *, const StenTile2D *, int, const Seg *);
-        const KFn fns[3] = {k_jacobi2d_cta<DT_F64, NS>, k_jacobi2d_cta<DT_F32, NS>, k_jacobi2d_cta<DT_BF16, NS>};
-        static bool attr[3] = {false, false, false};
-        if (!attr[which]) {
-            cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, NS * 512 * 16);
-            if (e != cudaSuccess) return e;
-            attr[which] = true;
-        }
-        fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs);
-        return cudaGetLastError();
-    }
+    if (variant == 3) return launch_stencil2d_cta(OP_JACOBI, dtype, parts, tiles, ntiles, segs, nullptr, smem, s);
     if (warps_per_cta < 1 || warps_per_cta > 8) warps_per_cta = 4;
     const int grid = (ntiles + warps_per_cta - 1) / warps_per_cta;
     const int block = 32 * warps_per_cta;

@@ -65,6 +65,11 @@ constexpr int JACOBI2D_STAGES = 8;
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
                             int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
                             cudaStream_t s);
+// The packed-stream kernel with a chosen point operation: op 0 the Jacobi step, op 1 the 3 x 3
+// convolution with weights[9] (device memory, binary64, row-major over the offsets
+// (-1,-1) (-1,0) (-1,1) (0,-1) ... (1,1)).
+cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                 const Seg *segs, const double *weights, size_t smem, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // 3-D 7-point step, fused with the exchange.  Per-warp variant: a tile is one warp's job, output

@@ -147,6 +147,17 @@ void register_builtins(Ctx &c)
         k.def = {{}, {off(0, 0, 0)}};
         add(k);
     }
+    {   // Sec. 5, 2-D convolution: use A at the eight neighbours and the centre, define B at (0,0);
+        // scalars: the nine weights, row-major over the offsets (-1,-1) .. (1,1)
+        KernelDef k;
+        k.name = "conv2d"; k.kind = K_CONV2D; k.narr = 2; k.nscal_f = 9; k.space = 1;
+        std::vector<Offset> u;
+        for (int a = -1; a <= 1; a++)
+            for (int b = -1; b <= 1; b++) u.push_back(off(a, b, 0));
+        k.use = {u, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
     {   // 3-D 7-point analogue of Jacobi kernel 1
         KernelDef k;
         k.name = "stencil3d"; k.kind = K_STENCIL3D; k.narr = 2; k.space = 1;
@@ -550,11 +561,15 @@ std::string epoch_sig(const Plan &pl)
 // sections are not exactly the halo strips of its tiles (then the exchange runs as a separate
 // copy launch).
 // Receive segments of a 2-D tile: the parts of the incoming moves on its four face strips.
+// With `corners` the row strips extend one column past each end (the diagonal neighbours of a
+// 3 x 3 operation); a corner cell then lies in the strips of up to three tiles, each of which
+// copies it (the same bits) before reading it.
 void tile2d_segments(const HDArray *X, const DevBuf &bx, StenTile2D &t, const std::vector<Move> &recv,
-                     Sten2DHost &h, int64_t &covered)
+                     Sten2DHost &h, int64_t &covered, bool corners = false)
 {
+    const int e = corners ? 1 : 0;
     const Box strips[4] = {
-        make_box(t.r0 - 1, t.c0, 0, t.r0, t.c1, 1), make_box(t.r1, t.c0, 0, t.r1 + 1, t.c1, 1),
+        make_box(t.r0 - 1, t.c0 - e, 0, t.r0, t.c1 + e, 1), make_box(t.r1, t.c0 - e, 0, t.r1 + 1, t.c1 + e, 1),
         make_box(t.r0, t.c0 - 1, 0, t.r1, t.c0, 1), make_box(t.r0, t.c1, 0, t.r1, t.c1 + 1, 1)};
     for (const Move &m : recv) {
         const DevBuf &src = X->buf[m.src];
@@ -589,7 +604,7 @@ void tile2d_segments(const HDArray *X, const DevBuf &bx, StenTile2D &t, const st
 // ns = min(256 / nch, 512 / (nch + 2)) and sl about tile_rows, balanced over the band's rows.
 bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                   const std::vector<Move> &recv, bool want_segs, Sten2DHost &h, int variant = 1,
-                  int band_chunks = 32)
+                  int band_chunks = 32, bool corners = false)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
     StenPart2D P;
@@ -616,9 +631,12 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
         t.part = part_index;
         t.seg0 = (int32_t)h.segs.size();
         t.nseg = 0;
-        if (want_segs && exact) tile2d_segments(X, bx, t, recv, h, covered);
+        if (want_segs && exact) tile2d_segments(X, bx, t, recv, h, covered, corners);
         h.tiles.push_back(t);
     };
+    // with corners every move outside W lies in the 1-ring of W, which the tiles' strips cover
+    // (some cells more than once), so the fused form is exact iff no move reaches into W
+    auto result = [&]() { return exact && (corners || covered == need); };
     if (variant == 3) {
         const int64_t chunks = (W.hi[1] - cb0 + VEC - 1) / VEC;
         const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(band_chunks, 32));
@@ -644,7 +662,7 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
                 add(t);
             }
         }
-        return exact && covered == need;
+        return result();
     }
     const int BAND = 32 * VEC;
     for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += H) {
@@ -661,7 +679,7 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
             add(t);
         }
     }
-    return exact && covered == need;
+    return result();
 }
 
 void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const Box &I, std::vector<Seg> &out);
@@ -867,7 +885,8 @@ int compile_plan(Plan &pl)
         }
     };
 
-    if (k.kind == K_JACOBI2D) {
+    if (k.kind == K_JACOBI2D || k.kind == K_CONV2D) {
+        const bool conv = k.kind == K_CONV2D;  // always the packed-stream kernel
         HDArray *X = pl.args[0], *Y = pl.args[1];
         const ArrStep *sx = nullptr;
         for (const ArrStep &st : pl.steps)
@@ -886,12 +905,12 @@ int compile_plan(Plan &pl)
                 for (const Move &m : sx->moves)
                     if (m.dst == p) recv.push_back(m);
             int t0 = (int)h.tiles.size();
-            const bool flat = g->variant == 2 && X->dtype != DT_BF16;
+            const bool flat = !conv && g->variant == 2 && X->dtype != DT_BF16;
             h.flat = flat;
-            h.variant = flat ? 2 : g->variant == 2 ? 1 : g->variant;
+            h.variant = conv ? 3 : flat ? 2 : g->variant == 2 ? 1 : g->variant;
             h.warps = g->warps_per_cta;
             bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
-                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2);
+                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2, conv);
             if (!ok) fused = false;
             dev_ranges.push_back({t0, (int)h.tiles.size()});
         }
@@ -904,10 +923,14 @@ int compile_plan(Plan &pl)
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart2D)});
         blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile2D)});
         blobs.push_back({h.segs.data(), h.segs.size() * sizeof(Seg)});
+        double wts[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 9 && conv; i++) wts[i] = i < (int)pl.scal.size() ? pl.scal[i] : 0.0;
+        blobs.push_back({wts, conv ? sizeof(wts) : 0});
         std::vector<const char *> addr;
         int rc = upload(blobs, pl.tables, addr);
         if (rc) return rc;
         const CopyTask *dx = (const CopyTask *)addr[0];
+        const int kind2d = conv ? L_CONV2D : h.flat ? L_FLAT2D : L_JACOBI2D;
         if (plain) {
             for (auto &gr : xfer_groups)
                 if (gr.second > gr.first) {
@@ -916,7 +939,7 @@ int compile_plan(Plan &pl)
                 }
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
-                LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
                 L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
@@ -927,7 +950,7 @@ int compile_plan(Plan &pl)
                 pl.launches.push_back(L);
             }
             if (!h.tiles.empty()) {
-                LaunchRec L; L.kind = h.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = X->dtype;
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
                 L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
@@ -1370,7 +1393,7 @@ int compile_plan(Plan &pl);
 // Y from an unchanged X and copies the same halo values again.
 int compile_tuned(Plan &pl)
 {
-    const bool stencil = pl.k->kind == K_JACOBI2D || pl.k->kind == K_STENCIL3D;
+    const bool stencil = pl.k->kind == K_JACOBI2D || pl.k->kind == K_STENCIL3D || pl.k->kind == K_CONV2D;
     if (!stencil || !g->autotune || g->recording || g->batching || g->tuning) return compile_plan(pl);
     const bool threed = pl.k->kind == K_STENCIL3D;
     load_tune_file();
@@ -1400,6 +1423,12 @@ int compile_tuned(Plan &pl)
                         cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3,
                                                    saved.band2});
             }
+    } else if (pl.k->kind == K_CONV2D) {  // the packed-stream kernel only
+        for (int fu : {1, 0})
+            for (int band : {8, 16, 32})
+                for (int rows : {16, 32, 64})
+                    cands.push_back(Ctx::Shape{saved.variant, rows, saved.warps, saved.tile_z, fu, saved.variant3,
+                                               saved.band3, saved.cta3, band});
     } else {
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
@@ -1459,9 +1488,10 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
     };
     switch (k.kind) {
     case K_JACOBI2D:
+    case K_CONV2D:
     case K_STENCIL3D:
         if (a[0] == a[1] || !same(a[0], a[1]) || a[0]->dtype != a[1]->dtype) return HDARRAY_ERR_INVAL;
-        if (a[0]->dim != (k.kind == K_JACOBI2D ? 2 : 3)) return HDARRAY_ERR_INVAL;
+        if (a[0]->dim != (k.kind == K_STENCIL3D ? 3 : 2)) return HDARRAY_ERR_INVAL;
         for (int p = 0; p < pt.nparts; p++) {  // every work element needs all its neighbours
             const Box &w = pt.box[p];
             if (w.empty()) continue;
@@ -2156,6 +2186,9 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
         return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
                               (unsigned *)L.p2, s);
     case L_SPLIT: return launch_split_panels((const SplitJob *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_CONV2D:
+        return launch_stencil2d_cta(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                                    (const Seg *)L.p2, (const double *)L.p3, (size_t)L.n3, s);
     case L_FLAT2D:
         return launch_jacobi2d_flat(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                     (const Seg *)L.p2, (size_t)L.n1, s);

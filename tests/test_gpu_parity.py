@@ -717,3 +717,82 @@ def test_stencil3d_special_values(gpu_lib, monkeypatch, variant):
     assert np.array_equal(np.isnan(got), np.isnan(want))
     ok = ~np.isnan(want)
     assert np.array_equal(got[ok].view(np.uint32), want[ok].view(np.uint32))
+
+
+# ---------------------------------------------------------------------------------------------
+# 2-D convolution (Sec. 5: eight neighbours and the centre, weights as scalars)
+# ---------------------------------------------------------------------------------------------
+
+def conv_prog(dims, P, ptype, dtype, w):
+    prog = [("create", "X", dtype, dims), ("create", "Y", dtype, dims),
+            ("part", "D", ptype, dims, (0, 0), dims, P),
+            ("part", "W", ptype, dims, (1, 1), tuple(n - 1 for n in dims), P),
+            ("write", "X", "D"), ("write", "Y", "D")]
+    # X -> Y, then Y -> X (moves Y's halo rows, columns and corners), then X -> Y with X unchanged
+    for src, dst in (("X", "Y"), ("Y", "X"), ("X", "Y"), ("X", "Y")):
+        prog.append(("apply", "conv2d", "W", [src, dst], list(w)))
+    return prog
+
+
+CONV_CASES = [((130, 301), 4, BLOCK, "float"), ((97, 131), 3, ROW, "double"), ((140, 270), 5, COL, "bf16"),
+              ((70, 600), 2, ROW, "bf16"), ((150, 70), 7, COL, "float"), ((259, 515), 6, BLOCK, "double")]
+
+
+@pytest.mark.parametrize("dims,P,ptype,dtype", CONV_CASES)
+@pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
+def test_conv2d_parity(gpu_lib, dims, P, ptype, dtype, mode):
+    x = synthetic.jacobi_field(dims, stream=94, dtype=dtype)
+    w = synthetic.normal(9, stream=95) * 0.3
+    lib, orc, *_ = run_program(conv_prog(dims, P, ptype, dtype, w), P, {"X": x, "Y": x}, gpu_lib, mode=mode)
+    for name in ("X", "Y"):
+        assert np.array_equal(read_all(lib, name, dims, dtype), orc.arrays[name].G)
+
+
+@pytest.mark.parametrize("env", [{"HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "3"}, {"HDARRAY_BAND2": "3"},
+                                 {"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
+                                 {"HDARRAY_BAND2": "32", "HDARRAY_TILE_ROWS": "64"}])
+def test_conv2d_execution_choices(gpu_lib, monkeypatch, env):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    dims, P = (203, 389), 6
+    x = synthetic.jacobi_field(dims, stream=96, dtype="float")
+    w = synthetic.normal(9, stream=97)
+    lib, orc, *_ = run_program(conv_prog(dims, P, BLOCK, "float", w), P, {"X": x, "Y": x}, gpu_lib)
+    for name in ("X", "Y"):
+        assert np.array_equal(read_all(lib, name, dims, "float"), orc.arrays[name].G)
+
+
+def test_conv2d_full_size_8192_block16(gpu_lib):
+    """The convolution workload at full size (8192^2 binary32, BLOCK 4 x 4) in a graph; outputs
+    sampled at partition corners and edges and at random, each recomputed by the oracle from its
+    3 x 3 neighbourhood."""
+    N, P = 8192, 16
+    x = synthetic.jacobi_field((N, N), stream=98, dtype="float")
+    w = synthetic.normal(9, stream=99)
+    gpu_lib(P)
+    X = H.HDArrayCreate("X", "float", None, N, N)
+    Y = H.HDArrayCreate("Y", "float", None, N, N)
+    D = H.HDArrayPartition(H.BLOCK, (N, N), (0, 0), (N, N), P)
+    Wp = H.HDArrayPartition(H.BLOCK, (N, N), (1, 1), (N - 1, N - 1), P)
+    H.HDArrayWrite(X, x, D)
+    H.HDArrayApplyKernel("conv2d", Wp, X, Y, *w)
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("conv2d", Wp, X, Y, *w)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, 3)
+    got = np.zeros((N, N), np.float32)
+    H.HDArrayRead(Y, got, D)
+    rng = np.random.default_rng(11)
+    samples = [tuple(int(v) for v in rng.integers(1, N - 1, 2)) for _ in range(40)]
+    for b in (2047, 2048, 2049, 4095, 4096, 6143, 6144):  # BLOCK 4 x 4 boundaries of the work region
+        samples += [(b, 1), (1, b), (b, b), (b, N - 2), (N - 2, b)]
+    samples += [(1, 1), (N - 2, N - 2), (1, N - 2), (N - 2, 1)]
+    L = oracle.lib()
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    for (i, j) in samples:
+        win = np.ascontiguousarray(x[i - 1:i + 2, j - 1:j + 2])
+        out = np.zeros((3, 3), np.float32)
+        work = np.zeros((3, 3), np.uint8)
+        work[1, 1] = 1
+        assert L.orc_conv2d(1, 3, 3, win.ctypes.data, out.ctypes.data, work.ctypes.data, wv.ctypes.data) == 0
+        assert got[i, j].view(np.uint32) == out[1, 1].view(np.uint32), (i, j)

@@ -299,6 +299,61 @@ def test_stencil3d_eigenmode_decay(shape, modes):
     np.testing.assert_allclose(B.G, lam ** 3 * u0, rtol=0, atol=1e-14)
 
 
+def _conv_program(x, w, P=3, ptype=ROW, dtype="double"):
+    o = Oracle(P)
+    dims = x.shape
+    data = o.partition(ptype, dims, (0, 0), dims)
+    work = o.partition(ptype, dims, (1, 1), (dims[0] - 1, dims[1] - 1))
+    X = o.create("X", dtype, dims)
+    Y = o.create("Y", dtype, dims)
+    o.write(X, x, data)
+    o.apply("conv2d", work, [X, Y], scalars=tuple(float(v) for v in w))
+    return Y
+
+
+def test_conv2d_matches_library_correlation():
+    """Sec. 5's convolution in binary64 against scipy's 2-D correlation (the same weights applied
+    at the same offsets, no flip) on the interior; the summation orders differ, so the bound is
+    9 roundings of sum |w| |x|.  Asymmetric weights catch a transposed or flipped filter."""
+    sig = pytest.importorskip("scipy.signal")
+    x = synthetic.normal(23 * 31, stream=88).reshape(23, 31)
+    w = synthetic.normal(9, stream=89)
+    Y = _conv_program(x, w, P=4, ptype=BLOCK)
+    ref = sig.correlate2d(x, w.reshape(3, 3), mode="valid")
+    mag = sig.correlate2d(np.abs(x), np.abs(w.reshape(3, 3)), mode="valid")
+    got = Y.G[1:-1, 1:-1]
+    assert (np.abs(got - ref) <= 9 * 2.0 ** -53 * mag).all()
+    assert not np.allclose(got, sig.correlate2d(x, w.reshape(3, 3).T, mode="valid"))
+
+
+@pytest.mark.parametrize("dtype", ["double", "float"])
+def test_conv2d_integer_exact(dtype):
+    """Small integer fields and weights: every product and partial sum is an exact integer in
+    both precisions, so the result equals the integer correlation exactly."""
+    x = np.floor(synthetic.uniform(17 * 19, stream=90) * 200 - 100).reshape(17, 19)
+    w = np.floor(synthetic.uniform(9, stream=91) * 16 - 8)
+    Y = _conv_program(x.astype(np.float64 if dtype == "double" else np.float32), w, P=3, ptype=COL, dtype=dtype)
+    xi, wi = x.astype(np.int64), w.astype(np.int64).reshape(3, 3)
+    ref = np.zeros((15, 17), np.int64)
+    for a in range(3):
+        for b in range(3):
+            ref += wi[a, b] * xi[a:a + 15, b:b + 17]
+    assert np.array_equal(Y.G[1:-1, 1:-1].astype(np.int64), ref)
+
+
+def test_conv2d_bf16_is_binary32_then_rounded():
+    """bfloat16 storage: binary32 arithmetic on the decoded values, then one round to nearest even
+    (torch's conversion) on the store."""
+    torch = pytest.importorskip("torch")
+    x = synthetic.jacobi_field((14, 16), stream=92, dtype="bf16")
+    w = synthetic.normal(9, stream=93)
+    yb = _conv_program(x, w, P=2, dtype="bf16").G
+    x32 = oracle.bf16_to_f32(x)
+    y32 = _conv_program(x32, w, P=2, dtype="float").G
+    want = torch.from_numpy(y32[1:-1, 1:-1].copy()).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(yb[1:-1, 1:-1], want)
+
+
 def test_pingpong_equals_two_kernel_form():
     """Jacobi with kernel 2 (B = A) and with swapped arguments produce identical values."""
     x = synthetic.jacobi_field((20, 23), stream=99)

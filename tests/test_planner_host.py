@@ -306,6 +306,26 @@ def test_table3_jacobi_volume_full_size(host_lib):
     assert c["plan_hits"] >= 4  # steady state comes from the cache (Sec. 4.2)
 
 
+def test_table3_convolution_volume_full_size(host_lib):
+    host_lib(32)
+    rows, L = 24080, 20480
+    B = H.HDArrayCreate("B", "float", None, rows, L)
+    A = H.HDArrayCreate("A", "float", None, rows, L)
+    D = H.HDArrayPartition(ROW, (rows, L), (0, 0), (rows, L), 32)
+    W = H.HDArrayPartition(ROW, (rows, L), (1, 1), (rows - 1, L - 1), 32)
+    H.HDArrayWrite(B, None, D)
+    H.HDArrayWrite(A, None, D)
+    w = [0.0, 0.125, 0.0, 0.125, 0.5, 0.125, 0.0, 0.125, 0.0]
+    per = []
+    for it in range(3):
+        H.HDArrayApplyKernel("conv2d", W, B, A, *w)
+        per.append(_moved_bytes(H, B, 4))
+    # the halo rows (with their corner cells) move once; B never changes, so nothing moves again
+    assert per == [2 * 31 * L * 4, 0, 0]
+    total = per[0]
+    assert round(total / 2 ** 20) == 5  # Table 3: 5 MB
+
+
 # ---------------------------------------------------------------------------------------------
 # errors and caching
 # ---------------------------------------------------------------------------------------------
