@@ -507,6 +507,60 @@ def workload_conv2d(H, torch, stream, args):
                          "frac": cells * 8 / (per * 1e-3) / 1e9 / hbm, "peak_source": src}}
 
 
+def workload_2mm(H, torch, stream, args):
+    """2MM (Sec. 5.1): D = A B, then E = C D, every iteration, on 8 logical devices with row
+    blocks and with column blocks -- the same products, different exchanges (Table 3's
+    partitioning study).  binary32 arrays on the tensor cores (bf16x3)."""
+    import numpy as np
+    import synthetic
+    n, P, iters = args.n2mm, 8, 4
+    host = {x: torch.from_numpy(synthetic.to_storage(synthetic.normal(n * n, stream=7 * 10 + i).reshape(n, n),
+                                                      "float")).pin_memory() for i, x in enumerate("ABCDE")}
+    flops = 2 * 2.0 * n * n * n  # two products per iteration
+    forms = {}
+    for form, ptype in (("row", H.ROW), ("col", H.COL)):
+        H.HDArrayInit(ndev=P)
+        H.HDArraySetStream(stream.cuda_stream)
+        arr = {x: H.HDArrayCreate(x, "float", None, n, n) for x in "ABCDE"}
+        Q = H.HDArrayPartition(ptype, (n, n), (0, 0), (n, n), P)
+        for x in "ABCDE":
+            H.HDArrayWrite(arr[x], host[x], Q)
+
+        def iteration():
+            H.HDArrayApplyKernel("gemm", Q, arr["A"], arr["B"], arr["D"], 1.0, 0.0, n, n, n)
+            moved = sum(int(np.prod(np.subtract(hi, lo))) for x in "AB" for _, _, lo, hi in H.HDArrayGetPlan(arr[x]))
+            H.HDArrayApplyKernel("gemm", Q, arr["C"], arr["D"], arr["E"], 1.0, 0.0, n, n, n)
+            moved += sum(int(np.prod(np.subtract(hi, lo))) for x in "CD" for _, _, lo, hi in H.HDArrayGetPlan(arr[x]))
+            return moved * 4
+
+        first = iteration()
+        steady = iteration()
+        H.HDArrayGraphBegin()
+        iteration()
+        gid = H.HDArrayGraphEnd()
+        for _ in range(args.warmup):
+            H.HDArrayGraphLaunch(gid, iters)
+        ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters), args.steps)
+        per = ms / iters
+        forms[form] = {"ms_per_iteration": per, "tflops_algorithmic": flops / (per * 1e-3) / 1e12,
+                       "exchange_bytes_first_iteration": first, "exchange_bytes_per_iteration": steady}
+        H.HDArrayExit()
+    peak = None
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except Exception:
+        pass
+    best = forms["col"]
+    return {"workload": "2MM (D = A B, E = C D) %d^2 FP32 on tensor cores (bf16x3), 8 logical devices, "
+                        "row vs column blocks, %d iterations per step" % (n, iters),
+            "metric": "TFLOP/s (algorithmic)", "value": best["tflops_algorithmic"],
+            "ms_per_step": best["ms_per_iteration"] * iters, "forms": forms,
+            "roofline": {"bound": "tensor", "kernel": "bf16x3 tcgen05 GEMM",
+                         "achieved": 3 * best["tflops_algorithmic"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": 3 * best["tflops_algorithmic"] / peak if peak else None,
+                         "note": "issued MMA flops (3 products per bf16x3 step) of the column form"}}
+
+
 def workload_batch(H, torch, stream, args):
     import numpy as np
     import synthetic
@@ -665,7 +719,7 @@ def run_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
-          "conv2d": workload_conv2d}[args.workload]
+          "conv2d": workload_conv2d, "2mm": workload_2mm}[args.workload]
     tpath = tune_setup(args)
     out = fn(H, torch, stream, args)
     out["autotuned"] = tune_report(tpath)
@@ -689,8 +743,9 @@ def main():
     ap.add_argument("--n3", type=int, default=512, help="3-D workload: cube side")
     ap.add_argument("--nb3", type=int, default=37, help="3-D workload: number of boxes (1 = one box)")
     ap.add_argument("--ninst", type=int, default=512, help="batch workload: number of instances")
+    ap.add_argument("--n2mm", type=int, default=8192, help="2mm workload: matrix side")
     ap.add_argument("--workload", default="jacobi2d",
-                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d"],
+                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d", "2mm"],
                     help="jacobi2d is the benchmark line; the others print their own line")
     args = ap.parse_args()
     global N, CELLS

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = taddr_s;
     const int nkt = (tile.kend + BK - 1) / BK;
-    const int mt = (tile.i0 - P.row0) / BM, nt = tile.j0 / BN;
+    const int mt = (tile.i0 - P.row0) / BM, nt = (tile.j0 - P.col0) / BN;
 
     if (warp == 0 && lane == 0) {  // producer
         uint32_t ph[P_STAGES] = {0u, 0u};

@@ -199,14 +199,14 @@ struct SplitJob {
     int32_t lower;             // A lower triangular
 };
 struct PanelPart {
-    const void *apanel;  // this device's A panel
-    const void *bpanel;  // the B panel
+    const void *apanel;  // A panel of this device's rows (row tiles from row0)
+    const void *bpanel;  // B panel of this device's columns (column tiles from col0)
     void *c;
     int64_t clo0, clo1, cs;
     int32_t row0;        // first row of the device's row tiles
     int32_t i1, j1;
     int32_t nkt, nkt_b;  // k tiles per row tile in the A and B panels
-    int32_t pad;
+    int32_t col0;        // first column of the device's column tiles
 };
 cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s);
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,

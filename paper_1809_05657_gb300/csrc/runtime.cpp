@@ -897,6 +897,15 @@ int compile_plan(Plan &pl)
         std::vector<std::pair<int, int>> dev_ranges;
         int idx = 0;
         const int VEC2 = 16 / X->esize;
+        // variant 4 (adaptive): the packed-stream kernel when every part is narrower than half a
+        // warp band (16 chunks), else the cp.async warp kernel
+        int adaptive = 1;
+        if (g->variant == 4) {
+            int64_t widest = 0;
+            for (int p = 0; p < pt.nparts; p++)
+                if (!pt.box[p].empty()) widest = std::max<int64_t>(widest, (pt.box[p].hi[1] - pt.box[p].lo[1] + VEC2) / VEC2);
+            adaptive = widest < 16 ? 3 : 1;
+        }
         for (int p = 0; p < pt.nparts; p++) {
             if (pt.box[p].empty()) continue;
             if ((Y->buf[p].alloc.lo[1] - X->buf[p].alloc.lo[1]) % VEC2 != 0) return HDARRAY_ERR_STATE;
@@ -907,7 +916,7 @@ int compile_plan(Plan &pl)
             int t0 = (int)h.tiles.size();
             const bool flat = !conv && g->variant == 2 && X->dtype != DT_BF16;
             h.flat = flat;
-            h.variant = conv ? 3 : flat ? 2 : g->variant == 2 ? 1 : g->variant;
+            h.variant = conv ? 3 : flat ? 2 : g->variant == 2 ? 1 : g->variant == 4 ? adaptive : g->variant;
             h.warps = g->warps_per_cta;
             bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
                            : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2, conv);
@@ -1155,59 +1164,62 @@ int compile_plan(Plan &pl)
         else
             add(0, (int)gp.size(), max_rows, max_cols);
     }
-    // Panel path: when every device's column tiles start on 256-column boundaries, split the operands
-    // once into pre-tiled bf16 panels and stream them with bulk copies.  The bookkeeping guarantees
-    // that after this call's exchange every device holds all of B, so one B panel (from the first
-    // device with work) serves all devices.
+    // Panel path: split the operands once into pre-tiled bf16 panels (128-byte swizzled, K-major)
+    // and stream them with bulk copies.  Each device's row range of A and column range of B get a
+    // panel, split from that device's own buffer (after this call's exchange it holds those rows
+    // of A and columns of B in full); devices with the same range share one panel (row blocks
+    // share B, column blocks share A).
     bool panel_ok = !tt.empty();
     for (const TcPart &t : tp) panel_ok = panel_ok && t.j1 > 0;
-    for (int p = 0; p < pt.nparts && panel_ok; p++)
-        if (!pt.box[p].empty() && pt.box[p].lo[1] % 256 != 0) panel_ok = false;
     if (panel_ok && getenv("HDARRAY_GEMM_NO_PANELS") == nullptr) {
         HDArray *A = pl.args[0], *B = pl.args[1];
-        const int64_t nk = A->n[1], nj = B->n[1];
-        std::vector<SplitJob> jobs;
+        const int64_t nk = A->n[1];
+        const int nkt_b = (int)((nk + 63) / 64);
+        std::vector<SplitJob> ajobs, bjobs;
         std::vector<PanelPart> pp;
+        std::map<std::pair<int64_t, int64_t>, size_t> aoff, boff;
         size_t total = 0;
-        int max_tiles = 0, first = -1;
-        std::vector<size_t> aoff;
         for (int p = 0; p < pt.nparts; p++) {
             const Box &W = pt.box[p];
             if (W.empty()) continue;
-            if (first < 0) first = p;
             const int64_t kend = (k.kind == K_TRMM) ? std::min<int64_t>(nk, W.hi[0]) : nk;
-            const int nkt = (int)((kend + 63) / 64), nmt = (int)((W.hi[0] - W.lo[0] + 127) / 128);
-            aoff.push_back(total);
-            total += (size_t)nmt * nkt * 2 * (128 * 64 * 2);
-            SplitJob J;
-            const DevBuf &ba = A->buf[p];
-            J.src = ba.ptr; J.dst = nullptr;
-            J.lo0 = ba.alloc.lo[0]; J.lo1 = ba.alloc.lo[1]; J.stride = ba.st[0];
-            J.row0 = (int32_t)W.lo[0]; J.row_end = (int32_t)W.hi[0]; J.kend = (int32_t)kend;
-            J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = 0;
-            J.lower = k.kind == K_TRMM ? 1 : 0;
-            jobs.push_back(J);
-            max_tiles = std::max(max_tiles, J.ntiles);
+            const int nkt = (int)((kend + 63) / 64);
+            const auto ka = std::make_pair(W.lo[0], W.hi[0]), kb = std::make_pair(W.lo[1], W.hi[1]);
+            if (!aoff.count(ka)) {
+                const int nmt = (int)((W.hi[0] - W.lo[0] + 127) / 128);
+                aoff[ka] = total;
+                total += (size_t)nmt * nkt * 2 * (128 * 64 * 2);
+                SplitJob J;
+                const DevBuf &ba = A->buf[p];
+                J.src = ba.ptr; J.dst = (void *)(uintptr_t)aoff[ka];  // offset until the panels exist
+                J.lo0 = ba.alloc.lo[0]; J.lo1 = ba.alloc.lo[1]; J.stride = ba.st[0];
+                J.row0 = (int32_t)W.lo[0]; J.row_end = (int32_t)W.hi[0]; J.kend = (int32_t)kend;
+                J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = 0;
+                J.lower = k.kind == K_TRMM ? 1 : 0;
+                ajobs.push_back(J);
+            }
+            if (!boff.count(kb)) {
+                const int nnt = (int)((W.hi[1] - W.lo[1] + 255) / 256);
+                boff[kb] = total;
+                total += (size_t)nnt * nkt_b * 2 * (256 * 64 * 2);
+                SplitJob J;
+                const DevBuf &bb = B->buf[p];
+                J.src = bb.ptr; J.dst = (void *)(uintptr_t)boff[kb];
+                J.lo0 = bb.alloc.lo[0]; J.lo1 = bb.alloc.lo[1]; J.stride = bb.st[0];
+                J.row0 = (int32_t)W.lo[1]; J.row_end = (int32_t)W.hi[1]; J.kend = (int32_t)nk;
+                J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = 256; J.transpose = 1; J.lower = 0;
+                bjobs.push_back(J);
+            }
             PanelPart q;
-            q.apanel = nullptr; q.bpanel = nullptr;
-            q.c = tp[pp.size()].c;
-            q.clo0 = tp[pp.size()].clo0; q.clo1 = tp[pp.size()].clo1; q.cs = tp[pp.size()].cs;
-            q.row0 = (int32_t)W.lo[0]; q.i1 = (int32_t)W.hi[0]; q.j1 = (int32_t)W.hi[1];
-            q.nkt = nkt; q.nkt_b = (int)((nk + 63) / 64); q.pad = 0;
+            const TcPart &t = tp[pp.size()];
+            q.apanel = (const void *)(uintptr_t)aoff[ka];
+            q.bpanel = (const void *)(uintptr_t)boff[kb];
+            q.c = t.c;
+            q.clo0 = t.clo0; q.clo1 = t.clo1; q.cs = t.cs;
+            q.row0 = (int32_t)W.lo[0]; q.col0 = (int32_t)W.lo[1];
+            q.i1 = (int32_t)W.hi[0]; q.j1 = (int32_t)W.hi[1];
+            q.nkt = nkt; q.nkt_b = nkt_b;
             pp.push_back(q);
-        }
-        const int nkt_b = (int)((nk + 63) / 64), nnt = (int)((nj + 255) / 256);
-        const size_t boff = total;
-        total += (size_t)nnt * nkt_b * 2 * (256 * 64 * 2);
-        {
-            SplitJob J;
-            const DevBuf &bb = B->buf[first];
-            J.src = bb.ptr; J.dst = nullptr;
-            J.lo0 = bb.alloc.lo[0]; J.lo1 = bb.alloc.lo[1]; J.stride = bb.st[0];
-            J.row0 = 0; J.row_end = (int32_t)nj; J.kend = (int32_t)nk;
-            J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = 256; J.transpose = 1; J.lower = 0;
-            jobs.push_back(J);
-            max_tiles = std::max(max_tiles, J.ntiles);
         }
         auto panels = std::make_shared<DevMem>();
         if (cudaMalloc(&panels->ptr, total) != cudaSuccess) {
@@ -1216,24 +1228,25 @@ int compile_plan(Plan &pl)
         }
         panels->bytes = total;
         char *base = (char *)panels->ptr;
-        for (size_t i = 0; i + 1 < jobs.size(); i++) jobs[i].dst = base + aoff[i];
-        jobs.back().dst = base + boff;
-        for (size_t i = 0; i < pp.size(); i++) {
-            pp[i].apanel = base + aoff[i];
-            pp[i].bpanel = base + boff;
+        for (SplitJob &J : ajobs) J.dst = base + (uintptr_t)J.dst;
+        for (SplitJob &J : bjobs) J.dst = base + (uintptr_t)J.dst;
+        for (PanelPart &q : pp) {
+            q.apanel = base + (uintptr_t)q.apanel;
+            q.bpanel = base + (uintptr_t)q.bpanel;
         }
         // tiles index the PanelPart table in the same order as TcPart
         std::vector<std::pair<const void *, size_t>> pb = {
-            {jobs.data(), (jobs.size() - 1) * sizeof(SplitJob)}, {&jobs.back(), sizeof(SplitJob)},
+            {ajobs.data(), ajobs.size() * sizeof(SplitJob)}, {bjobs.data(), bjobs.size() * sizeof(SplitJob)},
             {pp.data(), pp.size() * sizeof(PanelPart)}, {tt.data(), tt.size() * sizeof(TcTile)}};
         std::shared_ptr<DevMem> ptab;
         std::vector<const char *> pa;
         int rc2 = upload(pb, ptab, pa);
         if (rc2) return rc2;
-        int amax = 0;
-        for (size_t i = 0; i + 1 < jobs.size(); i++) amax = std::max(amax, jobs[i].ntiles);
-        LaunchRec SA; SA.kind = L_SPLIT; SA.p0 = pa[0]; SA.n0 = (int64_t)(jobs.size() - 1); SA.n1 = amax; SA.n3 = 0;
-        LaunchRec SB; SB.kind = L_SPLIT; SB.p0 = pa[1]; SB.n0 = 1; SB.n1 = jobs.back().ntiles; SB.n3 = 1;
+        int amax = 0, bmax = 0;
+        for (const SplitJob &J : ajobs) amax = std::max(amax, J.ntiles);
+        for (const SplitJob &J : bjobs) bmax = std::max(bmax, J.ntiles);
+        LaunchRec SA; SA.kind = L_SPLIT; SA.p0 = pa[0]; SA.n0 = (int64_t)ajobs.size(); SA.n1 = amax; SA.n3 = 0;
+        LaunchRec SB; SB.kind = L_SPLIT; SB.p0 = pa[1]; SB.n0 = (int64_t)bjobs.size(); SB.n1 = bmax; SB.n3 = 1;
         LaunchRec GM; GM.kind = L_GEMM_PANEL; GM.p0 = pa[2]; GM.p1 = pa[3]; GM.p2 = g->err_word;
         GM.n0 = (int64_t)tt.size();
         GM.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
@@ -2140,7 +2153,7 @@ int init_impl(int ndev, unsigned flags)
         const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
-        if (vv && atoi(vv) >= 0 && atoi(vv) <= 3) g->variant = atoi(vv);
+        if (vv && atoi(vv) >= 0 && atoi(vv) <= 4) g->variant = atoi(vv);
         const char *b2 = getenv("HDARRAY_BAND2");
         if (b2 && atoi(b2) > 0) g->band2 = atoi(b2);
         const char *at = getenv("HDARRAY_AUTOTUNE");

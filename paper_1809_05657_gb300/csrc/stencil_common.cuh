@@ -104,14 +104,13 @@ __device__ __forceinline__ void receive_flat(const Seg *__restrict__ segs, int s
         if (u < nb) *dst[u] = v[u];
 }
 
-// The warp's receive phase, then __syncwarp orders the copies before the warp's loads.
+// The warp's receive phase, then __syncwarp orders the copies before the warp's loads: the
+// barrier orders memory among the threads that take part in it, and cp.async reads are memory
+// operations of the issuing thread, so they see the other lanes' stores.
 template <typename E>
 __device__ __forceinline__ void receive_segments(const Seg *__restrict__ segs, int seg0, int nseg, int lane)
 {
-    if (nseg > 0) {
-        receive_flat<E>(segs, seg0, nseg, lane, 32);
-        __threadfence();  // the copies reach L2, where cp.async.cg loads read
-    }
+    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, lane, 32);
     __syncwarp();
 }
 
@@ -221,14 +220,12 @@ __device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, boo
 }
 
 
-// Receive segments copied by a whole CTA (then a barrier orders them before the CTA's loads).
+// Receive segments copied by a whole CTA, then a barrier orders them before the CTA's loads (as
+// for the warp form above, at CTA scope).
 template <typename E>
 __device__ __forceinline__ void receive_segments_cta(const Seg *__restrict__ segs, int seg0, int nseg)
 {
-    if (nseg > 0) {
-        receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
-        __threadfence();  // the copies reach L2, where cp.async.cg loads read
-    }
+    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
     __syncthreads();
 }
 

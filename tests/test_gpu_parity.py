@@ -796,3 +796,37 @@ def test_conv2d_full_size_8192_block16(gpu_lib):
         work[1, 1] = 1
         assert L.orc_conv2d(1, 3, 3, win.ctypes.data, out.ctypes.data, work.ctypes.data, wv.ctypes.data) == 0
         assert got[i, j].view(np.uint32) == out[1, 1].view(np.uint32), (i, j)
+
+
+# ---------------------------------------------------------------------------------------------
+# 2MM on row and column blocks (Sec. 5.1): the same products, different exchanges
+# ---------------------------------------------------------------------------------------------
+
+def two_mm_prog(n, P, ptype, iters, dtype):
+    prog = [("create", x, dtype, (n, n)) for x in "ABCDE"]
+    prog += [("part", "Q", ptype, (n, n), (0, 0), (n, n), P)]
+    prog += [("write", x, "Q") for x in "ABCDE"]
+    for _ in range(iters):
+        prog.append(("apply", "gemm", "Q", ["A", "B", "D"], (1.0, 0.0, n, n, n)))
+        prog.append(("apply", "gemm", "Q", ["C", "D", "E"], (1.0, 0.0, n, n, n)))
+    return prog
+
+
+@pytest.mark.parametrize("ptype", [ROW, COL, BLOCK])
+@pytest.mark.parametrize("dtype,n,P", [("double", 96, 4), ("float", 320, 4), ("float", 512, 2), ("float", 200, 6)])
+def test_2mm_parity(gpu_lib, ptype, dtype, n, P):
+    vals = {x: synthetic.to_storage(synthetic.normal(n * n, stream=100 + i).reshape(n, n), dtype)
+            for i, x in enumerate("ABCDE")}
+    lib, orc, *_ = run_program(two_mm_prog(n, P, ptype, 2, dtype), P, vals, gpu_lib, check_buffers=False)
+    got = {x: read_all(lib, x, (n, n), dtype, "Q").astype(np.float64) for x in "DE"}
+    A, B, C = (vals[x].astype(np.float64) for x in "ABC")
+    if dtype == "double":
+        for x in "DE":
+            ref = orc.arrays[x].G
+            assert np.abs(got[x] - ref).max() <= 1e-12 * np.abs(ref).max()
+    else:
+        # each product within the bf16x3 bound of its own (binary32) operands as stored on the GPU
+        z = np.zeros((n, n), np.float32)
+        assert (np.abs(got["D"] - A @ B) <= 2 * _bf16x3_bound(vals["A"], vals["B"], z, 1.0, 0.0, n)).all()
+        D32 = got["D"].astype(np.float32)
+        assert (np.abs(got["E"] - C @ D32.astype(np.float64)) <= 2 * _bf16x3_bound(vals["C"], D32, z, 1.0, 0.0, n)).all()

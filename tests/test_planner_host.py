@@ -326,6 +326,58 @@ def test_table3_convolution_volume_full_size(host_lib):
     assert round(total / 2 ** 20) == 5  # Table 3: 5 MB
 
 
+def _two_mm_volumes(P, n, iters, ptype):
+    """Elements moved per iteration by 2MM (D = A B, then E = C D, Sec. 5.1) with every array
+    written and every product computed on the same partition (ROW or COL)."""
+    names = "ABCDE"
+    arrs = {x: H.HDArrayCreate(x, "float", None, n, n) for x in names}
+    part = H.HDArrayPartition(ptype, (n, n), (0, 0), (n, n), P)
+    for x in names:
+        H.HDArrayWrite(arrs[x], None, part)
+    per = []
+    for _ in range(iters):
+        H.HDArrayApplyKernel("gemm", part, arrs["A"], arrs["B"], arrs["D"], 1.0, 0.0, n, n, n)
+        v = sum(_moved_bytes(H, arrs[x], 1) for x in "AB")
+        H.HDArrayApplyKernel("gemm", part, arrs["C"], arrs["D"], arrs["E"], 1.0, 0.0, n, n, n)
+        v += sum(_moved_bytes(H, arrs[x], 1) for x in "CD")
+        per.append(v)
+    return per
+
+
+def two_mm_prog(n, P, ptype, iters, dtype="double"):
+    prog = [("create", x, dtype, (n, n)) for x in "ABCDE"]
+    prog += [("part", "Q", ptype, (n, n), (0, 0), (n, n), P)]
+    prog += [("write", x, "Q") for x in "ABCDE"]
+    for _ in range(iters):
+        prog.append(("apply", "gemm", "Q", ["A", "B", "D"], (1.0, 0.0, n, n, n)))
+        prog.append(("apply", "gemm", "Q", ["C", "D", "E"], (1.0, 0.0, n, n, n)))
+    return prog
+
+
+@pytest.mark.parametrize("ptype", [ROW, COL])
+def test_2mm_messages(host_lib, ptype):
+    """2MM's messages, element by element, equal the oracle's for row and column blocks."""
+    assert run_both(two_mm_prog(22, 4, ptype, 3), 4, host_lib) >= 1
+
+
+def test_2mm_row_vs_column_partition_volumes(host_lib):
+    """Sec. 5.1 / Table 3: with row blocks, B is gathered once and D (redefined by the first
+    product in every iteration) is gathered by every device in every iteration; with column
+    blocks only A and C are gathered, once.  Over 100 iterations the totals are in the ratio
+    (1 + 100) : 2, which is Table 3's 1262 GB : 25 GB (the paper does not give 2MM's sizes, so the
+    ratio is what pins the volumes)."""
+    P, n = 32, 96
+    host_lib(P)
+    row = _two_mm_volumes(P, n, 4, ROW)
+    host_lib(P)
+    col = _two_mm_volumes(P, n, 4, COL)
+    g = (P - 1) * n * n  # one all-gather of an n x n array
+    assert row == [2 * g, g, g, g]
+    assert col == [2 * g, 0, 0, 0]
+    ratio = (row[0] + 99 * row[1]) / (col[0] + 99 * col[1])
+    assert abs(ratio - 1262 / 25) / ratio < 0.01
+
+
 # ---------------------------------------------------------------------------------------------
 # errors and caching
 # ---------------------------------------------------------------------------------------------
