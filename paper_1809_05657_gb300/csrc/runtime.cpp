@@ -601,7 +601,7 @@ void tile2d_segments(const HDArray *X, const DevBuf &bx, StenTile2D &t, const st
 // Tiles of the fused 2-D kernel for one device.  Warp variants (0, 1): column bands of 32 chunks
 // x tile_rows rows, a warp each.  Packed-stream variant (3): the box's chunks cut into bands of
 // equal width of at most band_chunks (<= 32); per band, tiles of ns streams x sl rows with
-// ns = min(256 / nch, 512 / (nch + 2)) and sl about tile_rows, balanced over the band's rows.
+// ns = min(256 / nch, 340 / (nch + 2)) and sl about tile_rows, balanced over the band's rows.
 bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                   const std::vector<Move> &recv, bool want_segs, Sten2DHost &h, int variant = 1,
                   int band_chunks = 32, bool corners = false)
@@ -642,7 +642,8 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
         const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(band_chunks, 32));
         const int64_t nb = (chunks + cap - 1) / cap;
         const int64_t nch = (chunks + nb - 1) / nb;
-        const int64_t G = std::min<int64_t>(256 / nch, 512 / (nch + 2));
+        // at most 340 staged slots (43.5 KB of ring per CTA): four CTAs per SM, the register limit
+        const int64_t G = std::max<int64_t>(1, std::min<int64_t>(256 / nch, 340 / (nch + 2)));
         const int64_t R = W.hi[0] - W.lo[0];
         const int64_t ntr = (R + G * H - 1) / (G * H);     // tiles down the band
         const int64_t sl = (R + ntr * G - 1) / (ntr * G);  // balanced stream length
