@@ -561,6 +561,77 @@ def workload_2mm(H, torch, stream, args):
                          "note": "issued MMA flops (3 products per bf16x3 step) of the column form"}}
 
 
+def workload_cov(H, torch, stream, args):
+    """Covariance (Sec. 5.1) of n samples x m variables, binary32 (the product on the tensor
+    cores, bf16x3), 32 logical devices: column means, centring, the upper-triangular product with
+    absolute use / trapezoid definition sections, the symmetric copy.  Row blocks of C split
+    evenly and balanced by the upper triangle's area (a manual partition)."""
+    import numpy as np
+    import synthetic
+    from paper_1809_05657_gb300.partitions import even_rows, triangle_balanced_rows as balanced_rows
+    n = m = args.ncov
+    P, iters = 32, 2
+    x = torch.from_numpy(synthetic.to_storage(synthetic.normal(n * m, stream=8).reshape(n, m), "float")).pin_memory()
+    flops = float(n) * m * (m + 1)  # the product's upper triangle (j >= i)
+    forms = {}
+    for form in ("even", "balanced"):
+        rows = balanced_rows(m, P) if form == "balanced" else even_rows(m, P)
+        H.HDArrayInit(ndev=P)
+        H.HDArraySetStream(stream.cuda_stream)
+        X = H.HDArrayCreate("X", "float", None, n, m)
+        M = H.HDArrayCreate("M", "float", None, 1, m)
+        Xc = H.HDArrayCreate("Xc", "float", None, n, m)
+        C = H.HDArrayCreate("C", "float", None, m, m)
+        DX = H.HDArrayPartition(H.ROW, (n, m), (0, 0), (n, m), P)
+        PM = H.HDArrayPartition(H.COL, (1, m), (0, 0), (1, m), P)
+        PC = H.HDArrayPartitionManual((m, m), [((rows[p], 0), (rows[p + 1], m)) for p in range(P)])
+        for p in range(P):
+            r0, r1 = rows[p], rows[p + 1]
+            H.HDArraySetAbsoluteUse("syrk", PC, Xc, p, (0, r0), (n, m))
+            H.HDArraySetTrapezoidDef("syrk", PC, C, p, (r0, r0, r0, m - 1, r1 - 1, r1 - 1, r1 - 1, m - 1))
+            H.HDArraySetAbsoluteUse("symmetrize", PC, C, p, (0, r0), (r1, r1))
+            t = max(r0, 1)
+            if t < r1:
+                H.HDArraySetTrapezoidDef("symmetrize", PC, C, p, (t, 0, t, t - 1, r1 - 1, 0, r1 - 1, r1 - 2))
+            else:
+                H.HDArraySetAbsoluteDef("symmetrize", PC, C, p, (0, 0), (0, 0))
+        H.HDArrayWrite(X, x, DX)
+
+        def moved(arrs):
+            return sum(int(np.prod(np.subtract(hi, lo))) for a in arrs for _, _, lo, hi in H.HDArrayGetPlan(a)) * 4
+
+        def iteration():
+            v = 0
+            H.HDArrayApplyKernel("colmean", PM, X, M)
+            v += moved([X])
+            H.HDArrayApplyKernel("center", DX, X, M, Xc)
+            v += moved([X, M])
+            H.HDArrayApplyKernel("syrk", PC, Xc, C, 1.0 / (n - 1))
+            v += moved([Xc])
+            H.HDArrayApplyKernel("symmetrize", PC, C)
+            v += moved([C])
+            return v
+
+        first = iteration()
+        steady = iteration()
+        H.HDArrayGraphBegin()
+        iteration()
+        gid = H.HDArrayGraphEnd()
+        for _ in range(args.warmup):
+            H.HDArrayGraphLaunch(gid, iters)
+        ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters), args.steps)
+        per = ms / iters
+        forms[form] = {"ms_per_iteration": per, "tflops_algorithmic": flops / (per * 1e-3) / 1e12,
+                       "exchange_bytes_first_iteration": first, "exchange_bytes_per_iteration": steady,
+                       "row_bounds_head": rows[:4]}
+        H.HDArrayExit()
+    best = min(forms.values(), key=lambda f: f["ms_per_iteration"])
+    return {"workload": "covariance of %d samples x %d variables, FP32 (product on tensor cores, bf16x3), "
+                        "32 logical devices, even vs area-balanced row blocks, %d iterations per step" % (n, m, iters),
+            "metric": "TFLOP/s (algorithmic, the product's upper triangle)", "value": best["tflops_algorithmic"],
+            "ms_per_step": best["ms_per_iteration"] * iters, "forms": forms}
+
+
 def workload_batch(H, torch, stream, args):
     import numpy as np
     import synthetic
@@ -719,7 +790,7 @@ def run_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
-          "conv2d": workload_conv2d, "2mm": workload_2mm}[args.workload]
+          "conv2d": workload_conv2d, "2mm": workload_2mm, "cov": workload_cov}[args.workload]
     tpath = tune_setup(args)
     out = fn(H, torch, stream, args)
     out["autotuned"] = tune_report(tpath)
@@ -744,8 +815,9 @@ def main():
     ap.add_argument("--nb3", type=int, default=37, help="3-D workload: number of boxes (1 = one box)")
     ap.add_argument("--ninst", type=int, default=512, help="batch workload: number of instances")
     ap.add_argument("--n2mm", type=int, default=8192, help="2mm workload: matrix side")
+    ap.add_argument("--ncov", type=int, default=10240, help="cov workload: samples = variables")
     ap.add_argument("--workload", default="jacobi2d",
-                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d", "2mm"],
+                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d", "2mm", "cov"],
                     help="jacobi2d is the benchmark line; the others print their own line")
     args = ap.parse_args()
     global N, CELLS

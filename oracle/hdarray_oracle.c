@@ -561,6 +561,73 @@ void orc_gemm_entries(int64_t nj, int64_t nk, double alpha, double beta, const d
     }
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Covariance (Sec. 5.1: a triangular product, then a symmetric copy).  X is n x m: n samples of */
+/* m variables.  binary64 or binary32 storage (prec 0 / 1).                                       */
+/* ------------------------------------------------------------------------------------------ */
+
+static void store_from_double(int prec, void *Y, int64_t i, double v)
+{
+    if (prec == 0) ((double *)Y)[i] = v;
+    else ((float *)Y)[i] = (float)v;
+}
+
+/* Column means: M is 1 x m; for each work element (0, j): M[0][j] = (X[0][j] + ... + X[n-1][j]) / n,
+ * summed in binary64 in row order, the quotient rounded to the storage type. */
+int orc_colmean(int prec, int64_t n, int64_t m, const void *X, void *M, const uint8_t *work)
+{
+    if (prec > 1) return -1;
+    for (int64_t j = 0; j < m; j++) {
+        if (!work[j]) continue;
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++) s += load_as_double(prec, X, i * m + j);
+        store_from_double(prec, M, j, s / (double)n);
+    }
+    return 0;
+}
+
+/* Centring: for each work element (i, j): Xc[i][j] = X[i][j] - M[0][j], one subtraction in the
+ * storage precision. */
+int orc_center(int prec, int64_t n, int64_t m, const void *X, const void *M, void *Xc, const uint8_t *work)
+{
+    if (prec > 1) return -1;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < m; j++) {
+            const int64_t c = i * m + j;
+            if (!work[c]) continue;
+            if (prec == 0) ((double *)Xc)[c] = ((const double *)X)[c] - ((const double *)M)[j];
+            else ((float *)Xc)[c] = ((const float *)X)[c] - ((const float *)M)[j];
+        }
+    return 0;
+}
+
+/* Upper-triangular product: for each work element (i, j) of the m x m array C with j >= i:
+ * C[i][j] = alpha * sum_k X[k][i] * X[k][j] (k ascending, binary64), rounded to the storage type.
+ * Work elements with j < i are left alone. */
+int orc_syrk_upper(int prec, int64_t n, int64_t m, double alpha, const void *X, void *C, const uint8_t *work)
+{
+    if (prec > 1) return -1;
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = i; j < m; j++) {
+            if (!work[i * m + j]) continue;
+            double s = 0.0;
+            for (int64_t k = 0; k < n; k++) s += load_as_double(prec, X, k * m + i) * load_as_double(prec, X, k * m + j);
+            store_from_double(prec, C, i * m + j, alpha * s);
+        }
+    return 0;
+}
+
+/* Symmetric copy: for each work element (i, j) with j < i: C[i][j] = C[j][i] (a bit copy); work
+ * elements with j >= i are left alone. */
+int orc_symmetrize(int prec, int64_t m, void *C, const uint8_t *work)
+{
+    const int64_t es = prec == 0 ? 8 : prec == 1 ? 4 : 2;
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < i; j++)
+            if (work[i * m + j]) memcpy((char *)C + (i * m + j) * es, (const char *)C + (j * m + i) * es, (size_t)es);
+    return 0;
+}
+
 /* HDArrayReduce (Table 2): fold the masked elements, in row-major order, in binary64.
  * op: 0 SUM, 1 PROD, 2 MAX, 3 MIN.  Returns -1 for an unknown op. */
 int orc_reduce(int prec, int64_t total, const void *X, const uint8_t *mask, int op, double *out)

@@ -60,6 +60,10 @@ def lib():
             "orc_jacobi2d": (i32, [i32, i64, i64, P, P, P]),
             "orc_stencil3d": (i32, [i32, i64, i64, i64, P, P, P]),
             "orc_conv2d": (i32, [i32, i64, i64, P, P, P, P]),
+            "orc_colmean": (i32, [i32, i64, i64, P, P, P]),
+            "orc_center": (i32, [i32, i64, i64, P, P, P, P]),
+            "orc_syrk_upper": (i32, [i32, i64, i64, ctypes.c_double, P, P, P]),
+            "orc_symmetrize": (i32, [i32, i64, P, P]),
             "orc_copy": (None, [i32, i64, P, P, P]),
             "orc_sqdiff": (None, [i32, i64, P, P, P, P]),
             "orc_gemm": (None, [i64, i64, i64, ctypes.c_double, ctypes.c_double, P, P, P, P]),
@@ -182,6 +186,29 @@ def _run_conv2d(o, arrs, work, scal):
         raise ValueError("conv2d: work element on the array border")
 
 
+def _run_colmean(o, arrs, work, scal):
+    X, M = arrs
+    if lib().orc_colmean(X.prec, X.dims[0], X.dims[1], _p(X.G), _p(M.G), _p(work)) != 0:
+        raise ValueError("colmean: double or float arrays")
+
+
+def _run_center(o, arrs, work, scal):
+    X, M, Xc = arrs
+    if lib().orc_center(X.prec, X.dims[0], X.dims[1], _p(X.G), _p(M.G), _p(Xc.G), _p(work)) != 0:
+        raise ValueError("center: double or float arrays")
+
+
+def _run_syrk(o, arrs, work, scal):
+    X, C = arrs
+    if lib().orc_syrk_upper(X.prec, X.dims[0], X.dims[1], float(scal[0]), _p(X.G), _p(C.G), _p(work)) != 0:
+        raise ValueError("syrk: double or float arrays")
+
+
+def _run_symmetrize(o, arrs, work, scal):
+    (C,) = arrs
+    lib().orc_symmetrize(C.prec, C.dims[0], _p(C.G), _p(work))
+
+
 def _run_stencil3d(o, arrs, work, scal):
     X, Y = arrs
     rc = lib().orc_stencil3d(X.prec, X.dims[0], X.dims[1], X.dims[2], _p(X.G), _p(Y.G), _p(work))
@@ -240,6 +267,17 @@ KERNELS = {
     # Sec. 5, 2-D convolution: the Jacobi offsets plus the four diagonals and the centre, nine
     # weights as scalars.  Arguments (X, Y, w0 .. w8).
     "conv2d": KernelSpec(2, {0: _C2 + [(0, 0)]}, {1: [(0, 0)]}, _run_conv2d, nscal=9),
+    # Covariance (Sec. 5.1).  Column means of X (n x m) into M (1 x m): use X's whole column.
+    "colmean": KernelSpec(2, {0: [(ALL, 0)]}, {1: [(0, 0)]}, _run_colmean),
+    # Xc = X - M (M broadcast down the columns).  Arguments (X, M, Xc).
+    "center": KernelSpec(3, {0: [(0, 0)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_center),
+    # C[i][j] = alpha * (X^T X)[i][j] for j >= i.  Arguments (X, C, alpha).  The use of X (columns i
+    # and j of every row) is not an offset pattern: by default all of X, normally narrowed with
+    # absolute sections; the definition is normally narrowed to the upper trapezoid.
+    "syrk": KernelSpec(2, {0: [(ALL, ALL)]}, {1: [(0, 0)]}, _run_syrk, nscal=1),
+    # C[i][j] = C[j][i] for j < i (the transposed use likewise narrowed with absolute sections,
+    # the definition to the lower trapezoid).  Argument (C).
+    "symmetrize": KernelSpec(1, {0: [(ALL, ALL)]}, {0: [(0, 0)]}, _run_symmetrize),
 }
 
 

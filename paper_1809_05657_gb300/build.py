@@ -40,7 +40,7 @@ def _stale(target, deps):
 def build(force=False, verbose=False, extra=()):
     """Compile and link if anything changed.  Returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "hdarray.h"))
     nvcc = _nvcc()
     jobs = []

@@ -7,7 +7,8 @@
 // the whole of B, which the exchange has gathered into its buffer (Sec. 5.1: GEMM all-gathers B).
 //
 // A plain shared-memory tiled DFMA kernel: 64 x 64 C tile per CTA, 256 threads with 4 x 4
-// outputs each, K in steps of 16.  This is the binary64 comparison form.
+// outputs each, K in steps of 16.  This is the binary64 comparison form.  It also serves the
+// covariance product C = alpha X^T X (A read transposed, only j >= i computed).
 #include "kernels.h"
 
 namespace hda {
@@ -20,6 +21,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmPart *__restrict__ p
     const GemmPart P = parts[blockIdx.z];
     const int i0 = P.i0 + blockIdx.y * GT, j0 = P.j0 + blockIdx.x * GT;
     if (i0 >= P.i1 || j0 >= P.j1) return;
+    if (P.upper && j0 + GT - 1 < i0) return;  // the tile lies below the diagonal
     const int ie = min(i0 + GT, P.i1);
     __shared__ double As[GK][GT + 1];
     __shared__ double Bs[GK][GT];
@@ -30,13 +32,15 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmPart *__restrict__ p
     double acc[4][4] = {};
     const int kend = P.lower ? min(P.nk, ie) : P.nk;
     for (int k0 = 0; k0 < kend; k0 += GK) {
-        // A tile: 64 rows x 16 k, transposed into As[k][i]
+        // A tile: 64 rows x 16 k, transposed into As[k][i] (consecutive threads on consecutive
+        // addresses: along k for a row-major A, along i for a transposed one)
         for (int e = threadIdx.x; e < GT * GK; e += 256) {
-            const int ii = e / GK, kk = e % GK;
+            const int ii = P.transa ? e % GT : e / GK, kk = P.transa ? e / GT : e % GK;
             const int i = i0 + ii, k = k0 + kk;
             double v = 0.0;
             if (i < P.i1 && k < kend && (!P.lower || k <= i))
-                v = A[(int64_t)(i - P.alo0) * P.as + (k - P.alo1)];
+                v = P.transa ? A[(int64_t)(k - P.alo0) * P.as + (i - P.alo1)]
+                             : A[(int64_t)(i - P.alo0) * P.as + (k - P.alo1)];
             As[kk][ii] = v;
         }
         // B tile: 16 k x 64 columns
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmPart *__restrict__ p
 #pragma unroll
         for (int v = 0; v < 4; v++) {
             const int j = j0 + tx * 4 + v;
-            if (j >= P.j1) continue;
+            if (j >= P.j1 || (P.upper && j < i)) continue;
             double *c = C + (int64_t)(i - P.clo0) * P.cs + (j - P.clo1);
             const double old = beta == 0.0 ? 0.0 : *c;
             *c = beta * old + alpha * acc[u][v];

@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
 #pragma unroll
                 for (int e = 0; e < 32; e++) {
                     const int j = tile.j0 + cc * 32 + e;
-                    if (j < P.j1) {
+                    if (j < P.j1 && (!P.upper || j >= i)) {
                         float *cp = crow + (j - P.clo1);
                         const float acc = __uint_as_float(r[e]);
                         *cp = beta == 0.0f ? alpha * acc : beta * *cp + alpha * acc;

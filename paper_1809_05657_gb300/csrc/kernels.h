@@ -157,7 +157,9 @@ struct GemmPart {
     int64_t clo0, clo1, cs;
     int32_t i0, i1, j0, j1;  // work box of C
     int32_t nk;
-    int32_t lower;
+    int32_t lower;   // A lower triangular (k <= i only)
+    int32_t transa;  // A[i][k] is element (k, i) of the A buffer (C = alpha X^T X: syrk)
+    int32_t upper;   // only the elements with j >= i of C are computed and stored
 };
 cudaError_t launch_gemm_f64(const GemmPart *parts, int nparts, int max_rows, int max_cols,
                             double alpha, double beta, cudaStream_t s);
@@ -207,8 +209,32 @@ struct PanelPart {
     int32_t i1, j1;
     int32_t nkt, nkt_b;  // k tiles per row tile in the A and B panels
     int32_t col0;        // first column of the device's column tiles
+    int32_t upper;       // store only the elements with j >= i
+    int32_t pad;
 };
 cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Covariance pieces (Sec. 5.1).  A task is one logical device's work box.
+// colmean: M[0][j] = (sum over the n rows of X[i][j]) / n for j in [j0, j1), binary64 sums in a
+//          fixed order (deterministic); centre: Xc = X - M over [i0, i1) x [j0, j1);
+// symmetrize: C[i][j] = C[j][i] for the elements with j < i of [i0, i1) x [j0, j1).
+// ------------------------------------------------------------------------------------------
+struct CovTask {
+    const void *x;  // colmean, centre: X; symmetrize: C (read at the transposed positions)
+    const void *m;  // colmean: M (written); centre: M (read)
+    void *y;        // centre: Xc; symmetrize: C (written)
+    int64_t xlo0, xlo1, xs;
+    int64_t mlo1;   // M's buffer origin column (its one row is row 0)
+    int64_t ylo0, ylo1, ys;
+    int32_t i0, i1, j0, j1;
+    int32_t n;      // colmean: the rows of X
+    int32_t pad;
+};
+cudaError_t launch_colmean(int dtype, const CovTask *tasks, int ntasks, int max_cols, cudaStream_t s);
+cudaError_t launch_center(int dtype, const CovTask *tasks, int ntasks, int max_rows, cudaStream_t s);
+cudaError_t launch_symmetrize(int dtype, const CovTask *tasks, int ntasks, int max_rows, int max_cols,
+                              cudaStream_t s);
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
                                float beta, unsigned *err, cudaStream_t s);
 cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles, float alpha, float beta,

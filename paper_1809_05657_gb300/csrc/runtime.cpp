@@ -158,6 +158,37 @@ void register_builtins(Ctx &c)
         k.def = {{}, {off(0, 0, 0)}};
         add(k);
     }
+    {   // Sec. 5.1 covariance: column means M (1 x m) of X (n x m); a work item (0, j) uses column j
+        KernelDef k;
+        k.name = "colmean"; k.kind = K_COLMEAN; k.narr = 2; k.space = 1;
+        k.use = {{off(ALL, 0, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // centring Xc = X - M, M broadcast down the columns; args X, M, Xc
+        KernelDef k;
+        k.name = "center"; k.kind = K_CENTER; k.narr = 3; k.space = 2;
+        k.use = {{off(0, 0, 0)}, {off(ALL, 0, 0)}, {}};
+        k.def = {{}, {}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // C[i][j] = alpha (X^T X)[i][j] for j >= i; args X, C, alpha.  The use of X (columns i and j
+        // of every row) is no offset pattern: all of X unless narrowed with absolute sections; the
+        // definition is normally narrowed to the upper trapezoid of each device's rows
+        KernelDef k;
+        k.name = "syrk"; k.kind = K_SYRK; k.narr = 2; k.nscal_f = 1; k.space = 1;
+        k.use = {{off(ALL, ALL, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+    }
+    {   // C[i][j] = C[j][i] for j < i (the symmetric copy); the transposed use likewise all of C
+        // unless narrowed, the definition normally the lower trapezoid
+        KernelDef k;
+        k.name = "symmetrize"; k.kind = K_SYMM; k.narr = 1; k.space = 0;
+        k.use = {{off(ALL, ALL, 0)}};
+        k.def = {{off(0, 0, 0)}};
+        add(k);
+    }
     {   // 3-D 7-point analogue of Jacobi kernel 1
         KernelDef k;
         k.name = "stencil3d"; k.kind = K_STENCIL3D; k.narr = 2; k.space = 1;
@@ -1050,6 +1081,7 @@ int compile_plan(Plan &pl)
     std::vector<GemmPart> gp;
     std::vector<TcPart> tp;
     std::vector<TcTile> tt;
+    std::vector<CovTask> cov;
     int max_rows = 0, max_cols = 0;
     for (int p = 0; p < pt.nparts; p++) {
         const Box &W = pt.box[p];
@@ -1079,8 +1111,32 @@ int compile_plan(Plan &pl)
                 pw.push_back(t);
             }
             pw_groups.push_back({b, (int)pw.size()});
-        } else if (k.kind == K_GEMM || k.kind == K_TRMM) {
-            HDArray *A = pl.args[0], *B = pl.args[1], *C = pl.args[2];
+        } else if (k.kind == K_COLMEAN || k.kind == K_CENTER || k.kind == K_SYMM) {
+            HDArray *X = pl.args[0];
+            const DevBuf &bx = X->buf[p];
+            CovTask t;
+            t.x = bx.ptr; t.m = nullptr; t.y = nullptr;
+            t.xlo0 = bx.alloc.lo[0]; t.xlo1 = bx.alloc.lo[1]; t.xs = bx.st[0];
+            t.mlo1 = 0; t.ylo0 = 0; t.ylo1 = 0; t.ys = 0;
+            t.i0 = (int32_t)W.lo[0]; t.i1 = (int32_t)W.hi[0]; t.j0 = (int32_t)W.lo[1]; t.j1 = (int32_t)W.hi[1];
+            t.n = (int32_t)X->n[0]; t.pad = 0;
+            if (k.kind != K_SYMM) {
+                const DevBuf &bm = pl.args[1]->buf[p];
+                t.m = bm.ptr;
+                t.mlo1 = bm.alloc.lo[1];
+            }
+            if (k.kind != K_COLMEAN) {
+                const DevBuf &by = k.kind == K_CENTER ? pl.args[2]->buf[p] : bx;
+                t.y = by.ptr;
+                t.ylo0 = by.alloc.lo[0]; t.ylo1 = by.alloc.lo[1]; t.ys = by.st[0];
+            }
+            cov.push_back(t);
+            max_rows = std::max<int>(max_rows, t.i1 - t.i0);
+            max_cols = std::max<int>(max_cols, t.j1 - t.j0);
+        } else if (k.kind == K_GEMM || k.kind == K_TRMM || k.kind == K_SYRK) {
+            const bool syrk = k.kind == K_SYRK;  // A = X read transposed, B = X, C = the second argument
+            HDArray *A = pl.args[0], *B = pl.args[0], *C = syrk ? pl.args[1] : pl.args[2];
+            if (!syrk) B = pl.args[1];
             const DevBuf &ba = A->buf[p], &bb = B->buf[p], &bc = C->buf[p];
             GemmPart q;
             q.a = ba.ptr; q.b = bb.ptr; q.c = bc.ptr;
@@ -1089,8 +1145,10 @@ int compile_plan(Plan &pl)
             q.clo0 = bc.alloc.lo[0]; q.clo1 = bc.alloc.lo[1]; q.cs = bc.st[0];
             q.i0 = (int32_t)W.lo[0]; q.i1 = (int32_t)W.hi[0];
             q.j0 = (int32_t)W.lo[1]; q.j1 = (int32_t)W.hi[1];
-            q.nk = (int32_t)A->n[1];
+            q.nk = (int32_t)(syrk ? A->n[0] : A->n[1]);
             q.lower = k.kind == K_TRMM ? 1 : 0;
+            q.transa = syrk ? 1 : 0;
+            q.upper = syrk ? 1 : 0;
             if (A->dtype == DT_F32) {  // tensor cores, bf16x3
                 TcPart t;
                 t.a = q.a; t.b = q.b; t.c = q.c;
@@ -1102,6 +1160,7 @@ int compile_plan(Plan &pl)
                 tp.push_back(t);
                 for (int ti = q.i0; ti < q.i1; ti += 128)
                     for (int tj = q.j0; tj < q.j1; tj += 256) {
+                        if (q.upper && tj + 255 < ti) continue;  // entirely below the diagonal
                         TcTile x;
                         x.part = pi; x.i0 = ti; x.j0 = tj;
                         x.kend = q.lower ? std::min(q.nk, std::min(ti + 128, q.i1)) : q.nk;
@@ -1126,9 +1185,11 @@ int compile_plan(Plan &pl)
     std::stable_sort(tt.begin(), tt.end(), [](const TcTile &x, const TcTile &y) { return x.kend > y.kend; });
     blobs.push_back({tp.data(), tp.size() * sizeof(TcPart)});
     blobs.push_back({tt.data(), tt.size() * sizeof(TcTile)});
+    blobs.push_back({cov.data(), cov.size() * sizeof(CovTask)});
     std::vector<const char *> addr;
     int rc = upload(blobs, pl.tables, addr);
     if (rc) return rc;
+
     auto push_copy = [&](const CopyTask *base, const std::vector<std::pair<int, int>> &groups, int64_t total) {
         if (plain) {
             for (auto &gr : groups)
@@ -1143,6 +1204,11 @@ int compile_plan(Plan &pl)
     };
     push_copy((const CopyTask *)addr[0], xfer_groups, (int64_t)xfer.size());
     push_copy((const CopyTask *)addr[1], local_groups, (int64_t)local.size());
+    if (!cov.empty()) {
+        LaunchRec L; L.kind = k.kind == K_COLMEAN ? L_COLMEAN : k.kind == K_CENTER ? L_CENTER : L_SYMM;
+        L.dtype = pl.args[0]->dtype; L.p0 = addr[6]; L.n0 = (int64_t)cov.size(); L.n1 = max_rows; L.n2 = max_cols;
+        pl.launches.push_back(L);
+    }
     if (!pw.empty()) {
         auto add = [&](int b, int e) {
             LaunchRec L; L.kind = L_SQDIFF; L.dtype = pl.args[0]->dtype;
@@ -1172,9 +1238,10 @@ int compile_plan(Plan &pl)
     // share B, column blocks share A).
     bool panel_ok = !tt.empty();
     for (const TcPart &t : tp) panel_ok = panel_ok && t.j1 > 0;
-    if (panel_ok && getenv("HDARRAY_GEMM_NO_PANELS") == nullptr) {
-        HDArray *A = pl.args[0], *B = pl.args[1];
-        const int64_t nk = A->n[1];
+    const bool syrk = k.kind == K_SYRK;  // only the panel kernel reads A transposed
+    if (panel_ok && (syrk || getenv("HDARRAY_GEMM_NO_PANELS") == nullptr)) {
+        HDArray *A = pl.args[0], *B = syrk ? pl.args[0] : pl.args[1];
+        const int64_t nk = syrk ? A->n[0] : A->n[1];
         const int nkt_b = (int)((nk + 63) / 64);
         std::vector<SplitJob> ajobs, bjobs;
         std::vector<PanelPart> pp;
@@ -1195,7 +1262,7 @@ int compile_plan(Plan &pl)
                 J.src = ba.ptr; J.dst = (void *)(uintptr_t)aoff[ka];  // offset until the panels exist
                 J.lo0 = ba.alloc.lo[0]; J.lo1 = ba.alloc.lo[1]; J.stride = ba.st[0];
                 J.row0 = (int32_t)W.lo[0]; J.row_end = (int32_t)W.hi[0]; J.kend = (int32_t)kend;
-                J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = 0;
+                J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = syrk ? 1 : 0;
                 J.lower = k.kind == K_TRMM ? 1 : 0;
                 ajobs.push_back(J);
             }
@@ -1220,6 +1287,7 @@ int compile_plan(Plan &pl)
             q.row0 = (int32_t)W.lo[0]; q.col0 = (int32_t)W.lo[1];
             q.i1 = (int32_t)W.hi[0]; q.j1 = (int32_t)W.hi[1];
             q.nkt = nkt; q.nkt_b = nkt_b;
+            q.upper = syrk ? 1 : 0; q.pad = 0;
             pp.push_back(q);
         }
         auto panels = std::make_shared<DevMem>();
@@ -1521,6 +1589,26 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
         if (a[2]->dtype != DT_F64 || a[2] == a[0] || a[2] == a[1]) return HDARRAY_ERR_INVAL;
         break;
     case K_EXCHANGE:
+        break;
+    case K_COLMEAN:
+    case K_CENTER: {
+        const HDArray *X = a[0], *M = a[1];
+        if (X->dim != 2 || M->dim != 2 || M->n[0] != 1 || M->n[1] != X->n[1] || X == M) return HDARRAY_ERR_INVAL;
+        if (X->dtype != M->dtype || (X->dtype != DT_F64 && X->dtype != DT_F32)) return HDARRAY_ERR_INVAL;
+        if (k.kind == K_CENTER) {
+            const HDArray *Y = a[2];
+            if (!same(X, Y) || Y == X || Y == M || Y->dtype != X->dtype) return HDARRAY_ERR_INVAL;
+        }
+        break;
+    }
+    case K_SYRK: {
+        const HDArray *X = a[0], *C = a[1];
+        if (X->dim != 2 || C->dim != 2 || C->n[0] != X->n[1] || C->n[1] != X->n[1] || C == X) return HDARRAY_ERR_INVAL;
+        if (X->dtype != C->dtype || (X->dtype != DT_F64 && X->dtype != DT_F32)) return HDARRAY_ERR_INVAL;
+        break;
+    }
+    case K_SYMM:
+        if (a[0]->dim != 2 || a[0]->n[0] != a[0]->n[1]) return HDARRAY_ERR_INVAL;
         break;
     case K_GEMM:
     case K_TRMM: {
@@ -2200,6 +2288,9 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
         return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
                               (unsigned *)L.p2, s);
     case L_SPLIT: return launch_split_panels((const SplitJob *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_COLMEAN: return launch_colmean(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n2, s);
+    case L_CENTER: return launch_center(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_SYMM: return launch_symmetrize(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, s);
     case L_CONV2D:
         return launch_stencil2d_cta(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                     (const Seg *)L.p2, (const double *)L.p3, (size_t)L.n3, s);

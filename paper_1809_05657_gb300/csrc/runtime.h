@@ -22,7 +22,7 @@ struct Offset {
     int32_t o[3];
 };
 
-enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D };
+enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D, K_COLMEAN, K_CENTER, K_SYRK, K_SYMM };
 
 // A built-in kernel: its arguments and the use/def offsets of each array argument, the table the
 // paper's frontend builds from the pragma clauses (Sec. 4.1).
@@ -66,7 +66,8 @@ struct Part {
 };
 
 // One kernel launch, recorded so that batches can merge it and graphs can replay it.
-enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL, L_FLAT2D, L_FLAT3D, L_CONV2D };
+enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL, L_FLAT2D, L_FLAT3D, L_CONV2D,
+             L_COLMEAN, L_CENTER, L_SYMM };
 struct LaunchRec {
     int kind = 0;
     int dtype = 0;

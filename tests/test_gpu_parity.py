@@ -830,3 +830,41 @@ def test_2mm_parity(gpu_lib, ptype, dtype, n, P):
         assert (np.abs(got["D"] - A @ B) <= 2 * _bf16x3_bound(vals["A"], vals["B"], z, 1.0, 0.0, n)).all()
         D32 = got["D"].astype(np.float32)
         assert (np.abs(got["E"] - C @ D32.astype(np.float64)) <= 2 * _bf16x3_bound(vals["C"], D32, z, 1.0, 0.0, n)).all()
+
+
+# ---------------------------------------------------------------------------------------------
+# covariance (Sec. 5.1): triangular product with absolute / trapezoid sections, symmetric copy
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("balanced", [False, True])
+@pytest.mark.parametrize("dtype,n,m,P", [("double", 70, 96, 4), ("float", 300, 384, 4), ("float", 130, 200, 3)])
+def test_covariance_parity(gpu_lib, balanced, dtype, n, m, P):
+    from cov_program import cov_prog
+    prog, rows = cov_prog(n, m, P, dtype=dtype, balanced=balanced)
+    x = synthetic.to_storage(synthetic.normal(n * m, stream=110).reshape(n, m) + 0.5, dtype)
+    lib, orc, *_ = run_program(prog, P, {"X": x}, gpu_lib, check_buffers=False)
+    M = read_all(lib, "M", (1, m), dtype, "PM").astype(np.float64)
+    Xc = read_all(lib, "Xc", (n, m), dtype, "DX")
+    C = read_all(lib, "C", (m, m), dtype, "PC")
+    # means: binary64 sums in another order (each within (n - 1) 2^-53 sum|x| of the exact sum),
+    # then rounded to the storage type (one unit in the last place of the stored mean)
+    Mo = orc.arrays["M"].G.astype(np.float64)
+    sums = 2 * (n + 1) * 2.0 ** -53 * np.abs(x.astype(np.float64)).sum(axis=0) / n
+    ulp = 0.0 if dtype == "double" else 2.0 ** -23
+    assert (np.abs(M - Mo) <= sums + ulp * np.abs(Mo) + 1e-300).all()
+    # centring is one subtraction in the storage precision of the device's own means
+    assert np.array_equal(Xc, (x - M.astype(x.dtype)).astype(x.dtype))
+    # the symmetric copy is exact
+    assert np.array_equal(C, C.T)
+    # the product: within the rounding bound of the arithmetic used, against the device's own Xc
+    X64 = Xc.astype(np.float64)
+    ref = X64.T @ X64 / (n - 1)
+    mag = np.abs(X64).T @ np.abs(X64) / (n - 1)
+    if dtype == "double":
+        bound = 2 * (n + 2) * 2.0 ** -53 * mag + 1e-300
+    else:
+        bound = 2 * _bf16x3_bound(Xc.T.copy(), Xc, np.zeros((m, m), np.float32), 1.0 / (n - 1), 0.0, n)
+    assert (np.abs(C.astype(np.float64) - ref) <= bound).all()
+    # and the oracle's covariance matrix agrees with numpy's
+    assert np.abs(orc.arrays["C"].G.astype(np.float64) - np.cov(x.astype(np.float64), rowvar=False)).max() \
+        <= (1e-12 if dtype == "double" else 1e-4) * np.abs(np.cov(x.astype(np.float64), rowvar=False)).max()

@@ -360,6 +360,16 @@ def test_2mm_messages(host_lib, ptype):
     assert run_both(two_mm_prog(22, 4, ptype, 3), 4, host_lib) >= 1
 
 
+@pytest.mark.parametrize("balanced", [False, True])
+def test_covariance_messages(host_lib, balanced):
+    """The covariance program (column means, centring, triangular product with absolute use and
+    trapezoid definitions, symmetric copy): messages equal the oracle's element by element, on
+    even and on area-balanced row blocks."""
+    from cov_program import cov_prog
+    prog, _ = cov_prog(40, 36, 4, balanced=balanced)
+    assert run_both(prog, 4, host_lib) >= 3
+
+
 def test_2mm_row_vs_column_partition_volumes(host_lib):
     """Sec. 5.1 / Table 3: with row blocks, B is gathered once and D (redefined by the first
     product in every iteration) is gathered by every device in every iteration; with column
