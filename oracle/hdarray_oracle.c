@@ -601,6 +601,38 @@ int orc_center(int prec, int64_t n, int64_t m, const void *X, const void *M, voi
     return 0;
 }
 
+/* Column norms (correlation): for each work element (0, j): S[0][j] = sqrt(sum_i X[i][j]^2), the
+ * sum of squares in binary64 in row order, the root in binary64, rounded to the storage type. */
+int orc_colnorm(int prec, int64_t n, int64_t m, const void *X, void *S, const uint8_t *work)
+{
+    if (prec > 1) return -1;
+    for (int64_t j = 0; j < m; j++) {
+        if (!work[j]) continue;
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++) {
+            const double v = load_as_double(prec, X, i * m + j);
+            s += v * v;
+        }
+        store_from_double(prec, S, j, sqrt(s));
+    }
+    return 0;
+}
+
+/* Column scaling (correlation): for each work element (i, j): Y[i][j] = X[i][j] / S[0][j], one
+ * division in the storage precision. */
+int orc_colscale(int prec, int64_t n, int64_t m, const void *X, const void *S, void *Y, const uint8_t *work)
+{
+    if (prec > 1) return -1;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < m; j++) {
+            const int64_t c = i * m + j;
+            if (!work[c]) continue;
+            if (prec == 0) ((double *)Y)[c] = ((const double *)X)[c] / ((const double *)S)[j];
+            else ((float *)Y)[c] = ((const float *)X)[c] / ((const float *)S)[j];
+        }
+    return 0;
+}
+
 /* Upper-triangular product: for each work element (i, j) of the m x m array C with j >= i:
  * C[i][j] = alpha * sum_k X[k][i] * X[k][j] (k ascending, binary64), rounded to the storage type.
  * Work elements with j < i are left alone. */

@@ -63,6 +63,8 @@ def lib():
             "orc_colmean": (i32, [i32, i64, i64, P, P, P]),
             "orc_center": (i32, [i32, i64, i64, P, P, P, P]),
             "orc_syrk_upper": (i32, [i32, i64, i64, ctypes.c_double, P, P, P]),
+            "orc_colnorm": (i32, [i32, i64, i64, P, P, P]),
+            "orc_colscale": (i32, [i32, i64, i64, P, P, P, P]),
             "orc_symmetrize": (i32, [i32, i64, P, P]),
             "orc_copy": (None, [i32, i64, P, P, P]),
             "orc_sqdiff": (None, [i32, i64, P, P, P, P]),
@@ -198,6 +200,18 @@ def _run_center(o, arrs, work, scal):
         raise ValueError("center: double or float arrays")
 
 
+def _run_colnorm(o, arrs, work, scal):
+    X, S = arrs
+    if lib().orc_colnorm(X.prec, X.dims[0], X.dims[1], _p(X.G), _p(S.G), _p(work)) != 0:
+        raise ValueError("colnorm: double or float arrays")
+
+
+def _run_colscale(o, arrs, work, scal):
+    X, S, Y = arrs
+    if lib().orc_colscale(X.prec, X.dims[0], X.dims[1], _p(X.G), _p(S.G), _p(Y.G), _p(work)) != 0:
+        raise ValueError("colscale: double or float arrays")
+
+
 def _run_syrk(o, arrs, work, scal):
     X, C = arrs
     if lib().orc_syrk_upper(X.prec, X.dims[0], X.dims[1], float(scal[0]), _p(X.G), _p(C.G), _p(work)) != 0:
@@ -271,6 +285,9 @@ KERNELS = {
     "colmean": KernelSpec(2, {0: [(ALL, 0)]}, {1: [(0, 0)]}, _run_colmean),
     # Xc = X - M (M broadcast down the columns).  Arguments (X, M, Xc).
     "center": KernelSpec(3, {0: [(0, 0)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_center),
+    # Correlation: column norms S (1 x m) of X, and Y = X / S (S broadcast down the columns).
+    "colnorm": KernelSpec(2, {0: [(ALL, 0)]}, {1: [(0, 0)]}, _run_colnorm),
+    "colscale": KernelSpec(3, {0: [(0, 0)], 1: [(ALL, 0)]}, {2: [(0, 0)]}, _run_colscale),
     # C[i][j] = alpha * (X^T X)[i][j] for j >= i.  Arguments (X, C, alpha).  The use of X (columns i
     # and j of every row) is not an offset pattern: by default all of X, normally narrowed with
     # absolute sections; the definition is normally narrowed to the upper trapezoid.

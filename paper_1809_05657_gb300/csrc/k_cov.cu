@@ -1,5 +1,6 @@
-// k_cov.cu -- the element-wise and copy pieces of the covariance program (Sec. 5.1): column
-// means, centring, and the symmetric copy that completes the triangular product.  The product
+// k_cov.cu -- the element-wise and copy pieces of the covariance and correlation programs
+// (Sec. 5.1): column means and norms, centring and scaling, and the symmetric copy that completes
+// the triangular product.  The product
 // itself (C = alpha X^T X, j >= i) runs on the GEMM kernels (k_gemm.cu, k_gemm_tc.cu).
 #include "kernels.h"
 
@@ -8,9 +9,9 @@ namespace hda {
 template <typename T>
 __device__ __forceinline__ double ld64(const T *p) { return (double)*p; }
 
-// Column means: one CTA per (device, 32 columns); lane = column, warp w sums the rows w, w+8, ...
-// in binary64, then the eight partial sums are folded in warp order (a fixed order: the result
-// does not depend on scheduling).
+// Column means (or norms): one CTA per (device, 32 columns); lane = column, warp w sums the rows
+// w, w+8, ... (or their squares) in binary64, then the eight partial sums are folded in warp order
+// (a fixed order: the result does not depend on scheduling).
 template <typename T>
 __global__ void __launch_bounds__(256) k_colmean(const CovTask *__restrict__ tasks)
 {
@@ -21,7 +22,14 @@ __global__ void __launch_bounds__(256) k_colmean(const CovTask *__restrict__ tas
     double s = 0.0;
     if (t.j0 + blockIdx.x * 32 < t.j1 && j < t.j1) {
         const T *x = reinterpret_cast<const T *>(t.x) + (j - t.xlo1);
-        for (int i = warp; i < t.n; i += 8) s += ld64(x + (int64_t)(i - t.xlo0) * t.xs);
+        if (t.mode == 0) {
+            for (int i = warp; i < t.n; i += 8) s += ld64(x + (int64_t)(i - t.xlo0) * t.xs);
+        } else {
+            for (int i = warp; i < t.n; i += 8) {
+                const double v = ld64(x + (int64_t)(i - t.xlo0) * t.xs);
+                s += v * v;
+            }
+        }
     }
     part[warp][lane] = s;
     __syncthreads();
@@ -30,11 +38,12 @@ __global__ void __launch_bounds__(256) k_colmean(const CovTask *__restrict__ tas
 #pragma unroll
         for (int w = 1; w < 8; w++) a += part[w][lane];
         T *m = const_cast<T *>(reinterpret_cast<const T *>(t.m));
-        m[j - t.mlo1] = (T)(a / (double)t.n);
+        m[j - t.mlo1] = (T)(t.mode == 0 ? a / (double)t.n : sqrt(a));
     }
 }
 
-// Centring: a warp per row of the device's box, four loads in flight per lane.
+// Centring (or scaling): a warp per row of the device's box, four loads in flight per lane; one
+// IEEE subtraction (or division) per element in the storage precision.
 template <typename T>
 __global__ void __launch_bounds__(256) k_center(const CovTask *__restrict__ tasks)
 {
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(256) k_center(const CovTask *__restrict__ task
             }
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (j + 32 * u < t.j1) y[j + 32 * u] = a[u] - b[u];
+            if (j + 32 * u < t.j1) y[j + 32 * u] = t.mode == 0 ? a[u] - b[u] : a[u] / b[u];
     }
 }
 

@@ -217,7 +217,8 @@ cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, 
 // ------------------------------------------------------------------------------------------
 // Covariance pieces (Sec. 5.1).  A task is one logical device's work box.
 // colmean: M[0][j] = (sum over the n rows of X[i][j]) / n for j in [j0, j1), binary64 sums in a
-//          fixed order (deterministic); centre: Xc = X - M over [i0, i1) x [j0, j1);
+//          fixed order (deterministic), or (mode 1) sqrt(sum of X[i][j]^2);
+// centre: Xc = X - M, or (mode 1) X / M, over [i0, i1) x [j0, j1);
 // symmetrize: C[i][j] = C[j][i] for the elements with j < i of [i0, i1) x [j0, j1).
 // ------------------------------------------------------------------------------------------
 struct CovTask {
@@ -229,7 +230,7 @@ struct CovTask {
     int64_t ylo0, ylo1, ys;
     int32_t i0, i1, j0, j1;
     int32_t n;      // colmean: the rows of X
-    int32_t pad;
+    int32_t mode;   // colmean: 0 mean, 1 root of the sum of squares; centre: 0 X - M, 1 X / M
 };
 cudaError_t launch_colmean(int dtype, const CovTask *tasks, int ntasks, int max_cols, cudaStream_t s);
 cudaError_t launch_center(int dtype, const CovTask *tasks, int ntasks, int max_rows, cudaStream_t s);

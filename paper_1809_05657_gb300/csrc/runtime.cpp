@@ -172,6 +172,18 @@ void register_builtins(Ctx &c)
         k.def = {{}, {}, {off(0, 0, 0)}};
         add(k);
     }
+    {   // correlation: column norms S (1 x m) of X, and Y = X / S; args (X, S) and (X, S, Y)
+        KernelDef k;
+        k.name = "colnorm"; k.kind = K_COLNORM; k.narr = 2; k.space = 1;
+        k.use = {{off(ALL, 0, 0)}, {}};
+        k.def = {{}, {off(0, 0, 0)}};
+        add(k);
+        KernelDef q;
+        q.name = "colscale"; q.kind = K_COLSCALE; q.narr = 3; q.space = 2;
+        q.use = {{off(0, 0, 0)}, {off(ALL, 0, 0)}, {}};
+        q.def = {{}, {}, {off(0, 0, 0)}};
+        add(q);
+    }
     {   // C[i][j] = alpha (X^T X)[i][j] for j >= i; args X, C, alpha.  The use of X (columns i and j
         // of every row) is no offset pattern: all of X unless narrowed with absolute sections; the
         // definition is normally narrowed to the upper trapezoid of each device's rows
@@ -1111,7 +1123,10 @@ int compile_plan(Plan &pl)
                 pw.push_back(t);
             }
             pw_groups.push_back({b, (int)pw.size()});
-        } else if (k.kind == K_COLMEAN || k.kind == K_CENTER || k.kind == K_SYMM) {
+        } else if (k.kind == K_COLMEAN || k.kind == K_CENTER || k.kind == K_SYMM || k.kind == K_COLNORM ||
+                   k.kind == K_COLSCALE) {
+            const bool reduce_cols = k.kind == K_COLMEAN || k.kind == K_COLNORM;
+            const bool pointwise = k.kind == K_CENTER || k.kind == K_COLSCALE;
             HDArray *X = pl.args[0];
             const DevBuf &bx = X->buf[p];
             CovTask t;
@@ -1119,14 +1134,15 @@ int compile_plan(Plan &pl)
             t.xlo0 = bx.alloc.lo[0]; t.xlo1 = bx.alloc.lo[1]; t.xs = bx.st[0];
             t.mlo1 = 0; t.ylo0 = 0; t.ylo1 = 0; t.ys = 0;
             t.i0 = (int32_t)W.lo[0]; t.i1 = (int32_t)W.hi[0]; t.j0 = (int32_t)W.lo[1]; t.j1 = (int32_t)W.hi[1];
-            t.n = (int32_t)X->n[0]; t.pad = 0;
+            t.n = (int32_t)X->n[0];
+            t.mode = (k.kind == K_COLNORM || k.kind == K_COLSCALE) ? 1 : 0;
             if (k.kind != K_SYMM) {
                 const DevBuf &bm = pl.args[1]->buf[p];
                 t.m = bm.ptr;
                 t.mlo1 = bm.alloc.lo[1];
             }
-            if (k.kind != K_COLMEAN) {
-                const DevBuf &by = k.kind == K_CENTER ? pl.args[2]->buf[p] : bx;
+            if (!reduce_cols) {
+                const DevBuf &by = pointwise ? pl.args[2]->buf[p] : bx;
                 t.y = by.ptr;
                 t.ylo0 = by.alloc.lo[0]; t.ylo1 = by.alloc.lo[1]; t.ys = by.st[0];
             }
@@ -1205,7 +1221,9 @@ int compile_plan(Plan &pl)
     push_copy((const CopyTask *)addr[0], xfer_groups, (int64_t)xfer.size());
     push_copy((const CopyTask *)addr[1], local_groups, (int64_t)local.size());
     if (!cov.empty()) {
-        LaunchRec L; L.kind = k.kind == K_COLMEAN ? L_COLMEAN : k.kind == K_CENTER ? L_CENTER : L_SYMM;
+        LaunchRec L;
+        L.kind = (k.kind == K_COLMEAN || k.kind == K_COLNORM) ? L_COLMEAN
+                 : (k.kind == K_CENTER || k.kind == K_COLSCALE) ? L_CENTER : L_SYMM;
         L.dtype = pl.args[0]->dtype; L.p0 = addr[6]; L.n0 = (int64_t)cov.size(); L.n1 = max_rows; L.n2 = max_cols;
         pl.launches.push_back(L);
     }
@@ -1591,11 +1609,13 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
     case K_EXCHANGE:
         break;
     case K_COLMEAN:
+    case K_COLNORM:
+    case K_COLSCALE:
     case K_CENTER: {
         const HDArray *X = a[0], *M = a[1];
         if (X->dim != 2 || M->dim != 2 || M->n[0] != 1 || M->n[1] != X->n[1] || X == M) return HDARRAY_ERR_INVAL;
         if (X->dtype != M->dtype || (X->dtype != DT_F64 && X->dtype != DT_F32)) return HDARRAY_ERR_INVAL;
-        if (k.kind == K_CENTER) {
+        if (k.kind == K_CENTER || k.kind == K_COLSCALE) {
             const HDArray *Y = a[2];
             if (!same(X, Y) || Y == X || Y == M || Y->dtype != X->dtype) return HDARRAY_ERR_INVAL;
         }

@@ -22,7 +22,7 @@ struct Offset {
     int32_t o[3];
 };
 
-enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D, K_COLMEAN, K_CENTER, K_SYRK, K_SYMM };
+enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D, K_COLMEAN, K_CENTER, K_SYRK, K_SYMM, K_COLNORM, K_COLSCALE };
 
 // A built-in kernel: its arguments and the use/def offsets of each array argument, the table the
 // paper's frontend builds from the pragma clauses (Sec. 4.1).

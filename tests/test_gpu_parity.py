@@ -836,11 +836,11 @@ def test_2mm_parity(gpu_lib, ptype, dtype, n, P):
 # covariance (Sec. 5.1): triangular product with absolute / trapezoid sections, symmetric copy
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("balanced", [False, True])
+@pytest.mark.parametrize("balanced,correlation", [(False, False), (True, False), (False, True)])
 @pytest.mark.parametrize("dtype,n,m,P", [("double", 70, 96, 4), ("float", 300, 384, 4), ("float", 130, 200, 3)])
-def test_covariance_parity(gpu_lib, balanced, dtype, n, m, P):
+def test_covariance_parity(gpu_lib, balanced, correlation, dtype, n, m, P):
     from cov_program import cov_prog
-    prog, rows = cov_prog(n, m, P, dtype=dtype, balanced=balanced)
+    prog, rows = cov_prog(n, m, P, dtype=dtype, balanced=balanced, correlation=correlation)
     x = synthetic.to_storage(synthetic.normal(n * m, stream=110).reshape(n, m) + 0.5, dtype)
     lib, orc, *_ = run_program(prog, P, {"X": x}, gpu_lib, check_buffers=False)
     M = read_all(lib, "M", (1, m), dtype, "PM").astype(np.float64)
@@ -856,15 +856,24 @@ def test_covariance_parity(gpu_lib, balanced, dtype, n, m, P):
     assert np.array_equal(Xc, (x - M.astype(x.dtype)).astype(x.dtype))
     # the symmetric copy is exact
     assert np.array_equal(C, C.T)
-    # the product: within the rounding bound of the arithmetic used, against the device's own Xc
+    alpha = 1.0 / (n - 1)
+    if correlation:  # unit-norm columns: S within the summation bound, the scaling one division
+        S = read_all(lib, "S", (1, m), dtype, "PM").astype(np.float64)
+        Xc64 = Xc.astype(np.float64)
+        Sref = np.sqrt((Xc64 ** 2).sum(axis=0))
+        assert (np.abs(S - Sref) <= (n + 2) * 2.0 ** -53 * Sref + (0 if dtype == "double" else 2.0 ** -23 * Sref)).all()
+        Xs = read_all(lib, "Xs", (n, m), dtype, "DX")
+        assert np.array_equal(Xs, (Xc / S.astype(Xc.dtype)).astype(Xc.dtype))
+        Xc, alpha = Xs, 1.0
+    # the product: within the rounding bound of the arithmetic used, against the device's own input
     X64 = Xc.astype(np.float64)
-    ref = X64.T @ X64 / (n - 1)
-    mag = np.abs(X64).T @ np.abs(X64) / (n - 1)
+    ref = alpha * X64.T @ X64
+    mag = alpha * np.abs(X64).T @ np.abs(X64)
     if dtype == "double":
         bound = 2 * (n + 2) * 2.0 ** -53 * mag + 1e-300
     else:
-        bound = 2 * _bf16x3_bound(Xc.T.copy(), Xc, np.zeros((m, m), np.float32), 1.0 / (n - 1), 0.0, n)
+        bound = 2 * _bf16x3_bound(Xc.T.copy(), Xc, np.zeros((m, m), np.float32), alpha, 0.0, n)
     assert (np.abs(C.astype(np.float64) - ref) <= bound).all()
-    # and the oracle's covariance matrix agrees with numpy's
-    assert np.abs(orc.arrays["C"].G.astype(np.float64) - np.cov(x.astype(np.float64), rowvar=False)).max() \
-        <= (1e-12 if dtype == "double" else 1e-4) * np.abs(np.cov(x.astype(np.float64), rowvar=False)).max()
+    # and the oracle's matrix agrees with numpy's
+    want = np.corrcoef(x.astype(np.float64), rowvar=False) if correlation else np.cov(x.astype(np.float64), rowvar=False)
+    assert np.abs(orc.arrays["C"].G.astype(np.float64) - want).max() <= (1e-12 if dtype == "double" else 1e-4) * np.abs(want).max()

@@ -354,6 +354,47 @@ def test_conv2d_bf16_is_binary32_then_rounded():
     assert np.array_equal(yb[1:-1, 1:-1], want)
 
 
+def _cov_oracle(x, P=3, correlation=False, balanced=False):
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from cov_program import cov_prog
+    from harness import OracleRun
+    n, m = x.shape
+    prog, _ = cov_prog(n, m, P, "double", balanced=balanced, correlation=correlation)
+    orc = OracleRun(P)
+    orc.run(prog, {"X": x})
+    return orc.arrays
+
+
+@pytest.mark.parametrize("balanced", [False, True])
+def test_covariance_program_matches_numpy(balanced):
+    """The oracle's covariance program (means, centring, triangular product, symmetric copy) gives
+    numpy's covariance matrix; its pieces are the plain definitions: centring and the scaling are
+    single IEEE operations, the copy makes C exactly symmetric."""
+    x = synthetic.normal(50 * 23, stream=112).reshape(50, 23) * 3 + 1
+    a = _cov_oracle(x, P=4, balanced=balanced)
+    n = x.shape[0]
+    assert np.allclose(a["M"].G[0], x.mean(axis=0), rtol=0, atol=1e-14 * np.abs(x).max())
+    assert np.array_equal(a["Xc"].G, x - a["M"].G[0])
+    C = a["C"].G
+    assert np.array_equal(C, C.T)
+    ref = np.cov(x, rowvar=False)
+    assert np.abs(C - ref).max() <= 1e-13 * np.abs(ref).max()
+    Xc = a["Xc"].G
+    assert np.abs(np.triu(C) - np.triu(Xc.T @ Xc / (n - 1))).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_correlation_program_matches_numpy():
+    x = synthetic.normal(40 * 17, stream=113).reshape(40, 17) * np.linspace(0.5, 4, 17) + 2
+    a = _cov_oracle(x, P=3, correlation=True)
+    S = a["S"].G[0]
+    assert np.allclose(S, np.sqrt((a["Xc"].G ** 2).sum(axis=0)), rtol=1e-15, atol=0)
+    assert np.array_equal(a["Xs"].G, a["Xc"].G / S)
+    C = a["C"].G
+    assert np.array_equal(C, C.T)
+    assert np.abs(C - np.corrcoef(x, rowvar=False)).max() <= 1e-14
+
+
 def test_pingpong_equals_two_kernel_form():
     """Jacobi with kernel 2 (B = A) and with swapped arguments produce identical values."""
     x = synthetic.jacobi_field((20, 23), stream=99)

@@ -360,13 +360,13 @@ def test_2mm_messages(host_lib, ptype):
     assert run_both(two_mm_prog(22, 4, ptype, 3), 4, host_lib) >= 1
 
 
-@pytest.mark.parametrize("balanced", [False, True])
-def test_covariance_messages(host_lib, balanced):
+@pytest.mark.parametrize("balanced,correlation", [(False, False), (True, False), (True, True)])
+def test_covariance_messages(host_lib, balanced, correlation):
     """The covariance program (column means, centring, triangular product with absolute use and
     trapezoid definitions, symmetric copy): messages equal the oracle's element by element, on
     even and on area-balanced row blocks."""
     from cov_program import cov_prog
-    prog, _ = cov_prog(40, 36, 4, balanced=balanced)
+    prog, _ = cov_prog(40, 36, 4, balanced=balanced, correlation=correlation)
     assert run_both(prog, 4, host_lib) >= 3
 
 
