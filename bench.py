@@ -632,6 +632,60 @@ def workload_cov(H, torch, stream, args):
             "ms_per_step": best["ms_per_iteration"] * iters, "forms": forms}
 
 
+def workload_small(H, torch, stream, args):
+    """The 256^2 binary64 Jacobi of the paper's program (ROW 4, the two kernels: the step then the
+    copy back, 10 iterations) and the FP64 residual via HDArrayReduce: it fits in L2 and is bound
+    by launch latency, so it reports microseconds per iteration (plain form: one launch per device
+    and kernel; fused form: one launch per kernel in a CUDA graph), no roofline claim."""
+    import synthetic
+    N, P, iters = 256, 4, 10
+    x = synthetic.jacobi_field((N, N), stream=0, dtype="double")
+    out = {}
+    for form, mode in (("plain", H.HDARRAY_MODE_PLAIN), ("fused", H.HDARRAY_MODE_FUSED)):
+        H.HDArrayInit(ndev=P)
+        H.HDArraySetStream(stream.cuda_stream)
+        H.HDArraySetMode(mode)
+        B = H.HDArrayCreate("B", "double", None, N, N)
+        A = H.HDArrayCreate("A", "double", None, N, N)
+        R = H.HDArrayCreate("R", "double", None, N, N)
+        D = H.HDArrayPartition(H.ROW, (N, N), (0, 0), (N, N), P)
+        W = H.HDArrayPartition(H.ROW, (N, N), (1, 1), (N - 1, N - 1), P)
+        H.HDArrayWrite(B, x, D)
+        H.HDArrayWrite(A, x, D)
+
+        def iteration():
+            H.HDArrayApplyKernel("jacobi2d", W, B, A)
+            H.HDArrayApplyKernel("copy", W, A, B)
+
+        for _ in range(3):
+            iteration()
+        H.HDArrayGraphBegin()
+        iteration()
+        gid = H.HDArrayGraphEnd()
+
+        def step():
+            H.HDArrayGraphLaunch(gid, iters)
+            H.HDArrayApplyKernel("sqdiff", W, A, B, R)
+            return H.HDArrayReduce(R, H.SUM, W)
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = step()
+        dt = (time.perf_counter() - t0) / args.steps
+        out[form] = {"ms_per_step": dt * 1e3, "us_per_iteration": dt * 1e6 / iters, "residual": res}
+        H.HDArrayExit()
+    cells = (N - 2) * (N - 2)
+    best = out["fused"]
+    return {"workload": "Jacobi 256^2 FP64, ROW 4, the step and the copy kernels, 10 iterations + FP64 "
+                        "residual (HDArrayReduce, synchronous) per step; host wall clock per step",
+            "metric": "Gcell-updates/s", "value": cells * iters / (best["ms_per_step"] * 1e-3) / 1e9,
+            "ms_per_step": best["ms_per_step"], "forms": out,
+            "roofline": {"bound": "launch latency", "note": "fits in L2; reported in microseconds per iteration",
+                         "frac": None}}
+
+
 def workload_batch(H, torch, stream, args):
     import numpy as np
     import synthetic
@@ -790,7 +844,8 @@ def run_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
-          "conv2d": workload_conv2d, "2mm": workload_2mm, "cov": workload_cov}[args.workload]
+          "conv2d": workload_conv2d, "2mm": workload_2mm, "cov": workload_cov,
+          "small": workload_small}[args.workload]
     tpath = tune_setup(args)
     out = fn(H, torch, stream, args)
     out["autotuned"] = tune_report(tpath)
@@ -817,7 +872,7 @@ def main():
     ap.add_argument("--n2mm", type=int, default=8192, help="2mm workload: matrix side")
     ap.add_argument("--ncov", type=int, default=10240, help="cov workload: samples = variables")
     ap.add_argument("--workload", default="jacobi2d",
-                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d", "2mm", "cov"],
+                    choices=["jacobi2d", "stencil3d", "batch", "trmm", "conv2d", "2mm", "cov", "small"],
                     help="jacobi2d is the benchmark line; the others print their own line")
     args = ap.parse_args()
     global N, CELLS
