@@ -663,10 +663,13 @@ def workload_small(H, torch, stream, args):
         iteration()
         gid = H.HDArrayGraphEnd()
 
-        def step():
-            H.HDArrayGraphLaunch(gid, iters)
+        def step():  # the residual of the last iteration: new iterate A against the old B
+            H.HDArrayGraphLaunch(gid, iters - 1)
+            H.HDArrayApplyKernel("jacobi2d", W, B, A)
             H.HDArrayApplyKernel("sqdiff", W, A, B, R)
-            return H.HDArrayReduce(R, H.SUM, W)
+            r = H.HDArrayReduce(R, H.SUM, W)
+            H.HDArrayApplyKernel("copy", W, A, B)
+            return r
 
         for _ in range(args.warmup):
             step()

@@ -293,6 +293,55 @@ int HDArrayReadDeviceBuffer(HDArray_t *hA, int dev, const int64_t *lo, const int
 int HDArrayReduceBufferNoAlloc(const void *x, const char *type, int dim, const int64_t *extent,
                                const int64_t *strides, REDUCE_OP op, double *result, void *stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* User kernels (extension).  In the paper, users write their own device kernels and give each */
+/* array argument use/def clauses, which the frontend turns into the runtime's kernel table     */
+/* (Sec. 3, Sec. 4.1).  Here a kernel is a host launcher the runtime calls after the exchange;  */
+/* its use/def offsets are set with HDArraySetOffsetUse/Def (or per call with absolute and      */
+/* trapezoid sections).                                                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+#define HDARRAY_MAX_KERNEL_ARRAYS 8
+
+/* One logical device's share of a call of a user kernel. */
+typedef struct {
+    int dev;                                          /* logical device */
+    int64_t lo[3], hi[3];                             /* work box, in the index space of the
+                                                         kernel's space argument (user dimension
+                                                         order; unused dimensions lo 0, hi 1) */
+    void *buf[HDARRAY_MAX_KERNEL_ARRAYS];             /* device buffer of each array argument on
+                                                         this device (NULL if it has none) */
+    int64_t buf_lo[HDARRAY_MAX_KERNEL_ARRAYS][3];     /* coordinates of the buffer's first element */
+    int64_t buf_stride[HDARRAY_MAX_KERNEL_ARRAYS][3]; /* element strides of dimensions 0..2 */
+} HDArrayWork_t;
+
+/* A user kernel's launcher.  HDArrayApplyKernel calls it once per call, after queueing the copies
+ * of the incoming sections on the library stream, with the work of every logical device whose
+ * work box is not empty (the buffers then hold every element the device uses).  It queues its
+ * device work on `stream` (a cudaStream_t), touching only its devices' buffers, and defines exactly
+ * the def sections; it returns 0, or a negative code that the apply returns.  It may run during
+ * stream capture (HDArrayGraphBegin) and inside batches.  `user` is the pointer given at
+ * registration; `work` and `scalars` are valid during the call only. */
+typedef int (*HDArrayLauncher_t)(const HDArrayWork_t *work, int nwork, const double *scalars, int nscal,
+                                 void *stream, void *user);
+
+/* Register (or replace) the user kernel kName: narr array arguments (at most
+ * HDARRAY_MAX_KERNEL_ARRAYS), nscal floating scalars after them, the work partition covering the
+ * index space of argument spaceArg.  Every argument's use and def offsets start empty.  A name of a
+ * built-in kernel is rejected (HDARRAY_ERR_INVAL). */
+int HDArrayRegisterKernel(const char *kName, int narr, int nscal, int spaceArg, HDArrayLauncher_t launcher,
+                          void *user);
+
+/* Device memory for array buffers and the library's descriptor tables from a caller-supplied
+ * allocator (a framework's caching allocator, say) instead of cudaMalloc / cudaFree.  alloc returns
+ * at least `bytes` bytes of device memory aligned to 256 bytes, or NULL; free_fn releases it.
+ * (NULL, NULL) restores cudaMalloc / cudaFree.  Takes effect for later allocations: set it before
+ * creating arrays; memory is always released by the allocator that provided it, after the device
+ * has finished all queued work (as cudaFree would wait). */
+typedef void *(*HDArrayAlloc_t)(size_t bytes, void *user);
+typedef void (*HDArrayFree_t)(void *ptr, void *user);
+int HDArraySetAllocator(HDArrayAlloc_t alloc, HDArrayFree_t free_fn, void *user);
+
 /* Counters since HDArrayInit: [0] kernel launches issued by the library, [1] section bytes
  * moved between device buffers, [2] plans computed (cache misses), [3] plan cache hits,
  * [4] graph launches.  n values are written (n <= 5). */

@@ -351,9 +351,9 @@ int ensure_buffer(HDArray *a, int p, const Box &need)
     set_strides(a, nbuf);
     nbuf.bytes = (size_t)nb.volume() * a->esize;
     void *ptr = nullptr;
-    if (cudaMalloc(&ptr, nbuf.bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return HDARRAY_ERR_NOMEM;
+    {
+        const int arc = dev_alloc(&ptr, nbuf.bytes);
+        if (arc) return arc;
     }
     nbuf.ptr = (char *)ptr;
     CUDA_TRY(cudaMemsetAsync(nbuf.ptr, 0, nbuf.bytes, g->stream));
@@ -361,7 +361,7 @@ int ensure_buffer(HDArray *a, int p, const Box &need)
         int rc = copy_box_d2d(a, b, nbuf, b.alloc);
         if (rc) return rc;
         CUDA_TRY(cudaStreamSynchronize(g->stream));
-        cudaFree(b.ptr);
+        dev_free(b.ptr);
     }
     b = nbuf;
     a->epoch++;
@@ -447,10 +447,12 @@ int upload(const std::vector<std::pair<const void *, size_t>> &parts, std::share
         for (size_t i = 0; i < parts.size(); i++) addrs.push_back(nullptr);
         return HDARRAY_OK;
     }
-    if (cudaMalloc(&mem->ptr, total) != cudaSuccess) {
-        cudaGetLastError();
-        mem->ptr = nullptr;
-        return HDARRAY_ERR_NOMEM;
+    {
+        const int arc = dev_alloc(&mem->ptr, total);
+        if (arc) {
+            mem->ptr = nullptr;
+            return arc;
+        }
     }
     mem->bytes = total;
     std::vector<char> host(total, 0);
@@ -909,6 +911,7 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
 int compile_plan(Plan &pl)
 {
     pl.launches.clear();
+    pl.user_work.clear();
     pl.copy_host.clear();
     pl.s2 = Sten2DHost{};
     pl.fused = false;
@@ -1123,6 +1126,23 @@ int compile_plan(Plan &pl)
                 pw.push_back(t);
             }
             pw_groups.push_back({b, (int)pw.size()});
+        } else if (k.kind == K_USER) {
+            HDArrayWork_t w;
+            memset(&w, 0, sizeof(w));
+            w.dev = p;
+            for (int d = 0; d < 3; d++) {
+                w.lo[d] = W.lo[d];
+                w.hi[d] = W.hi[d];
+            }
+            for (int i = 0; i < (int)pl.args.size() && i < HDARRAY_MAX_KERNEL_ARRAYS; i++) {
+                const DevBuf &b = pl.args[i]->buf[p];
+                w.buf[i] = b.ptr;
+                for (int d = 0; d < 3; d++) {
+                    w.buf_lo[i][d] = b.alloc.lo[d];
+                    w.buf_stride[i][d] = b.st[d];
+                }
+            }
+            pl.user_work.push_back(w);
         } else if (k.kind == K_COLMEAN || k.kind == K_CENTER || k.kind == K_SYMM || k.kind == K_COLNORM ||
                    k.kind == K_COLSCALE) {
             const bool reduce_cols = k.kind == K_COLMEAN || k.kind == K_COLNORM;
@@ -1220,6 +1240,12 @@ int compile_plan(Plan &pl)
     };
     push_copy((const CopyTask *)addr[0], xfer_groups, (int64_t)xfer.size());
     push_copy((const CopyTask *)addr[1], local_groups, (int64_t)local.size());
+    if (k.kind == K_USER && !pl.user_work.empty()) {
+        LaunchRec L; L.kind = L_USER;
+        L.p0 = pl.user_work.data(); L.n0 = (int64_t)pl.user_work.size();
+        L.p1 = pl.scal.data(); L.n1 = (int64_t)pl.scal.size(); L.p2 = &k;
+        pl.launches.push_back(L);
+    }
     if (!cov.empty()) {
         LaunchRec L;
         L.kind = (k.kind == K_COLMEAN || k.kind == K_COLNORM) ? L_COLMEAN
@@ -1309,9 +1335,12 @@ int compile_plan(Plan &pl)
             pp.push_back(q);
         }
         auto panels = std::make_shared<DevMem>();
-        if (cudaMalloc(&panels->ptr, total) != cudaSuccess) {
-            cudaGetLastError();
-            return HDARRAY_ERR_NOMEM;
+        {
+            const int arc = dev_alloc(&panels->ptr, total);
+            if (arc) {
+                panels->ptr = nullptr;
+                return arc;
+            }
         }
         panels->bytes = total;
         char *base = (char *)panels->ptr;
@@ -1365,6 +1394,7 @@ int issue_recorded(const LaunchRec &L)
 {
     cudaError_t e = issue(L, g->stream);
     if (e != cudaSuccess) {
+        if (L.kind == L_USER) return user_launch_rc();  // the user launcher's own code
         if (trace()) fprintf(stderr, "hdarray: launch failed: %s\n", cudaGetErrorString(e));
         return HDARRAY_ERR_CUDA;
     }
@@ -1629,6 +1659,9 @@ int validate_args(const KernelDef &k, const Part &pt, const std::vector<HDArray 
     }
     case K_SYMM:
         if (a[0]->dim != 2 || a[0]->n[0] != a[0]->n[1]) return HDARRAY_ERR_INVAL;
+        break;
+    case K_USER:
+        if (k.narr > HDARRAY_MAX_KERNEL_ARRAYS || !k.launcher) return HDARRAY_ERR_INVAL;
         break;
     case K_GEMM:
     case K_TRMM: {
@@ -2204,7 +2237,7 @@ int abs_trap(const char *kname, int part, HDArray *a, int dev, const int64_t *c,
 void free_array_buffers(HDArray *a)
 {
     for (DevBuf &b : a->buf)
-        if (b.ptr) cudaFree(b.ptr);
+        if (b.ptr) dev_free(b.ptr);
     a->buf.clear();
 }
 
@@ -2288,8 +2321,68 @@ namespace hda {
 
 DevMem::~DevMem()
 {
-    if (ptr) cudaFree(ptr);
+    if (ptr) dev_free(ptr);
 }
+
+namespace {
+struct AllocHooks {
+    HDArrayAlloc_t alloc = nullptr;
+    HDArrayFree_t free_fn = nullptr;
+    void *user = nullptr;
+};
+AllocHooks g_hooks;
+std::unordered_map<void *, AllocHooks> g_custom;  // allocations made through a caller's allocator
+int g_user_rc = 0;                                // a user launcher's last failure code
+}  // namespace
+
+int dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (g_hooks.alloc) {
+        void *q = g_hooks.alloc(bytes, g_hooks.user);
+        if (!q) return HDARRAY_ERR_NOMEM;
+        if ((uintptr_t)q % 256 != 0) {  // the buffers' row phase and the bulk copies need it
+            g_hooks.free_fn(q, g_hooks.user);
+            return HDARRAY_ERR_INVAL;
+        }
+        g_custom[q] = g_hooks;
+        *p = q;
+        return HDARRAY_OK;
+    }
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return HDARRAY_ERR_NOMEM;
+    }
+    return HDARRAY_OK;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    auto it = g_custom.find(p);
+    if (it != g_custom.end()) {
+        const AllocHooks h = it->second;
+        g_custom.erase(it);
+        // cudaFree waits for the device; a caching allocator may hand the memory to other work at
+        // once, so wait for every queued use of it first
+        cudaDeviceSynchronize();
+        h.free_fn(p, h.user);
+        return;
+    }
+    cudaFree(p);
+}
+
+int set_allocator(HDArrayAlloc_t alloc, HDArrayFree_t free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return HDARRAY_ERR_INVAL;
+    g_hooks.alloc = alloc;
+    g_hooks.free_fn = free_fn;
+    g_hooks.user = user;
+    return HDARRAY_OK;
+}
+
+int user_launch_rc() { return g_user_rc; }
 
 cudaError_t issue(const LaunchRec &L, cudaStream_t s)
 {
@@ -2308,6 +2401,14 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
         return launch_gemm_tc((const TcPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0, (float)L.f1,
                               (unsigned *)L.p2, s);
     case L_SPLIT: return launch_split_panels((const SplitJob *)L.p0, (int)L.n0, (int)L.n1, s);
+    case L_USER: {
+        const KernelDef *kd = (const KernelDef *)L.p2;
+        const int rc = kd->launcher((const HDArrayWork_t *)L.p0, (int)L.n0, (const double *)L.p1, (int)L.n1,
+                                    (void *)s, kd->user);
+        if (rc == 0) return cudaSuccess;
+        g_user_rc = rc < 0 ? rc : HDARRAY_ERR_CUDA;
+        return cudaErrorUnknown;
+    }
     case L_COLMEAN: return launch_colmean(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n2, s);
     case L_CENTER: return launch_center(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, s);
     case L_SYMM: return launch_symmetrize(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, s);
@@ -2693,6 +2794,35 @@ static int set_offsets(const char *kName, int argIndex, int noff, const int32_t 
     (use ? k.use : k.def)[argIndex] = v;
     k.version++;
     return HDARRAY_OK;
+}
+
+int HDArrayRegisterKernel(const char *kName, int narr, int nscal, int spaceArg, HDArrayLauncher_t launcher,
+                          void *user)
+{
+    if (!g || !g->inited) return set_err(HDARRAY_ERR_STATE);
+    if (!kName || !*kName || !launcher || narr < 1 || narr > HDARRAY_MAX_KERNEL_ARRAYS || nscal < 0 ||
+        spaceArg < 0 || spaceArg >= narr)
+        return set_err(HDARRAY_ERR_INVAL);
+    auto it = g->kernels.find(kName);
+    if (it != g->kernels.end() && it->second.kind != K_USER) return set_err(HDARRAY_ERR_INVAL);
+    KernelDef k;
+    k.name = kName;
+    k.kind = K_USER;
+    k.narr = narr;
+    k.nscal_f = nscal;
+    k.space = spaceArg;
+    k.use.assign(narr, {});
+    k.def.assign(narr, {});
+    k.launcher = launcher;
+    k.user = user;
+    if (it != g->kernels.end()) k.version = it->second.version + 1;  // plans of the old one are stale
+    g->kernels[kName] = k;
+    return HDARRAY_OK;
+}
+
+int HDArraySetAllocator(HDArrayAlloc_t alloc, HDArrayFree_t free_fn, void *user)
+{
+    return set_err(set_allocator(alloc, free_fn, user));
 }
 
 int HDArraySetOffsetUse(const char *kName, int argIndex, int noff, const int32_t *offs)

@@ -11,6 +11,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "hdarray.h"
 #include "kernels.h"
 #include "sections.h"
 
@@ -22,7 +23,7 @@ struct Offset {
     int32_t o[3];
 };
 
-enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D, K_COLMEAN, K_CENTER, K_SYRK, K_SYMM, K_COLNORM, K_COLSCALE };
+enum KKind { K_JACOBI2D, K_COPY, K_STENCIL3D, K_SQDIFF, K_GEMM, K_TRMM, K_EXCHANGE, K_CONV2D, K_COLMEAN, K_CENTER, K_SYRK, K_SYMM, K_COLNORM, K_COLSCALE, K_USER };
 
 // A built-in kernel: its arguments and the use/def offsets of each array argument, the table the
 // paper's frontend builds from the pragma clauses (Sec. 4.1).
@@ -35,6 +36,8 @@ struct KernelDef {
     int space = 0;    // the argument whose index space the work partition covers
     std::vector<std::vector<Offset>> use, def;  // per array argument
     uint64_t version = 1;
+    HDArrayLauncher_t launcher = nullptr;  // user kernels (HDArrayRegisterKernel)
+    void *user = nullptr;
 };
 
 // A device buffer: the box of coordinates it covers and element strides of dimensions 0..2.
@@ -67,7 +70,7 @@ struct Part {
 
 // One kernel launch, recorded so that batches can merge it and graphs can replay it.
 enum LKind { L_COPY, L_JACOBI2D, L_SQDIFF, L_GEMM64, L_STENCIL3D, L_GEMM_TC, L_SPLIT, L_GEMM_PANEL, L_FLAT2D, L_FLAT3D, L_CONV2D,
-             L_COLMEAN, L_CENTER, L_SYMM };
+             L_COLMEAN, L_CENTER, L_SYMM, L_USER };
 struct LaunchRec {
     int kind = 0;
     int dtype = 0;
@@ -136,7 +139,15 @@ struct Plan {
     std::shared_ptr<DevMem> panels;   // pre-split bf16 operand panels (tensor-core GEMM)
     std::shared_ptr<DevMem> extra_tables;  // descriptor tables of the panel launches
     uint64_t split_version[2] = {~0ull, ~0ull};  // content versions of A and B the panels hold
+    std::vector<HDArrayWork_t> user_work;         // a user kernel's per-device work
 };
+
+// Device memory: cudaMalloc / cudaFree, or the allocator set with HDArraySetAllocator (each
+// allocation is released by the allocator that provided it).
+int dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+int set_allocator(HDArrayAlloc_t alloc, HDArrayFree_t free_fn, void *user);
+int user_launch_rc();  // the failure code of the last user launcher that failed
 
 }  // namespace hda
 

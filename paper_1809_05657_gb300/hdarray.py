@@ -85,7 +85,27 @@ SIGNATURES = {
     "HDArrayReadDeviceBuffer": (ctypes.c_int, [_P, ctypes.c_int, _I64P, _I64P, _P]),
     "HDArrayReduceBufferNoAlloc": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int, _I64P, _I64P,
                                                   ctypes.c_int, _P, _P]),
+    "HDArrayRegisterKernel": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "HDArraySetAllocator": (ctypes.c_int, [_P, _P, _P]),
 }
+
+HDARRAY_MAX_KERNEL_ARRAYS = 8
+
+
+class HDArrayWork(ctypes.Structure):
+    """HDArrayWork_t: one logical device's share of a call of a user kernel."""
+    _fields_ = [("dev", ctypes.c_int),
+                ("lo", ctypes.c_int64 * 3), ("hi", ctypes.c_int64 * 3),
+                ("buf", ctypes.c_void_p * HDARRAY_MAX_KERNEL_ARRAYS),
+                ("buf_lo", (ctypes.c_int64 * 3) * HDARRAY_MAX_KERNEL_ARRAYS),
+                ("buf_stride", (ctypes.c_int64 * 3) * HDARRAY_MAX_KERNEL_ARRAYS)]
+
+
+LAUNCHER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(HDArrayWork), ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_keep = {}  # C callbacks must outlive their registration
 
 
 def lib():
@@ -251,6 +271,33 @@ def _offs(offs):
         a[i, : len(o)] = o
     a = np.ascontiguousarray(a)
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def HDArrayRegisterKernel(kname, narr, nscal, space_arg, launcher):
+    """Register a user kernel.  launcher(work, scalars, stream) gets a list of HDArrayWork (one per
+    logical device with work), the scalars as a list of floats and the cudaStream_t as an int; it
+    queues its device work on that stream and returns 0 (or a negative error code)."""
+    def thunk(work, nwork, scal, nscal_, stream, user):
+        try:
+            rc = launcher([work[i] for i in range(nwork)], [scal[i] for i in range(nscal_)], stream or 0)
+            return int(rc or 0)
+        except Exception:
+            return -6  # HDARRAY_ERR_CUDA: the launcher raised
+    cb = LAUNCHER(thunk)
+    _keep[("kernel", kname)] = cb
+    return _chk(lib().HDArrayRegisterKernel(kname.encode(), narr, nscal, space_arg,
+                                            ctypes.cast(cb, _P), None), "HDArrayRegisterKernel")
+
+
+def HDArraySetAllocator(alloc=None, free=None):
+    """Device memory from alloc(bytes) -> int pointer and free(int pointer); None, None restores
+    cudaMalloc / cudaFree."""
+    if alloc is None and free is None:
+        return _chk(lib().HDArraySetAllocator(None, None, None), "HDArraySetAllocator")
+    a = ALLOC(lambda n, u: int(alloc(int(n)) or 0))
+    f = FREE(lambda p, u: free(int(p)))
+    _keep.setdefault("allocators", []).append((a, f))  # memory it gave out is freed through it later
+    return _chk(lib().HDArraySetAllocator(ctypes.cast(a, _P), ctypes.cast(f, _P), None), "HDArraySetAllocator")
 
 
 def HDArraySetOffsetUse(kname, arg, offs):

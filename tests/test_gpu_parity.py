@@ -63,9 +63,11 @@ def device_buffers_match(lib_run, orc_run, names):
             assert not held_out.any()
 
 
-def run_program(prog, ndev, values, gpu_lib, check_buffers=True, mode=H.HDARRAY_MODE_FUSED):
+def run_program(prog, ndev, values, gpu_lib, check_buffers=True, mode=H.HDARRAY_MODE_FUSED, setup=None):
     gpu_lib(ndev)
     H.HDArraySetMode(mode)
+    if setup:
+        setup()
     lib = LibraryRun(H, ndev)
     lib_out = lib.run(prog, values)
     orc = OracleRun(ndev)
@@ -178,12 +180,13 @@ def test_residual_flow_cfg1(gpu_lib):
     dims, P = (256, 256), 4
     x = synthetic.jacobi_field(dims, stream=0, dtype="double")
     prog, _ = jacobi_prog(dims, P, 10, ROW, "double", pingpong=False)
-    prog += [("create", "R", "double", dims), ("apply", "sqdiff", "W", ["A", "B", "R"]),
-             ("reduce", "R", 0, "W")]
+    # the residual of the last step, between the new iterate A and the old B (before the copy back)
+    prog = prog[:-1] + [("create", "R", "double", dims), ("apply", "sqdiff", "W", ["A", "B", "R"]),
+                        ("reduce", "R", 0, "W"), prog[-1]]
     lib, orc, lib_out, orc_out, _ = run_program(prog, P, {"B": x, "A": x}, gpu_lib,
                                                 mode=H.HDARRAY_MODE_PLAIN)
-    g, w = lib_out[-1]["_value"], orc_out[-1]["_value"]
-    assert abs(g - w) <= 1e-12 * abs(w)
+    g, w = lib_out[-2]["_value"], orc_out[-2]["_value"]
+    assert w > 0 and abs(g - w) <= 1e-12 * abs(w)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -877,3 +880,86 @@ def test_covariance_parity(gpu_lib, balanced, correlation, dtype, n, m, P):
     # and the oracle's matrix agrees with numpy's
     want = np.corrcoef(x.astype(np.float64), rowvar=False) if correlation else np.cov(x.astype(np.float64), rowvar=False)
     assert np.abs(orc.arrays["C"].G.astype(np.float64) - want).max() <= (1e-12 if dtype == "double" else 1e-4) * np.abs(want).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# user kernels (HDArrayRegisterKernel) and a caller-supplied allocator (HDArraySetAllocator)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["float", "double"])
+@pytest.mark.parametrize("ptype,P", [(BLOCK, 6), (COL, 5), (ROW, 3)])
+@pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
+def test_user_kernel_parity(gpu_lib, dtype, ptype, P, mode):
+    """A user kernel (torch on views of the library's buffers) behind the library's exchange:
+    messages and values equal the oracle's, including a kernel with scalars, in a graph replay."""
+    torch = pytest.importorskip("torch")
+    import user_kernels
+    user_kernels.register_oracle()
+    np_t = NP[dtype]
+
+    def setup():
+        H.HDArrayRegisterKernel("max4", 2, 0, 1, user_kernels.max4_launcher(torch, np_t))
+        H.HDArraySetOffsetUse("max4", 0, user_kernels.J4)
+        H.HDArraySetOffsetDef("max4", 1, [(0, 0)])
+        H.HDArrayRegisterKernel("axpb", 2, 2, 1, user_kernels.axpb_launcher(torch, np_t))
+        H.HDArraySetOffsetUse("axpb", 0, [(0, 0)])
+        H.HDArraySetOffsetDef("axpb", 1, [(0, 0)])
+
+    dims = (130, 117)
+    x = synthetic.to_storage(synthetic.normal(dims[0] * dims[1], stream=120).reshape(dims), dtype)
+    prog = [("create", "B", dtype, dims), ("create", "A", dtype, dims),
+            ("part", "D", ptype, dims, (0, 0), dims, P), ("part", "W", ptype, dims, (1, 1), (dims[0] - 1, dims[1] - 1), P),
+            ("write", "B", "D"), ("write", "A", "D")]
+    for i in range(4):
+        src, dst = ("B", "A") if i % 2 == 0 else ("A", "B")
+        prog.append(("apply", "max4", "W", [src, dst]))
+        prog.append(("apply", "axpb", "W", [dst, dst == "A" and "B" or "A"], (0.5, -0.25)))
+        prog.append(("apply", "max4", "W", [dst == "A" and "B" or "A", dst]))
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib, mode=mode, setup=setup)
+    for name in ("A", "B"):
+        assert np.array_equal(read_all(lib, name, dims, dtype), orc.arrays[name].G)
+
+
+def test_user_kernel_error_code(gpu_lib):
+    gpu_lib(2)
+    H.HDArrayRegisterKernel("fails", 2, 0, 1, lambda work, scal, stream: -4)
+    H.HDArraySetOffsetUse("fails", 0, [(0, 0)])
+    H.HDArraySetOffsetDef("fails", 1, [(0, 0)])
+    X = H.HDArrayCreate("X", "float", None, 16, 16)
+    Y = H.HDArrayCreate("Y", "float", None, 16, 16)
+    Pp = H.HDArrayPartition(H.ROW, (16, 16), (0, 0), (16, 16), 2)
+    with pytest.raises(H.HDArrayError) as e:
+        H.HDArrayApplyKernel("fails", Pp, X, Y)
+    assert e.value.code == -4
+
+
+def test_caller_allocator(gpu_lib):
+    """Array buffers and tables from torch's caching allocator: results unchanged, every
+    allocation and release went through it."""
+    torch = pytest.importorskip("torch")
+    calls = {"alloc": 0, "free": 0}
+    live = set()
+
+    def alloc(n):
+        p = torch.cuda.caching_allocator_alloc(n)
+        calls["alloc"] += 1
+        live.add(p)
+        return p
+
+    def free(p):
+        calls["free"] += 1
+        live.discard(p)
+        torch.cuda.caching_allocator_delete(p)
+
+    H.HDArraySetAllocator(alloc, free)
+    try:
+        dims, P = (150, 201), 4
+        x = synthetic.jacobi_field(dims, stream=121, dtype="float")
+        prog, last = jacobi_prog(dims, P, 6, BLOCK, "float", True)
+        lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+        assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+        assert calls["alloc"] > 0
+        H.HDArrayExit()
+        assert calls["free"] == calls["alloc"] and not live
+    finally:
+        H.HDArraySetAllocator(None, None)

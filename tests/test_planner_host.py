@@ -370,6 +370,40 @@ def test_covariance_messages(host_lib, balanced, correlation):
     assert run_both(prog, 4, host_lib) >= 3
 
 
+@pytest.mark.parametrize("ptype", [ROW, COL, BLOCK])
+def test_user_kernel_messages(host_lib, ptype):
+    """A registered user kernel with its own use/def offsets: the library's messages equal the
+    oracle's for the same clauses (no launcher runs without a GPU)."""
+    import user_kernels
+    user_kernels.register_oracle()
+    host_lib(5)
+    H.HDArrayRegisterKernel("max4", 2, 0, 1, lambda work, scal, stream: 0)
+    H.HDArraySetOffsetUse("max4", 0, user_kernels.J4)
+    H.HDArraySetOffsetDef("max4", 1, [(0, 0)])
+    dims = (41, 37)
+    prog = [("create", "B", "double", dims), ("create", "A", "double", dims),
+            ("part", "D", ptype, dims, (0, 0), dims, 5), ("part", "W", ptype, dims, (1, 1), (40, 36), 5),
+            ("write", "B", "D")]
+    for i in range(3):
+        prog.append(("apply", "max4", "W", ["B", "A"] if i % 2 == 0 else ["A", "B"]))
+    lib_out = LibraryRun(H, 5).run(prog)
+    orc_out = OracleRun(5).run(prog)
+    assert compare_messages(orc_out, lib_out, prog, {"B": dims, "A": dims}, 5) >= 3
+
+
+def test_user_kernel_registration_errors(host_lib):
+    host_lib(2)
+    cb = lambda work, scal, stream: 0  # noqa: E731
+    with pytest.raises(H.HDArrayError):
+        H.HDArrayRegisterKernel("jacobi2d", 2, 0, 1, cb)  # a built-in name
+    with pytest.raises(H.HDArrayError):
+        H.HDArrayRegisterKernel("k", 9, 0, 0, cb)  # too many arrays
+    with pytest.raises(H.HDArrayError):
+        H.HDArrayRegisterKernel("k", 2, 0, 2, cb)  # space argument out of range
+    H.HDArrayRegisterKernel("k", 2, 0, 1, cb)
+    H.HDArrayRegisterKernel("k", 2, 1, 1, cb)  # re-registration replaces it
+
+
 def test_2mm_row_vs_column_partition_volumes(host_lib):
     """Sec. 5.1 / Table 3: with row blocks, B is gathered once and D (redefined by the first
     product in every iteration) is gathered by every device in every iteration; with column
