@@ -69,9 +69,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit = WAIT_LIMIT)
 {
-    for (unsigned i = 0; i < WAIT_LIMIT; i++) {
+    for (unsigned i = 0; i < limit; i++) {
         if (mbar_try(bar, parity)) return true;
         __nanosleep(64);
     }
@@ -336,16 +336,19 @@ constexpr int P_STAGES = 2;
 // Warp-specialised GEMM: warp 0 lane 0 streams panel tiles into a two-stage ring with bulk copies
 // (full barriers carry the byte count), warp 1 lane 0 issues the MMAs and commits each stage back
 // to its empty barrier and the final result to the done barrier, warps 4..7 read the accumulator
-// from tensor memory and write C.  Every wait is bounded.
+// from tensor memory and write C.  Every wait is bounded: the ring's waits give up after
+// spin_limit polls (the library's setting), and then the producer waits -- with the fixed limit --
+// for the bulk copies it has issued, the MMAs already issued complete before the tensor memory is
+// released, the tile's C is left alone and the error word is set.
 __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *__restrict__ parts,
                                                                const TcTile *__restrict__ tiles, float alpha,
-                                                               float beta, unsigned *err)
+                                                               float beta, unsigned *err, unsigned spin_limit)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], done;
     __shared__ uint32_t taddr_s;
-    __shared__ int fail;
+    __shared__ volatile int fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TcTile tile = tiles[blockIdx.x];
     const PanelPart P = parts[tile.part];
@@ -373,12 +376,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
 
     if (warp == 0 && lane == 0) {  // producer
         uint32_t ph[P_STAGES] = {0u, 0u};
+        int fills[P_STAGES] = {0, 0};
         for (int kt = 0; kt < nkt && !fail; kt++) {
             const int s = kt % P_STAGES;
             if (kt >= P_STAGES) {
-                if (!mbar_wait(smem_u32(&empty[s]), ph[s])) { fail = 1; break; }
+                if (!mbar_wait(smem_u32(&empty[s]), ph[s], spin_limit)) { fail = 1; break; }
                 ph[s] ^= 1u;
             }
+            fills[s]++;
             uint8_t *st = smem + s * STAGE_BYTES;
             const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * 2) * A_BYTES;
             const uint8_t *bp = reinterpret_cast<const uint8_t *>(P.bpanel) + (size_t)((nt * P.nkt_b + kt) * 2) * B_BYTES;
@@ -387,12 +392,15 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
             bulk_g2s(smem_u32(st), ap, 2 * A_BYTES, fb);                  // A hi, A lo
             bulk_g2s(smem_u32(st + 2 * A_BYTES), bp, 2 * B_BYTES, fb);    // B hi, B lo
         }
+        if (fail)  // every bulk copy issued lands before the CTA's shared memory is released
+            for (int s = 0; s < P_STAGES; s++)
+                if (fills[s] > 0) mbar_wait(smem_u32(&full[s]), (uint32_t)((fills[s] - 1) & 1));
     } else if (warp == 1 && lane == 0) {  // MMA issuer
         uint32_t ph[P_STAGES] = {0u, 0u};
         int kt = 0;
         for (; kt < nkt && !fail; kt++) {
             const int s = kt % P_STAGES;
-            if (!mbar_wait(smem_u32(&full[s]), ph[s])) { fail = 1; break; }
+            if (!mbar_wait(smem_u32(&full[s]), ph[s], spin_limit)) { fail = 1; break; }
             ph[s] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
@@ -466,7 +474,7 @@ cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, 
 }
 
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
-                               float beta, unsigned *err, cudaStream_t s)
+                               float beta, unsigned *err, unsigned spin_limit, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     static bool attr = false;
@@ -476,7 +484,7 @@ cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_gemm_bf16x3_panels<<<ntiles, 256, sm, s>>>(parts, tiles, alpha, beta, err);
+    k_gemm_bf16x3_panels<<<ntiles, 256, sm, s>>>(parts, tiles, alpha, beta, err, spin_limit);
     return cudaGetLastError();
 }
 

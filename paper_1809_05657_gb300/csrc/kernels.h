@@ -236,8 +236,11 @@ cudaError_t launch_colmean(int dtype, const CovTask *tasks, int ntasks, int max_
 cudaError_t launch_center(int dtype, const CovTask *tasks, int ntasks, int max_rows, cudaStream_t s);
 cudaError_t launch_symmetrize(int dtype, const CovTask *tasks, int ntasks, int max_rows, int max_cols,
                               cudaStream_t s);
+// spin_limit: polls of each pipeline wait before the kernel gives up (sets *err); the waits for
+// copies and MMAs already issued always use the fixed limit.
+constexpr unsigned GEMM_SPIN_LIMIT_DEFAULT = 1u << 24;
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
-                               float beta, unsigned *err, cudaStream_t s);
+                               float beta, unsigned *err, unsigned spin_limit, cudaStream_t s);
 cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles, float alpha, float beta,
                            unsigned *err, cudaStream_t s);
 

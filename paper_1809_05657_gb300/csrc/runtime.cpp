@@ -81,6 +81,7 @@ struct Ctx {
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
     int band2 = 32;         // 2-D packed-stream variant: most 16-byte chunks per band
+    unsigned spin_limit = GEMM_SPIN_LIMIT_DEFAULT;  // polls of a GEMM pipeline wait (HDARRAY_SPIN_LIMIT)
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
@@ -1365,6 +1366,7 @@ int compile_plan(Plan &pl)
         LaunchRec SB; SB.kind = L_SPLIT; SB.p0 = pa[1]; SB.n0 = (int64_t)bjobs.size(); SB.n1 = bmax; SB.n3 = 1;
         LaunchRec GM; GM.kind = L_GEMM_PANEL; GM.p0 = pa[2]; GM.p1 = pa[3]; GM.p2 = g->err_word;
         GM.n0 = (int64_t)tt.size();
+        GM.n3 = (int64_t)g->spin_limit;
         GM.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
         GM.f1 = pl.scal.size() > 1 ? pl.scal[1] : 0.0;
         pl.launches.push_back(SA);
@@ -2306,6 +2308,8 @@ int init_impl(int ndev, unsigned flags)
         if (v3 && atoi(v3) >= 0 && atoi(v3) <= 2) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
+        const char *sl = getenv("HDARRAY_SPIN_LIMIT");
+        if (sl && *sl) g->spin_limit = (unsigned)strtoul(sl, nullptr, 10);
         const char *b3 = getenv("HDARRAY_BAND3");
         if (b3 && atoi(b3) > 0) g->band3 = atoi(b3);
         const char *c3 = getenv("HDARRAY_CTA3");
@@ -2423,7 +2427,7 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
                                      (const Seg *)L.p2, (size_t)L.n1, s);
     case L_GEMM_PANEL:
         return launch_gemm_panels((const PanelPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0,
-                                  (float)L.f1, (unsigned *)L.p2, s);
+                                  (float)L.f1, (unsigned *)L.p2, (unsigned)L.n3, s);
     default: return cudaErrorInvalidValue;
     }
 }
