@@ -47,14 +47,20 @@ struct Elem<DT_BF16> {
             a[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
         }
     }
-    __device__ static uint32_t bits(A a) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    // two values rounded to nearest even into one bfloat16 pair (the first in the low half, as
+    // stored), one conversion instruction per pair
+    __device__ static uint32_t pair(A lo, A hi)
+    {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&p);
+    }
     __device__ static V pack(const A *a)
     {
         V v;
-        v.x = bits(a[0]) | (bits(a[1]) << 16);
-        v.y = bits(a[2]) | (bits(a[3]) << 16);
-        v.z = bits(a[4]) | (bits(a[5]) << 16);
-        v.w = bits(a[6]) | (bits(a[7]) << 16);
+        v.x = pair(a[0], a[1]);
+        v.y = pair(a[2], a[3]);
+        v.z = pair(a[4], a[5]);
+        v.w = pair(a[6], a[7]);
         return v;
     }
     __device__ static A load1(const E *p) { return __bfloat162float(*p); }
