@@ -271,29 +271,56 @@ def gpu_arm(args, rank, world):
 
 
 def e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args):
-    """Same step through the public API with the input written from pinned host memory and the
-    residual read back to the host in every step."""
-    def step():
-        H.HDArrayWrite(B, xh, D)                       # host -> device, 268 MB
+    """Same step through the public API with the input coming from pinned host memory and the
+    residual read back to the host in every step.  The next step's host->device copy runs on a
+    side stream while this step computes (two device staging buffers, events between the
+    streams); HDArrayWrite then loads the staged field into the partitions' buffers."""
+    flat = xh.reshape(-1)
+    stage = [torch.empty(N * N, dtype=torch.float32, device="cuda") for _ in range(2)]
+    side = torch.cuda.Stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in used:
+        e.record(stream)
+
+    def prefetch(k):
+        slot = k % 2
+        side.wait_event(used[slot])                    # the Write that last read this buffer is done
+        with torch.cuda.stream(side):
+            stage[slot].copy_(flat, non_blocking=True)  # host -> device, 268 MB
+        copied[slot].record(side)
+
+    def step(k):
+        slot = k % 2
+        stream.wait_event(copied[slot])
+        H.HDArrayWrite(B, stage[slot], D)              # device -> partitions
+        used[slot].record(stream)
+        prefetch(k + 1)                                # overlaps this step's compute
         for _ in range(2):                             # back into the periodic state
             H.HDArrayApplyKernel("jacobi2d", W, B, A)
             H.HDArrayApplyKernel("jacobi2d", W, A, B)
         H.HDArrayGraphLaunch(gid, (ITERS - 4) // 2)
         H.HDArrayApplyKernel("sqdiff", W, B, A, R)
         return H.HDArrayReduce(R, H.SUM, W)            # device -> host, 8 bytes
+    prefetch(0)
+    k = 0
     for _ in range(max(1, args.warmup)):
-        step()
+        step(k)
+        k += 1
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(1, args.steps // 2)
     t0.record(stream)
     for _ in range(steps):
-        step()
+        step(k)
+        k += 1
+    stream.wait_event(copied[k % 2])  # the timed region holds every copy issued inside it
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     return {"value": CELLS * ITERS / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "h2d_bytes_per_step": N * N * 4, "d2h_bytes_per_step": 8}
+            "h2d_bytes_per_step": N * N * 4, "d2h_bytes_per_step": 8,
+            "note": "the next step's host->device copy overlaps this step's compute (side stream)"}
 
 
 def extra_forms(H, torch, stream, args):
