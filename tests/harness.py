@@ -235,3 +235,67 @@ def compare_messages(orc_out, lib_out, prog, dims_of, ndev, coords=None):
                                         [got[tuple(b)] for b in bad]))
             ncalls += 1
     return ncalls
+
+
+# ---------------------------------------------------------------------------------------------
+# Jacobi values at single points, for arrays too large for a whole oracle run
+# ---------------------------------------------------------------------------------------------
+
+def light_cone(x, prec, samples, T):
+    """Value after T Jacobi steps at each sample, from the oracle on the sample's light cone.
+
+    A value after T steps depends only on cells within distance T, so the oracle runs on the
+    window of radius T + 1 around the sample with the window's outer ring held fixed (the
+    array's own boundary where the window reaches it).  x is not modified."""
+    n0, n1 = x.shape
+    out = []
+    for (i, j) in samples:
+        r0, r1 = max(0, i - T - 1), min(n0, i + T + 2)
+        c0, c1 = max(0, j - T - 1), min(n1, j + T + 2)
+        B = x[r0:r1, c0:c1].copy()  # a copy even when the window is the whole array
+        A = B.copy()
+        work = np.zeros(B.shape, np.uint8)
+        gi = np.arange(r0, r1)[:, None]
+        gj = np.arange(c0, c1)[None, :]
+        inside = (gi >= 1) & (gi < n0 - 1) & (gj >= 1) & (gj < n1 - 1)
+        border = np.zeros(B.shape, bool)
+        border[0, :] = border[-1, :] = border[:, 0] = border[:, -1] = True
+        work[(inside & ~border)] = 1
+        L = oracle.lib()
+        for _ in range(T):
+            rc = L.orc_jacobi2d(prec, B.shape[0], B.shape[1], B.ctypes.data, A.ctypes.data, work.ctypes.data)
+            assert rc == 0
+            A, B = B, A
+        out.append(B[i - r0, j - c0])
+    return np.array(out)
+
+
+def light_cone3(x, prec, samples, T):
+    """The 3-D form of light_cone (7-point stencil, orc_stencil3d)."""
+    n0, n1, n2 = x.shape
+    out = []
+    L = oracle.lib()
+    for (i, j, k) in samples:
+        lo = [max(0, v - T - 1) for v in (i, j, k)]
+        hi = [min(n, v + T + 2) for v, n in zip((i, j, k), (n0, n1, n2))]
+        B = x[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].copy()
+        A = B.copy()
+        g = np.meshgrid(*[np.arange(a, b) for a, b in zip(lo, hi)], indexing="ij")
+        inside = np.ones(B.shape, bool)
+        for d, n in enumerate((n0, n1, n2)):
+            inside &= (g[d] >= 1) & (g[d] < n - 1)
+        border = np.zeros(B.shape, bool)
+        for d in range(3):
+            idx = [slice(None)] * 3
+            idx[d] = 0
+            border[tuple(idx)] = True
+            idx[d] = -1
+            border[tuple(idx)] = True
+        work = np.ascontiguousarray((inside & ~border).astype(np.uint8))
+        for _ in range(T):
+            rc = L.orc_stencil3d(prec, B.shape[0], B.shape[1], B.shape[2], B.ctypes.data, A.ctypes.data,
+                                 work.ctypes.data)
+            assert rc == 0
+            A, B = B, A
+        out.append(B[i - lo[0], j - lo[1], k - lo[2]])
+    return np.array(out)

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synthetic
-from harness import LibraryRun, OracleRun, compare_messages
+from harness import LibraryRun, OracleRun, compare_messages, light_cone, light_cone3
 
 pytestmark = pytest.mark.gpu
 
@@ -343,31 +343,6 @@ def test_graph_replay(gpu_lib, dtype):
 # full size, in the benchmark's configuration: sampled outputs against the oracle
 # ---------------------------------------------------------------------------------------------
 
-def light_cone(x, prec, samples, T):
-    """Value after T Jacobi steps at each sample, from the oracle on the sample's light cone."""
-    n0, n1 = x.shape
-    out = []
-    for (i, j) in samples:
-        r0, r1 = max(0, i - T - 1), min(n0, i + T + 2)
-        c0, c1 = max(0, j - T - 1), min(n1, j + T + 2)
-        B = np.ascontiguousarray(x[r0:r1, c0:c1])
-        A = B.copy()
-        work = np.zeros(B.shape, np.uint8)
-        gi = np.arange(r0, r1)[:, None]
-        gj = np.arange(c0, c1)[None, :]
-        inside = (gi >= 1) & (gi < n0 - 1) & (gj >= 1) & (gj < n1 - 1)
-        border = np.zeros(B.shape, bool)
-        border[0, :] = border[-1, :] = border[:, 0] = border[:, -1] = True
-        work[(inside & ~border)] = 1
-        L = oracle.lib()
-        for _ in range(T):
-            rc = L.orc_jacobi2d(prec, B.shape[0], B.shape[1], B.ctypes.data, A.ctypes.data, work.ctypes.data)
-            assert rc == 0
-            A, B = B, A
-        out.append(B[i - r0, j - c0])
-    return np.array(out)
-
-
 @pytest.mark.parametrize("dtype", ["float", "bf16"])
 def test_full_size_8192_block16_graph(gpu_lib, dtype):
     n, P, T = 8192, 16, 100
@@ -457,36 +432,6 @@ def test_stencil3d_wide_rows(gpu_lib):
     got = np.zeros(dims, np.float32)
     H.HDArrayRead(lib.arrays["A"], got, lib.parts["D"])
     assert np.array_equal(got, orc.arrays["A"].G)
-
-
-def light_cone3(x, prec, samples, T):
-    n0, n1, n2 = x.shape
-    out = []
-    L = oracle.lib()
-    for (i, j, k) in samples:
-        lo = [max(0, v - T - 1) for v in (i, j, k)]
-        hi = [min(n, v + T + 2) for v, n in zip((i, j, k), (n0, n1, n2))]
-        B = np.ascontiguousarray(x[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])
-        A = B.copy()
-        g = np.meshgrid(*[np.arange(a, b) for a, b in zip(lo, hi)], indexing="ij")
-        inside = np.ones(B.shape, bool)
-        for d, n in enumerate((n0, n1, n2)):
-            inside &= (g[d] >= 1) & (g[d] < n - 1)
-        border = np.zeros(B.shape, bool)
-        for d in range(3):
-            idx = [slice(None)] * 3
-            idx[d] = 0
-            border[tuple(idx)] = True
-            idx[d] = -1
-            border[tuple(idx)] = True
-        work = np.ascontiguousarray((inside & ~border).astype(np.uint8))
-        for _ in range(T):
-            rc = L.orc_stencil3d(prec, B.shape[0], B.shape[1], B.shape[2], B.ctypes.data, A.ctypes.data,
-                                 work.ctypes.data)
-            assert rc == 0
-            A, B = B, A
-        out.append(B[i - lo[0], j - lo[1], k - lo[2]])
-    return np.array(out)
 
 
 def test_full_size_stencil3d_512_37_boxes(gpu_lib):
@@ -963,3 +908,97 @@ def test_caller_allocator(gpu_lib):
         assert calls["free"] == calls["alloc"] and not live
     finally:
         H.HDArraySetAllocator(None, None)
+
+
+# ---------------------------------------------------------------------------------------------
+# full sizes of the batch and triangular-GEMM workloads, in the launch form bench.py times,
+# checked on sampled outputs the oracle computes one by one
+# ---------------------------------------------------------------------------------------------
+
+def test_full_size_batch_512_instances(gpu_lib):
+    """512 instances (sides log-uniform 64..2048, 2-16 ROW/COL parts, FP32), merged into one
+    launch per iteration inside a graph, 200 iterations; samples in 24 instances (partition
+    boundaries, corners, random) against the oracle's light cone."""
+    insts = synthetic.jacobi_instances(512, stream=5)
+    ndev = max(p for _, _, p, _ in insts)
+    gpu_lib(ndev)
+    arrs, xs = [], []
+    for i, (r, c, P, kind) in enumerate(insts):
+        t = ROW if kind == "ROW" else COL
+        x = synthetic.jacobi_field((r, c), stream=1000 + i, dtype="float")
+        B = H.HDArrayCreate("B", "float", None, r, c)
+        A = H.HDArrayCreate("A", "float", None, r, c)
+        D = H.HDArrayPartition(t, (r, c), (0, 0), (r, c), P)
+        W = H.HDArrayPartition(t, (r, c), (1, 1), (r - 1, c - 1), P)
+        H.HDArrayWrite(B, x, D)
+        arrs.append((B, A, D, W))
+        xs.append(x)
+
+    def iteration(flip):
+        H.HDArrayBatchBegin()
+        for B, A, D, W in arrs:
+            H.HDArrayApplyKernel("jacobi2d", W, *((A, B) if flip else (B, A)))
+        H.HDArrayBatchEnd()
+
+    T = 200
+    for _ in range(2):
+        iteration(False)
+        iteration(True)
+    H.HDArrayGraphBegin()
+    iteration(False)
+    iteration(True)
+    gid = H.HDArrayGraphEnd()  # recording also ran its two iterations
+    H.HDArrayGraphLaunch(gid, (T - 6) // 2)
+    rng = np.random.default_rng(17)
+    for i in rng.choice(len(insts), 24, replace=False):
+        r, c, P, kind = insts[i]
+        B, A, D, W = arrs[i]
+        got = np.zeros((r, c), np.float32)
+        H.HDArrayRead(B, got, D)
+        bx = oracle.partition_boxes(ROW if kind == "ROW" else COL, P, (r, c), (1, 1), (r - 1, c - 1))
+        samples = [tuple(int(v) for v in rng.integers(1, (r - 1, c - 1))) for _ in range(2)]
+        for lo, hi in bx[:3]:  # partition edges: the exchanged halo matters here
+            samples.append((lo[0], lo[1]))
+            samples.append((hi[0] - 1, hi[1] - 1))
+        want = light_cone(xs[i], 1, samples, T)
+        gotv = np.array([got[s] for s in samples])
+        assert np.array_equal(gotv, want), "instance %d" % i
+
+
+@pytest.mark.parametrize("dtype", ["double", "float"])
+def test_full_size_trmm_8192x4096(gpu_lib, dtype):
+    """tril(A) 8192^2 x B 8192x4096 on 8 row blocks with trapezoid use sections (binary64 on the
+    DFMA pipe, binary32 on the tensor cores): sampled entries against the oracle's exact binary64
+    entries (FP64 within 1e-12 relative to |A||B|, bf16x3 within its bound)."""
+    n, m, P = 8192, 4096, 8
+    a, b = synthetic.tri_gemm_inputs(n, m, stream=4, dtype=dtype)
+    gpu_lib(P)
+    A = H.HDArrayCreate("A", dtype, None, n, n)
+    B = H.HDArrayCreate("B", dtype, None, n, m)
+    C = H.HDArrayCreate("C", dtype, None, n, m)
+    R = H.HDArrayPartition(H.ROW, (n, m), (0, 0), (n, m), P)
+    RA = H.HDArrayPartition(H.ROW, (n, n), (0, 0), (n, n), P)
+    rows = [n * p // P for p in range(P + 1)]
+    for p in range(P):
+        r0, r1 = rows[p], rows[p + 1]
+        H.HDArraySetTrapezoidUse("trmm", R, A, p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1))
+    H.HDArrayWrite(A, a, RA)
+    H.HDArrayWrite(B, b, R)
+    H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)
+    got = np.zeros((n, m), NP[dtype])
+    H.HDArrayRead(C, got, R)
+    rng = np.random.default_rng(23)
+    ij = [(int(rng.integers(0, n)), int(rng.integers(0, m))) for _ in range(200)]
+    ij += [(r, 0) for r in rows[1:-1]] + [(r - 1, m - 1) for r in rows[1:]] + [(0, 0), (n - 1, m - 1)]
+    ij = np.ascontiguousarray(np.array(ij, np.int64))
+    A64, B64 = np.tril(a.astype(np.float64)), b.astype(np.float64)
+    want = np.zeros(len(ij))
+    oracle.lib().orc_gemm_entries(m, n, 1.0, 0.0, A64.ctypes.data, B64.ctypes.data, None, len(ij),
+                                  ij.ctypes.data, want.ctypes.data)
+    gotv = np.array([got[i, j] for i, j in ij], np.float64)
+    mag = np.array([np.abs(A64[i, :i + 1]) @ np.abs(B64[:i + 1, j]) for i, j in ij])
+    if dtype == "double":
+        assert (np.abs(gotv - want) <= 1e-12 * mag).all()
+    else:
+        k = np.array([i + 1 for i, _ in ij])
+        assert (np.abs(gotv - want) <= 2 * (3 * 2.0 ** -16 + (k + 2) * 2.0 ** -24) * mag).all()
