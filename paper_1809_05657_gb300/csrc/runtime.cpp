@@ -85,6 +85,7 @@ struct Ctx {
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
+    int row_align = 16;     // bytes: device buffer rows start and end on this boundary (16 .. 1024)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
     bool tuning = false;  // compile_plan is being called by the tuner
@@ -338,13 +339,15 @@ int ensure_buffer(HDArray *a, int p, const Box &need)
     if (b.ptr && box_contains(b.alloc, need)) return HDARRAY_OK;
     if (g->recording) g->rec_invalid = true;  // recorded launches would point at the old buffer
     Box nb = b.ptr ? box_hull(b.alloc, need) : need;
-    // Innermost dimension: rows padded to whole 128-byte lines, with the origin at 1 (mod the line)
-    // in array coordinates, the same for every buffer.  Coordinate 1 -- the first element after a
-    // one-element boundary ring -- and every 128 bytes after it then start a line, so a work region
-    // that starts right after the ring is chunk-aligned for 16-byte vector access, and two buffers
-    // always agree on which coordinates are vector-aligned.
+    // Innermost dimension: rows padded to whole row_align-byte units (16 bytes unless set), with
+    // the origin at 1 (mod the unit) in array coordinates, the same for every buffer.  Coordinate 1
+    // -- the first element after a one-element boundary ring -- and every unit after it then start
+    // a 16-byte chunk, so a work region that starts right after the ring is chunk-aligned for
+    // vector access, and two buffers always agree on which coordinates are vector-aligned.  The
+    // smallest unit keeps the rows of a narrow partition dense: consecutive rows share DRAM
+    // sectors instead of each row touching its own partly used 128-byte line.
     const int in = a->dim - 1;
-    const int64_t al = 128 / a->esize;
+    const int64_t al = std::max<int64_t>(1, g->row_align / a->esize);
     nb.lo[in] = align_down(nb.lo[in] - 1, al) + 1;
     nb.hi[in] = align_up(nb.hi[in] - 1, al) + 1;
     DevBuf nbuf;
@@ -2298,6 +2301,8 @@ int init_impl(int ndev, unsigned flags)
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
         if (vv && atoi(vv) >= 0 && atoi(vv) <= 4) g->variant = atoi(vv);
+        const char *ra = getenv("HDARRAY_ROW_ALIGN");
+        if (ra && atoi(ra) >= 16 && atoi(ra) <= 1024 && (atoi(ra) & (atoi(ra) - 1)) == 0) g->row_align = atoi(ra);
         const char *b2 = getenv("HDARRAY_BAND2");
         if (b2 && atoi(b2) > 0) g->band2 = atoi(b2);
         const char *at = getenv("HDARRAY_AUTOTUNE");
