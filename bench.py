@@ -178,6 +178,23 @@ def tune_report(path):
     return out
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every replica's timed region ends before the job's does."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, world, ms):
+    """Whole-job rate of `world` independent replicas that each processed units_per_rank units
+    in at most ms milliseconds (weak scaling: the per-GPU work is fixed)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def gpu_arm(args, rank, world):
     import numpy as np
     import torch
@@ -243,19 +260,14 @@ def gpu_arm(args, rank, world):
         t1.record(stream)
         torch.cuda.synchronize()
     c1 = H.HDArrayGetCounters()
-    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(t0.elapsed_time(t1), world, "cuda")
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     launches = c1["launches"] - c0["launches"]
     per_launch_ms = kernel_ms / (args.steps * ITERS)
     algo_bytes = CELLS * 8 + 2 * xbytes
     hbm, src = peaks()
     achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
-    value = world * CELLS * ITERS * args.steps / (ms * 1e-3) / 1e9
+    value = replica_rate(CELLS * ITERS * args.steps, world, ms) / 1e9
 
     # end to end: inputs from pinned host memory, the residual back to the host
     e2e = None
