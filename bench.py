@@ -814,21 +814,24 @@ def workload_trmm(H, torch, stream, args):
     H.HDArrayExit()
     hbm, src = peaks()
     out = {"workload": "tril(A) 8192x8192 x B 8192x4096, 8 row partitions; FP64 plain form (DFMA) and "
-                       "FP32 arrays on BF16 tensor cores (bf16x3)",
+                       "FP32 arrays on BF16 tensor cores (bf16x3, and bf16x6 for binary32 accuracy)",
            "metric": "TFLOP/s (algorithmic)", "fp64": {"value": flops / (ms * 1e-3) / 1e12, "ms_per_call": ms},
            "exchange": {"bytes": moved, "ms": exch_ms, "GB_s": 2 * moved / (exch_ms * 1e-3) / 1e9,
                         "hbm_frac": 2 * moved / (exch_ms * 1e-3) / 1e9 / hbm, "peak_source": src}}
     if not args.quick:
-        out["bf16x3"] = trmm_bf16x3(H, torch, stream, args, a, b)
+        out["bf16x3"] = trmm_tc(H, torch, stream, args, a, b, 2)
+        out["bf16x6"] = trmm_tc(H, torch, stream, args, a, b, 3)
         out["value"] = out["bf16x3"]["tflops_algorithmic"]
     else:
         out["value"] = out["fp64"]["value"]
     return out
 
 
-def trmm_bf16x3(H, torch, stream, args, a64, b64):
-    """The same triangular product on binary32 arrays with the tensor-core bf16x3 kernel; error
-    against binary64 on sampled entries (the binary64 product of the binary32 inputs)."""
+def trmm_tc(H, torch, stream, args, a64, b64, split):
+    """The same triangular product on binary32 arrays on the tensor cores, in the bf16x3 (split 2)
+    or bf16x6 (split 3) form; error against binary64 on sampled entries (the binary64 product of
+    the binary32 inputs), among them the first rows, where few terms leave the split's error
+    unaveraged."""
     import numpy as np
     import oracle
     n, m, P = 8192, 4096, 8
@@ -836,6 +839,7 @@ def trmm_bf16x3(H, torch, stream, args, a64, b64):
     b = b64.astype(np.float32)
     H.HDArrayInit(ndev=P)
     H.HDArraySetStream(stream.cuda_stream)
+    H.HDArraySetGemmSplit(split)
     A = H.HDArrayCreate("A", "float", None, n, n)
     B = H.HDArrayCreate("B", "float", None, n, m)
     C = H.HDArrayCreate("C", "float", None, n, m)
@@ -856,16 +860,18 @@ def trmm_bf16x3(H, torch, stream, args, a64, b64):
     H.HDArrayExit()
     rng = np.random.default_rng(4)
     ij = np.stack([rng.integers(0, n, 256), rng.integers(0, m, 256)], 1)
-    ij = np.concatenate([ij, [[0, 0], [1, 5], [127, 4095], [128, 1], [8191, 4095], [4095, 2048]]])
+    ij = np.concatenate([ij, [[0, 0], [1, 5], [127, 4095], [128, 1], [8191, 4095], [4095, 2048]],
+                         [[i, j] for i in range(4) for j in rng.integers(0, m, 64)]])
     ref = oracle.gemm_entries(np.tril(a.astype(np.float64)), b.astype(np.float64), None, 1.0, 0.0, ij)
     mag = np.array([np.abs(a[i, :i + 1].astype(np.float64)) @ np.abs(b[:i + 1, j].astype(np.float64))
                     for i, j in ij])
     g = got[ij[:, 0], ij[:, 1]].astype(np.float64)
     flops = 2.0 * m * (n * (n + 1) / 2)
-    issued = 0.0  # MMA flops actually issued: 3 products per K step, whole 128 x 256 tiles
+    products = 3 if split == 2 else 6
+    issued = 0.0  # MMA flops actually issued: 3 or 6 products per K step over whole 128-row tiles
     for ti in range(0, n, 128):
         kend = min(n, ti + 128)
-        issued += 3 * 2.0 * 128 * m * ((kend + 63) // 64 * 64)
+        issued += products * 2.0 * 128 * m * ((kend + 63) // 64 * 64)
     try:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
     except Exception:
@@ -875,7 +881,7 @@ def trmm_bf16x3(H, torch, stream, args, a64, b64):
             "tensor_frac": issued / (ms * 1e-3) / 1e12 / peak, "peak_tflops": peak,
             "err_componentwise_max": float((np.abs(g - ref) / mag).max()),
             "err_normwise": float(np.abs(g - ref).max() / np.abs(ref).max()),
-            "samples": int(len(ij))}
+            "samples": int(len(ij)), "products_per_k_step": products}
 
 
 def run_workload(args):

@@ -222,6 +222,17 @@ int HDArraySetStream(void *stream);
 /* HDARRAY_MODE_FUSED (default) or HDARRAY_MODE_PLAIN. */
 int HDArraySetMode(int mode);
 
+/* Precision form of binary32 GEMMs (gemm, trmm, syrk) on the tensor cores, after Henry, Tang &
+ * Heinecke (ARITH 2019): HDARRAY_GEMM_BF16X3 (default) splits every operand value into two
+ * bfloat16 parts and keeps three products per pair (about 3 * 2^-16 of |a||b| per product);
+ * HDARRAY_GEMM_BF16X6 splits into three parts and keeps six products (about 2^-22), as accurate
+ * as binary32 products, at twice the tensor work.  Plans compiled for the other form are
+ * recompiled on their next call; graphs recorded before keep the form they recorded.  Returns
+ * HDARRAY_ERR_INVAL for another value, HDARRAY_ERR_STATE inside a batch or a graph recording. */
+#define HDARRAY_GEMM_BF16X3 2
+#define HDARRAY_GEMM_BF16X6 3
+int HDArraySetGemmSplit(int parts);
+
 /* Tile-shape autotuning of the fused stencil launches (also enabled by HDARRAY_AUTOTUNE=1): the
  * first time a stencil plan of a new (kernel, type, partition shape) is compiled in its fused form,
  * the candidate tile shapes are timed on the GPU and the fastest is kept (in memory, and appended

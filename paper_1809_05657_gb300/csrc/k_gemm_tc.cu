@@ -270,16 +270,45 @@ cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles,
 // ==========================================================================================
 // Pre-split operand panels and the pipelined tensor-core GEMM.
 //
-// Panels: the bf16 hi and lo parts of A (per device, its 128-row tiles) and of B^T (256-column
-// tiles), each 128 x 64 (A) or 256 x 64 (B) tile stored contiguously in exactly the K-major
-// 128-byte-swizzled layout the MMA reads, so a K step of a CTA is four contiguous bulk copies.
-// A panel tile (mt, kt) part q sits at ((mt * nkt + kt) * 2 + q) * A_BYTES; a B panel tile
-// (nt, kt) part q at ((nt * nkt + kt) * 2 + q) * B_BYTES.
+// Panels: the bf16 parts of A (per device, its 128-row tiles) and of B^T (column tiles of the
+// CTA width), each 128 x 64 (A) or BNp x 64 (B) tile stored contiguously in exactly the K-major
+// 128-byte-swizzled layout the MMA reads, so a K step of a CTA is two contiguous bulk copies.
+// With NSP parts per operand (2: hi, lo -- "bf16x3"; 3: hi, mid, lo -- "bf16x6"), a panel tile
+// (mt, kt) part q sits at ((mt * nkt + kt) * NSP + q) * A_BYTES and a B panel tile (nt, kt) part q
+// at ((nt * nkt + kt) * NSP + q) * BNp * 128.
+//
+// bf16x6 (the same paper's higher-accuracy form): x = hi + mid + lo with hi = bf16(x),
+// mid = bf16(x - hi), lo = bf16(x - hi - mid) (both differences exact in binary32), and the six
+// products whose magnitude is at least about 2^-16 of a*b are kept: hi*hi, hi*mid, mid*hi, hi*lo,
+// mid*mid, lo*hi.  The split leaves about 2^-24 of each operand and the dropped products
+// (mid*lo, lo*mid, lo*lo) about 2^-23 of a*b, so the result is as accurate as binary32 products.
+// Its CTA tile is 128 x 128 (three parts of A and of B fill the same 96 KB stage as two parts of
+// a 128 x 256 tile).
 // ==========================================================================================
 
 namespace {
 
-// One CTA per (tile, part pair): thread -> 16-byte chunk (row r, 8 consecutive k), both parts.
+// bf16 hi / mid / lo split of one binary32 value
+__device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l)
+{
+    const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(bh);
+    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(bm);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
+__device__ __forceinline__ uint4 pack8(const uint16_t *v)
+{
+    uint4 u;
+    u.x = v[0] | ((uint32_t)v[1] << 16); u.y = v[2] | ((uint32_t)v[3] << 16);
+    u.z = v[4] | ((uint32_t)v[5] << 16); u.w = v[6] | ((uint32_t)v[7] << 16);
+    return u;
+}
+
+// One CTA per (tile, part set): thread -> 16-byte chunk (row r, 8 consecutive k), every part.
 __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict__ jobs)
 {
     const SplitJob J = jobs[blockIdx.y];
@@ -287,15 +316,15 @@ __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict_
     const int tile = blockIdx.x;      // row tile * nkt + k tile
     if (tile >= J.ntiles) return;
     const int mt = tile / tiles_per_row, kt = tile - mt * tiles_per_row;
-    const int rows = J.rows_per_tile;  // 128 (A) or 256 (B)
+    const int rows = J.rows_per_tile;  // 128 (A) or the CTA width (B)
+    const int nsp = J.nparts;          // 2 or 3
     const float *src = reinterpret_cast<const float *>(J.src);
-    uint8_t *hi = reinterpret_cast<uint8_t *>(J.dst) + (size_t)tile * 2 * rows * 128;
-    uint8_t *lo = hi + (size_t)rows * 128;
+    uint8_t *part0 = reinterpret_cast<uint8_t *>(J.dst) + (size_t)tile * nsp * rows * 128;
     for (int q = threadIdx.x; q < rows * 8; q += blockDim.x) {
         const int r = J.transpose ? (q & (rows - 1)) : (q >> 3);
         const int c = J.transpose ? (q / rows) : (q & 7);
         const int row = J.row0 + mt * rows + r;  // A: row i; B: column n
-        uint16_t h[8], l[8];
+        uint16_t h[8], m[8], l[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) {
             const int k = kt * 64 + c * 8 + e;
@@ -304,15 +333,18 @@ __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict_
                 if (J.transpose) v = src[(int64_t)(k - J.lo0) * J.stride + (row - J.lo1)];  // B[k][n]
                 else v = src[(int64_t)(row - J.lo0) * J.stride + (k - J.lo1)];             // A[i][k]
             }
-            split(v, h[e], l[e]);
+            if (nsp == 3) split3(v, h[e], m[e], l[e]);
+            else split(v, h[e], l[e]);
         }
-        uint4 H, L;
-        H.x = h[0] | ((uint32_t)h[1] << 16); H.y = h[2] | ((uint32_t)h[3] << 16);
-        H.z = h[4] | ((uint32_t)h[5] << 16); H.w = h[6] | ((uint32_t)h[7] << 16);
-        L.x = l[0] | ((uint32_t)l[1] << 16); L.y = l[2] | ((uint32_t)l[3] << 16);
-        L.z = l[4] | ((uint32_t)l[5] << 16); L.w = l[6] | ((uint32_t)l[7] << 16);
-        *reinterpret_cast<uint4 *>(hi + sw_off(r, c)) = H;
-        *reinterpret_cast<uint4 *>(lo + sw_off(r, c)) = L;
+        const uint32_t off = sw_off(r, c);
+        const size_t pb = (size_t)rows * 128;
+        *reinterpret_cast<uint4 *>(part0 + off) = pack8(h);
+        if (nsp == 3) {
+            *reinterpret_cast<uint4 *>(part0 + pb + off) = pack8(m);
+            *reinterpret_cast<uint4 *>(part0 + 2 * pb + off) = pack8(l);
+        } else {
+            *reinterpret_cast<uint4 *>(part0 + pb + off) = pack8(l);
+        }
     }
 }
 
@@ -331,6 +363,27 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
 
 constexpr int P_STAGES = 2;
 
+// Panel GEMM geometry for NSP bf16 parts per operand.
+template <int NSP>
+struct PanelGeo {
+    static constexpr int BNp = NSP == 3 ? 128 : 256;              // CTA tile width
+    static constexpr int B_BYTESp = BNp * BK * 2;                 // one part of the B slice
+    static constexpr int STAGEp = NSP * A_BYTES + NSP * B_BYTESp;  // 96 KB for both forms
+    static constexpr uint32_t IDESCp = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNp >> 3) << 17) |
+                                       ((uint32_t)(BM >> 4) << 24);
+};
+static_assert(PanelGeo<2>::STAGEp == STAGE_BYTES && PanelGeo<3>::STAGEp == STAGE_BYTES, "stage size");
+
+__device__ __forceinline__ void mma_bf16_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 }  // namespace
 
 // Warp-specialised GEMM: warp 0 lane 0 streams panel tiles into a two-stage ring with bulk copies
@@ -340,10 +393,14 @@ constexpr int P_STAGES = 2;
 // spin_limit polls (the library's setting), and then the producer waits -- with the fixed limit --
 // for the bulk copies it has issued, the MMAs already issued complete before the tensor memory is
 // released, the tile's C is left alone and the error word is set.
+template <int NSP>
 __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *__restrict__ parts,
                                                                const TcTile *__restrict__ tiles, float alpha,
                                                                float beta, unsigned *err, unsigned spin_limit)
 {
+    using G = PanelGeo<NSP>;
+    constexpr int BNp = G::BNp;
+    constexpr uint32_t TMEM_COLSp = (uint32_t)BNp;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], done;
@@ -354,7 +411,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     const PanelPart P = parts[tile.part];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
-                     "r"(TMEM_COLS)
+                     "r"(TMEM_COLSp)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -372,7 +429,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = taddr_s;
     const int nkt = (tile.kend + BK - 1) / BK;
-    const int mt = (tile.i0 - P.row0) / BM, nt = (tile.j0 - P.col0) / BN;
+    const int mt = (tile.i0 - P.row0) / BM, nt = (tile.j0 - P.col0) / BNp;
 
     if (warp == 0 && lane == 0) {  // producer
         uint32_t ph[P_STAGES] = {0u, 0u};
@@ -384,13 +441,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
                 ph[s] ^= 1u;
             }
             fills[s]++;
-            uint8_t *st = smem + s * STAGE_BYTES;
-            const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * 2) * A_BYTES;
-            const uint8_t *bp = reinterpret_cast<const uint8_t *>(P.bpanel) + (size_t)((nt * P.nkt_b + kt) * 2) * B_BYTES;
+            uint8_t *st = smem + s * G::STAGEp;
+            const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * NSP) * A_BYTES;
+            const uint8_t *bp = reinterpret_cast<const uint8_t *>(P.bpanel) + (size_t)((nt * P.nkt_b + kt) * NSP) * G::B_BYTESp;
             const uint32_t fb = smem_u32(&full[s]);
-            mbar_expect(fb, (uint32_t)STAGE_BYTES);
-            bulk_g2s(smem_u32(st), ap, 2 * A_BYTES, fb);                  // A hi, A lo
-            bulk_g2s(smem_u32(st + 2 * A_BYTES), bp, 2 * B_BYTES, fb);    // B hi, B lo
+            mbar_expect(fb, (uint32_t)G::STAGEp);
+            bulk_g2s(smem_u32(st), ap, NSP * A_BYTES, fb);                     // every part of A
+            bulk_g2s(smem_u32(st + NSP * A_BYTES), bp, NSP * G::B_BYTESp, fb);  // every part of B
         }
         if (fail)  // every bulk copy issued lands before the CTA's shared memory is released
             for (int s = 0; s < P_STAGES; s++)
@@ -403,14 +460,19 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
             if (!mbar_wait(smem_u32(&full[s]), ph[s], spin_limit)) { fail = 1; break; }
             ph[s] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_hi = st, a_lo = st + A_BYTES, b_hi = st + 2 * A_BYTES, b_lo = st + 2 * A_BYTES + B_BYTES;
+            const uint32_t st = smem_u32(smem + s * G::STAGEp);
+            const uint32_t a0 = st, b0 = st + NSP * A_BYTES;  // part q at + q * A_BYTES / B_BYTESp
 #pragma unroll
             for (int kk = 0; kk < BK / 16; kk++) {
                 const uint32_t off = kk * 32;
-                mma_bf16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (kt > 0 || kk > 0) ? 1u : 0u);
-                mma_bf16(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1u);
-                mma_bf16(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+                // (A part, B part) pairs: x3 keeps (0,0) (0,1) (1,0); x6 adds (0,2) (1,1) (2,0)
+#pragma unroll
+                for (int pr = 0; pr < (NSP == 3 ? 6 : 3); pr++) {
+                    const int qa = pr == 2 ? 1 : pr == 4 ? 1 : pr == 5 ? 2 : 0;
+                    const int qb = pr == 1 ? 1 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+                    mma_bf16_id(tmem, sw128_desc(a0 + qa * A_BYTES + off), sw128_desc(b0 + qb * G::B_BYTESp + off),
+                                G::IDESCp, (kt > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&empty[s]))
@@ -430,7 +492,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
         const int lane_base = 32 * (warp & 3);
         const int i = tile.i0 + lane_base + lane;
         float *C = reinterpret_cast<float *>(P.c);
-        for (int cc = 0; cc < BN / 32; cc++) {
+        for (int cc = 0; cc < BNp / 32; cc++) {
             uint32_t r[32];
             const uint32_t ta = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(cc * 32);
             asm volatile(
@@ -462,7 +524,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLSp) : "memory");
 }
 
 cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s)
@@ -474,17 +536,19 @@ cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, 
 }
 
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
-                               float beta, unsigned *err, unsigned spin_limit, cudaStream_t s)
+                               float beta, unsigned *err, unsigned spin_limit, int nparts, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    static bool attr = false;
+    if (nparts != 2 && nparts != 3) return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};
     const size_t sm = (size_t)P_STAGES * STAGE_BYTES + 1024;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3_panels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto fn = nparts == 3 ? k_gemm_bf16x3_panels<3> : k_gemm_bf16x3_panels<2>;
+    if (!attr[nparts - 2]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[nparts - 2] = true;
     }
-    k_gemm_bf16x3_panels<<<ntiles, 256, sm, s>>>(parts, tiles, alpha, beta, err, spin_limit);
+    fn<<<ntiles, 256, sm, s>>>(parts, tiles, alpha, beta, err, spin_limit);
     return cudaGetLastError();
 }
 

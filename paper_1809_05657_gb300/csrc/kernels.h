@@ -196,9 +196,10 @@ struct SplitJob {
     int32_t row0, row_end;     // A: rows of C's row tiles; B: columns of C's column tiles
     int32_t kend;              // K extent
     int32_t nkt, ntiles;       // k tiles per row tile, total tiles
-    int32_t rows_per_tile;     // 128 (A) or 256 (B)
+    int32_t rows_per_tile;     // 128 (A) or the GEMM's CTA width (B: 256 for 2 parts, 128 for 3)
     int32_t transpose;         // 1 for B (stored as B^T)
     int32_t lower;             // A lower triangular
+    int32_t nparts;            // bf16 parts per value: 2 (hi, lo) or 3 (hi, mid, lo)
 };
 struct PanelPart {
     const void *apanel;  // A panel of this device's rows (row tiles from row0)
@@ -210,7 +211,7 @@ struct PanelPart {
     int32_t nkt, nkt_b;  // k tiles per row tile in the A and B panels
     int32_t col0;        // first column of the device's column tiles
     int32_t upper;       // store only the elements with j >= i
-    int32_t pad;
+    int32_t nparts;      // bf16 parts per operand value: 2 (bf16x3) or 3 (bf16x6)
 };
 cudaError_t launch_split_panels(const SplitJob *jobs, int njobs, int max_tiles, cudaStream_t s);
 
@@ -239,8 +240,9 @@ cudaError_t launch_symmetrize(int dtype, const CovTask *tasks, int ntasks, int m
 // spin_limit: polls of each pipeline wait before the kernel gives up (sets *err); the waits for
 // copies and MMAs already issued always use the fixed limit.
 constexpr unsigned GEMM_SPIN_LIMIT_DEFAULT = 1u << 24;
+// nparts 2: bf16x3 products, 128 x 256 CTA tiles; 3: bf16x6 products, 128 x 128 CTA tiles.
 cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int ntiles, float alpha,
-                               float beta, unsigned *err, unsigned spin_limit, cudaStream_t s);
+                               float beta, unsigned *err, unsigned spin_limit, int nparts, cudaStream_t s);
 cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles, float alpha, float beta,
                            unsigned *err, cudaStream_t s);
 

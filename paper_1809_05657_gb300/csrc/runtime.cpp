@@ -85,6 +85,7 @@ struct Ctx {
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
+    int gemm_parts = 2;     // binary32 GEMM on tensor cores: 2 bf16 parts (bf16x3) or 3 (bf16x6)
     int row_align = 16;     // bytes: device buffer rows start and end on this boundary (16 .. 1024)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
     bool autotune = false;
@@ -1198,9 +1199,10 @@ int compile_plan(Plan &pl)
                 t.i1 = q.i1; t.j1 = q.j1; t.lower = q.lower; t.pad = 0;
                 const int pi = (int)tp.size();
                 tp.push_back(t);
+                const int tcbn = g->gemm_parts == 3 ? 128 : 256;  // CTA tile width of the form
                 for (int ti = q.i0; ti < q.i1; ti += 128)
-                    for (int tj = q.j0; tj < q.j1; tj += 256) {
-                        if (q.upper && tj + 255 < ti) continue;  // entirely below the diagonal
+                    for (int tj = q.j0; tj < q.j1; tj += tcbn) {
+                        if (q.upper && tj + tcbn - 1 < ti) continue;  // entirely below the diagonal
                         TcTile x;
                         x.part = pi; x.i0 = ti; x.j0 = tj;
                         x.kend = q.lower ? std::min(q.nk, std::min(ti + 128, q.i1)) : q.nk;
@@ -1287,7 +1289,9 @@ int compile_plan(Plan &pl)
     bool panel_ok = !tt.empty();
     for (const TcPart &t : tp) panel_ok = panel_ok && t.j1 > 0;
     const bool syrk = k.kind == K_SYRK;  // only the panel kernel reads A transposed
-    if (panel_ok && (syrk || getenv("HDARRAY_GEMM_NO_PANELS") == nullptr)) {
+    const int nsp = g->gemm_parts;       // bf16 parts per value (3: only the panel kernel has it)
+    const int tcbn = nsp == 3 ? 128 : 256;
+    if (panel_ok && (syrk || nsp == 3 || getenv("HDARRAY_GEMM_NO_PANELS") == nullptr)) {
         HDArray *A = pl.args[0], *B = syrk ? pl.args[0] : pl.args[1];
         const int64_t nk = syrk ? A->n[0] : A->n[1];
         const int nkt_b = (int)((nk + 63) / 64);
@@ -1304,7 +1308,7 @@ int compile_plan(Plan &pl)
             if (!aoff.count(ka)) {
                 const int nmt = (int)((W.hi[0] - W.lo[0] + 127) / 128);
                 aoff[ka] = total;
-                total += (size_t)nmt * nkt * 2 * (128 * 64 * 2);
+                total += (size_t)nmt * nkt * nsp * (128 * 64 * 2);
                 SplitJob J;
                 const DevBuf &ba = A->buf[p];
                 J.src = ba.ptr; J.dst = (void *)(uintptr_t)aoff[ka];  // offset until the panels exist
@@ -1312,18 +1316,20 @@ int compile_plan(Plan &pl)
                 J.row0 = (int32_t)W.lo[0]; J.row_end = (int32_t)W.hi[0]; J.kend = (int32_t)kend;
                 J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = syrk ? 1 : 0;
                 J.lower = k.kind == K_TRMM ? 1 : 0;
+                J.nparts = nsp;
                 ajobs.push_back(J);
             }
             if (!boff.count(kb)) {
-                const int nnt = (int)((W.hi[1] - W.lo[1] + 255) / 256);
+                const int nnt = (int)((W.hi[1] - W.lo[1] + tcbn - 1) / tcbn);
                 boff[kb] = total;
-                total += (size_t)nnt * nkt_b * 2 * (256 * 64 * 2);
+                total += (size_t)nnt * nkt_b * nsp * ((size_t)tcbn * 64 * 2);
                 SplitJob J;
                 const DevBuf &bb = B->buf[p];
                 J.src = bb.ptr; J.dst = (void *)(uintptr_t)boff[kb];
                 J.lo0 = bb.alloc.lo[0]; J.lo1 = bb.alloc.lo[1]; J.stride = bb.st[0];
                 J.row0 = (int32_t)W.lo[1]; J.row_end = (int32_t)W.hi[1]; J.kend = (int32_t)nk;
-                J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = 256; J.transpose = 1; J.lower = 0;
+                J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = tcbn; J.transpose = 1; J.lower = 0;
+                J.nparts = nsp;
                 bjobs.push_back(J);
             }
             PanelPart q;
@@ -1335,7 +1341,7 @@ int compile_plan(Plan &pl)
             q.row0 = (int32_t)W.lo[0]; q.col0 = (int32_t)W.lo[1];
             q.i1 = (int32_t)W.hi[0]; q.j1 = (int32_t)W.hi[1];
             q.nkt = nkt; q.nkt_b = nkt_b;
-            q.upper = syrk ? 1 : 0; q.pad = 0;
+            q.upper = syrk ? 1 : 0; q.nparts = nsp;
             pp.push_back(q);
         }
         auto panels = std::make_shared<DevMem>();
@@ -1369,6 +1375,7 @@ int compile_plan(Plan &pl)
         LaunchRec SB; SB.kind = L_SPLIT; SB.p0 = pa[1]; SB.n0 = (int64_t)bjobs.size(); SB.n1 = bmax; SB.n3 = 1;
         LaunchRec GM; GM.kind = L_GEMM_PANEL; GM.p0 = pa[2]; GM.p1 = pa[3]; GM.p2 = g->err_word;
         GM.n0 = (int64_t)tt.size();
+        GM.n1 = nsp;
         GM.n3 = (int64_t)g->spin_limit;
         GM.f0 = pl.scal.size() > 0 ? pl.scal[0] : 1.0;
         GM.f1 = pl.scal.size() > 1 ? pl.scal[1] : 0.0;
@@ -2432,7 +2439,7 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
                                      (const Seg *)L.p2, (size_t)L.n1, s);
     case L_GEMM_PANEL:
         return launch_gemm_panels((const PanelPart *)L.p0, (const TcTile *)L.p1, (int)L.n0, (float)L.f0,
-                                  (float)L.f1, (unsigned *)L.p2, (unsigned)L.n3, s);
+                                  (float)L.f1, (unsigned *)L.p2, (unsigned)L.n3, (int)L.n1, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -2862,6 +2869,19 @@ int HDArraySetMode(int mode)
     if (mode != g->mode) {
         g->mode = mode;
         for (auto &kv : g->memo) kv.second->compiled_sig.clear();
+        g->batch_cache.clear();
+    }
+    return HDARRAY_OK;
+}
+
+int HDArraySetGemmSplit(int parts)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (parts != HDARRAY_GEMM_BF16X3 && parts != HDARRAY_GEMM_BF16X6) return HDARRAY_ERR_INVAL;
+    if (g->recording || g->batching) return HDARRAY_ERR_STATE;
+    if (parts != g->gemm_parts) {
+        g->gemm_parts = parts;
+        for (auto &kv : g->memo) kv.second->compiled_sig.clear();  // recompiled on their next use
         g->batch_cache.clear();
     }
     return HDARRAY_OK;

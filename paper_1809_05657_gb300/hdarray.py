@@ -21,6 +21,7 @@ HDARRAY_SUM, HDARRAY_PROD, HDARRAY_MAX, HDARRAY_MIN = 0, 1, 2, 3
 SUM, PROD, MAX, MIN = HDARRAY_SUM, HDARRAY_PROD, HDARRAY_MAX, HDARRAY_MIN
 HDARRAY_ALL = -(2 ** 31)
 HDARRAY_MODE_FUSED, HDARRAY_MODE_PLAIN = 0, 1
+HDARRAY_GEMM_BF16X3, HDARRAY_GEMM_BF16X6 = 2, 3
 HDARRAY_INIT_HOST_ONLY = 1
 
 ERRORS = {0: "ok", -1: "INVAL", -2: "NOMEM", -3: "RACE", -4: "RANGE", -5: "TIMEOUT", -6: "CUDA",
@@ -68,6 +69,7 @@ SIGNATURES = {
     "HDArrayNumDevices": (ctypes.c_int, []),
     "HDArraySetStream": (ctypes.c_int, [_P]),
     "HDArraySetMode": (ctypes.c_int, [ctypes.c_int]),
+    "HDArraySetGemmSplit": (ctypes.c_int, [ctypes.c_int]),
     "HDArraySetAutotune": (ctypes.c_int, [ctypes.c_int]),
     "HDArrayBatchBegin": (ctypes.c_int, []),
     "HDArrayBatchEnd": (ctypes.c_int, []),
@@ -317,6 +319,11 @@ def HDArraySetStream(stream=None):
 
 def HDArraySetMode(mode):
     return _chk(lib().HDArraySetMode(mode), "HDArraySetMode")
+
+
+def HDArraySetGemmSplit(parts):
+    """HDARRAY_GEMM_BF16X3 (2 bf16 parts per value) or HDARRAY_GEMM_BF16X6 (3 parts)."""
+    return _chk(lib().HDArraySetGemmSplit(parts), "HDArraySetGemmSplit")
 
 
 def HDArraySetAutotune(on=True):

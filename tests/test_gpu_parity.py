@@ -479,10 +479,22 @@ def _bf16x3_bound(A, B, C0, alpha, beta, k):
     return (3 * 2.0 ** -16 + (k + 2) * 2.0 ** -24) * mag + 1e-30
 
 
-@pytest.mark.parametrize("panels", [True, False])
+def _bf16x6_bound(A, B, C0, alpha, beta, k):
+    """Componentwise bound for the bf16x6 product: x = hi + mid + lo + d with |d| <= 2^-24 |x|,
+    |mid| <= 2^-8 |x|, |lo| <= 2^-16 |x|; the kept products miss d and mid*lo, lo*mid, lo*lo, at
+    most 4 * 2^-24 |a||b| per product, and six binary32 accumulations per k step add
+    (6k + 2) * 2^-24."""
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    mag = abs(alpha) * (np.abs(A64) @ np.abs(B64)) + abs(beta) * np.abs(C0.astype(np.float64))
+    return (4 * 2.0 ** -24 + (6 * k + 2) * 2.0 ** -24) * mag + 1e-30, mag
+
+
+@pytest.mark.parametrize("panels,split", [(True, 2), (False, 2), (True, 3)])
 @pytest.mark.parametrize("shape,P,lower", [((200, 300, 150), 2, False), ((512, 256, 512), 4, True),
                                             ((384, 520, 384), 3, True)])
-def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower, panels, monkeypatch):
+def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower, panels, split, monkeypatch):
+    """split 2: bf16x3 within its componentwise bound; split 3: bf16x6 within its bound and within
+    1e-5 of |A||B| componentwise (binary32 accuracy)."""
     if not panels:  # the fallback kernel that splits while loading
         monkeypatch.setenv("HDARRAY_GEMM_NO_PANELS", "1")
     ni, nj, nk = shape
@@ -507,14 +519,20 @@ def test_gemm_bf16x3_parity(gpu_lib, shape, P, lower, panels, monkeypatch):
             prog.append(("trap_use", "trmm", "R", "A", p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1)))
     prog += [("write", "A", "RA"), ("write", "B", "RB"), ("write", "C", "R"),
              ("apply", kname, "R", ["A", "B", "C"], scal)]
-    lib, orc, *_ = run_program(prog, P, {"A": a, "B": b, "C": c}, gpu_lib, check_buffers=False)
+    setup = (lambda: H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X6)) if split == 3 else None
+    lib, orc, *_ = run_program(prog, P, {"A": a, "B": b, "C": c}, gpu_lib, check_buffers=False, setup=setup)
     device_buffers_match(lib, orc, ["A", "B"])  # the all-gathered B is bit-exact on every device
     got = np.zeros((ni, nj), np.float32)
     H.HDArrayRead(lib.arrays["C"], got, lib.parts["R"])
     ref = beta * c.astype(np.float64) + alpha * (np.tril(a.astype(np.float64)) if lower else a.astype(np.float64)) @ b.astype(np.float64)
-    bound = _bf16x3_bound(np.tril(a) if lower else a, b, c, alpha, beta, nk)
     err = np.abs(got.astype(np.float64) - ref)
-    assert (err <= 2 * bound).all(), float((err / bound).max())
+    if split == 2:
+        bound = _bf16x3_bound(np.tril(a) if lower else a, b, c, alpha, beta, nk)
+        assert (err <= 2 * bound).all(), float((err / bound).max())
+    else:
+        bound, mag = _bf16x6_bound(np.tril(a) if lower else a, b, c, alpha, beta, nk)
+        assert (err <= bound).all(), float((err / bound).max())
+        assert (err <= 1e-5 * mag).all(), float((err / mag).max())
     # the binary64 oracle's own result agrees with numpy to far better than the bound
     assert np.abs(orc.arrays["C"].G.astype(np.float64) - ref).max() <= 1e-5 * np.abs(ref).max()
 
@@ -827,6 +845,40 @@ def test_covariance_parity(gpu_lib, balanced, correlation, dtype, n, m, P):
     assert np.abs(orc.arrays["C"].G.astype(np.float64) - want).max() <= (1e-12 if dtype == "double" else 1e-4) * np.abs(want).max()
 
 
+@pytest.mark.parametrize("balanced", [False, True])
+def test_covariance_bf16x6(gpu_lib, balanced):
+    """The triangular product (transposed A, upper-triangle output, 128-column tiles) in the bf16x6
+    form: within its bound and within 1e-5 of |X^T||X| componentwise; messages as the oracle's."""
+    from cov_program import cov_prog
+    n, m, P = 300, 384, 4
+    prog, rows = cov_prog(n, m, P, dtype="float", balanced=balanced)
+    x = synthetic.to_storage(synthetic.normal(n * m, stream=111).reshape(n, m) + 0.5, "float")
+    lib, orc, *_ = run_program(prog, P, {"X": x}, gpu_lib, check_buffers=False,
+                               setup=lambda: H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X6))
+    Xc = read_all(lib, "Xc", (n, m), "float", "DX")
+    C = read_all(lib, "C", (m, m), "float", "PC")
+    assert np.array_equal(C, C.T)
+    alpha = 1.0 / (n - 1)
+    X64 = Xc.astype(np.float64)
+    err = np.abs(C.astype(np.float64) - alpha * X64.T @ X64)
+    bound, mag = _bf16x6_bound(Xc.T.copy(), Xc, np.zeros((m, m), np.float32), alpha, 0.0, n)
+    assert (err <= bound).all(), float((err / bound).max())
+    assert (err <= 1e-5 * mag).all(), float((err / mag).max())
+
+
+def test_gemm_split_setting(gpu_lib):
+    """HDArraySetGemmSplit accepts the two forms only, and not inside a batch."""
+    gpu_lib(2)
+    with pytest.raises(H.HDArrayError):
+        H.HDArraySetGemmSplit(4)
+    H.HDArrayBatchBegin()
+    with pytest.raises(H.HDArrayError):
+        H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X6)
+    H.HDArrayBatchEnd()
+    H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X6)
+    H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X3)
+
+
 # ---------------------------------------------------------------------------------------------
 # user kernels (HDArrayRegisterKernel) and a caller-supplied allocator (HDArraySetAllocator)
 # ---------------------------------------------------------------------------------------------
@@ -965,14 +1017,16 @@ def test_full_size_batch_512_instances(gpu_lib):
         assert np.array_equal(gotv, want), "instance %d" % i
 
 
-@pytest.mark.parametrize("dtype", ["double", "float"])
-def test_full_size_trmm_8192x4096(gpu_lib, dtype):
+@pytest.mark.parametrize("dtype,split", [("double", 0), ("float", 2), ("float", 3)])
+def test_full_size_trmm_8192x4096(gpu_lib, dtype, split):
     """tril(A) 8192^2 x B 8192x4096 on 8 row blocks with trapezoid use sections (binary64 on the
     DFMA pipe, binary32 on the tensor cores): sampled entries against the oracle's exact binary64
     entries (FP64 within 1e-12 relative to |A||B|, bf16x3 within its bound)."""
     n, m, P = 8192, 4096, 8
     a, b = synthetic.tri_gemm_inputs(n, m, stream=4, dtype=dtype)
     gpu_lib(P)
+    if split == 3:
+        H.HDArraySetGemmSplit(H.HDARRAY_GEMM_BF16X6)
     A = H.HDArrayCreate("A", dtype, None, n, n)
     B = H.HDArrayCreate("B", dtype, None, n, m)
     C = H.HDArrayCreate("C", dtype, None, n, m)
@@ -997,8 +1051,11 @@ def test_full_size_trmm_8192x4096(gpu_lib, dtype):
                                   ij.ctypes.data, want.ctypes.data)
     gotv = np.array([got[i, j] for i, j in ij], np.float64)
     mag = np.array([np.abs(A64[i, :i + 1]) @ np.abs(B64[:i + 1, j]) for i, j in ij])
+    k = np.array([i + 1 for i, _ in ij])
     if dtype == "double":
         assert (np.abs(gotv - want) <= 1e-12 * mag).all()
-    else:
-        k = np.array([i + 1 for i, _ in ij])
+    elif split == 2:
         assert (np.abs(gotv - want) <= 2 * (3 * 2.0 ** -16 + (k + 2) * 2.0 ** -24) * mag).all()
+    else:  # bf16x6: its bound, and binary32 accuracy (1e-5 of |A||B| componentwise)
+        assert (np.abs(gotv - want) <= (4 + 6 * k + 2) * 2.0 ** -24 * mag).all()
+        assert (np.abs(gotv - want) <= 1e-5 * mag).all()
