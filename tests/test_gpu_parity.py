@@ -146,6 +146,31 @@ def test_jacobi2d_degenerate(gpu_lib):
         H.HDArrayExit()
 
 
+def test_empty_work_region(gpu_lib):
+    """A call over a partition whose work region is empty moves nothing, launches nothing and
+    leaves the arrays as they were; zero-size arrays are refused."""
+    dims, P = (40, 56), 4
+    gpu_lib(P)
+    x = synthetic.jacobi_field(dims, stream=14, dtype="float")
+    B = H.HDArrayCreate("B", "float", None, *dims)
+    A = H.HDArrayCreate("A", "float", None, *dims)
+    D = H.HDArrayPartition(ROW, dims, (0, 0), dims, P)
+    E = H.HDArrayPartition(ROW, dims, (5, 1), (5, dims[1] - 1), P)  # no rows
+    H.HDArrayWrite(B, x, D)
+    H.HDArrayWrite(A, x, D)
+    c0 = H.HDArrayGetCounters()
+    H.HDArrayApplyKernel("jacobi2d", E, B, A)
+    c1 = H.HDArrayGetCounters()
+    assert c1["launches"] == c0["launches"]
+    assert H.HDArrayGetPlan(B) == []
+    got = np.zeros(dims, np.float32)
+    H.HDArrayRead(A, got, D)
+    assert np.array_equal(got, x)
+    for bad in ((0, 5), (5, 0)):
+        with pytest.raises(H.HDArrayError):
+            H.HDArrayCreate("Z", "float", None, *bad)
+
+
 # ---------------------------------------------------------------------------------------------
 # Reduce, residual
 # ---------------------------------------------------------------------------------------------
