@@ -368,8 +368,18 @@ def test_graph_replay(gpu_lib, dtype):
 # full size, in the benchmark's configuration: sampled outputs against the oracle
 # ---------------------------------------------------------------------------------------------
 
+# tile shapes: the library's defaults, and the shapes the autotuner picks for bench.py on a GB300
+TUNED_2D = {"float": {"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16", "HDARRAY_WARPS_PER_CTA": "4"},
+            "bf16": {"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_TILE_ROWS": "32", "HDARRAY_WARPS_PER_CTA": "8"}}
+
+
+@pytest.mark.parametrize("tuned", [False, True])
 @pytest.mark.parametrize("dtype", ["float", "bf16"])
-def test_full_size_8192_block16_graph(gpu_lib, dtype):
+def test_full_size_8192_block16_graph(gpu_lib, dtype, tuned, monkeypatch):
+    """The benchmark workload (8192^2, BLOCK 4 x 4, a 2-iteration graph replayed to 100
+    iterations) with the default tile shape and with the one bench.py runs after autotuning."""
+    for k, v in (TUNED_2D[dtype].items() if tuned else ()):
+        monkeypatch.setenv(k, v)
     n, P, T = 8192, 16, 100
     dims = (n, n)
     x = synthetic.jacobi_field(dims, stream=1, dtype=dtype)
@@ -459,7 +469,12 @@ def test_stencil3d_wide_rows(gpu_lib):
     assert np.array_equal(got, orc.arrays["A"].G)
 
 
-def test_full_size_stencil3d_512_37_boxes(gpu_lib):
+@pytest.mark.parametrize("tile_z", [None, "32"])
+def test_full_size_stencil3d_512_37_boxes(gpu_lib, tile_z, monkeypatch):
+    """512^3 on the 37 k-d boxes, 50 iterations in a graph, with the default tile depth and the
+    one bench.py's autotuner picks (32 planes)."""
+    if tile_z:
+        monkeypatch.setenv("HDARRAY_TILE_Z", tile_z)
     n, T = 512, 50
     boxes = synthetic.kd_boxes(n, 37, stream=3)
     x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
@@ -753,10 +768,13 @@ def test_conv2d_execution_choices(gpu_lib, monkeypatch, env):
         assert np.array_equal(read_all(lib, name, dims, "float"), orc.arrays[name].G)
 
 
-def test_conv2d_full_size_8192_block16(gpu_lib):
+@pytest.mark.parametrize("rows", [None, "16"])
+def test_conv2d_full_size_8192_block16(gpu_lib, rows, monkeypatch):
     """The convolution workload at full size (8192^2 binary32, BLOCK 4 x 4) in a graph; outputs
     sampled at partition corners and edges and at random, each recomputed by the oracle from its
-    3 x 3 neighbourhood."""
+    3 x 3 neighbourhood; default tile rows and the autotuned 16."""
+    if rows:
+        monkeypatch.setenv("HDARRAY_TILE_ROWS", rows)
     N, P = 8192, 16
     x = synthetic.jacobi_field((N, N), stream=98, dtype="float")
     w = synthetic.normal(9, stream=99)
