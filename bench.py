@@ -420,7 +420,7 @@ def oracle_sample(iters):
     return time.perf_counter() - t, (n - 2) * (n - 2) * iters
 
 
-def cpu_baseline(iters=4):
+def cpu_baseline(iters=8):
     sec, cells = oracle_sample(iters)
     return {"value": cells / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%dx%d FP32 grid, same 16-device BLOCK data/work partitions, %d iterations, "
