@@ -1574,7 +1574,7 @@ int compile_tuned(Plan &pl)
     } else {
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
-                for (int rows : {16, 32, 64})
+                for (int rows : {4, 8, 16, 32, 64})  // short tiles: more warps for small grids
                     for (int w : {4, 8})
                         cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
                                                    saved.band2});
