@@ -92,6 +92,7 @@ struct Ctx {
     bool tuning = false;  // compile_plan is being called by the tuner
     struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3, cta3, band2; };
     std::map<std::string, Shape> tuned;
+    bool tune_file_loaded = false;  // HDARRAY_TUNE_CACHE read into `tuned` (once per HDArrayInit)
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
     int last_error = 0;
@@ -1477,9 +1478,8 @@ const char *tune_file() { return getenv("HDARRAY_TUNE_CACHE"); }
 
 void load_tune_file()
 {
-    static bool loaded = false;
-    if (loaded || !tune_file()) return;
-    loaded = true;
+    if (g->tune_file_loaded || !tune_file()) return;
+    g->tune_file_loaded = true;
     FILE *f = fopen(tune_file(), "r");
     if (!f) return;
     char key[4096];

@@ -171,6 +171,26 @@ def test_empty_work_region(gpu_lib):
             H.HDArrayCreate("Z", "float", None, *bad)
 
 
+def test_tune_cache_file(gpu_lib, monkeypatch, tmp_path):
+    """Autotuning with HDARRAY_TUNE_CACHE: the first run times the candidates and appends the
+    chosen shape (key and nine integers); after a new HDArrayInit the shape comes from the file,
+    nothing is appended, and the results stay bit-exact against the oracle."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("HDARRAY_AUTOTUNE", "1")
+    monkeypatch.setenv("HDARRAY_TUNE_CACHE", str(cache))
+    dims, P = (300, 260), 4
+    x = synthetic.jacobi_field(dims, stream=15, dtype="float")
+    prog, last = jacobi_prog(dims, P, 6, BLOCK, "float", True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+    lines = cache.read_text().splitlines()
+    assert lines and all(len(ln.split()) == 10 for ln in lines)
+    H.HDArrayExit()
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, "float"), orc.arrays[last].G)
+    assert cache.read_text().splitlines() == lines
+
+
 # ---------------------------------------------------------------------------------------------
 # Reduce, residual
 # ---------------------------------------------------------------------------------------------
