@@ -18,8 +18,9 @@
  *   - Calls of the paper's prototypes that return void record an error code readable with
  *     HDArrayGetLastError(); every other call returns it: 0 = HDARRAY_OK, negative = error.
  *     Nothing aborts the process.
- *   - The library runs on the current CUDA device, on one stream (HDArraySetStream).  Kernel
- *     launches are asynchronous; HDArrayRead, HDArrayReduce and HDArraySync wait for the stream.
+ *   - The library runs on the CUDA device that is current at HDArrayInit, on one stream
+ *     (HDArraySetStream); keep that device current while calling it.  Kernel launches are
+ *     asynchronous; HDArrayRead, HDArrayReduce and HDArraySync wait for the stream.
  *   - Not thread safe: one host thread drives the library.
  */
 #ifndef HDARRAY_H
