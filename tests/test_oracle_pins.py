@@ -458,6 +458,32 @@ def test_reduce_closed_forms():
     assert s == vals[1:-1, 1:-1].sum()  # small integers: exact in any order
 
 
+@pytest.mark.parametrize("dtype", ["double", "float"])
+def test_sqdiff_residual_integer_field(dtype):
+    """The residual kernel (Sec. 5's convergence test, (X - Y)^2 into a binary64 array) on integer
+    fields X[i][j] = 3i, Y[i][j] = j over a work region away from the border: every value is the
+    exact integer (3i - j)^2 inside the region and 0 outside it.  (X - Y)^2 does not see the
+    operand order, so the fields pin the indexing: 3i - j changes under a transposed or shifted
+    index, and the region's edges under a wrong clip."""
+    n0, n1 = 23, 31
+    i, j = np.meshgrid(np.arange(n0), np.arange(n1), indexing="ij")
+    x, y = (3 * i).astype(np.float64), j.astype(np.float64)
+    o = Oracle(3)
+    full = o.partition(ROW, (n0, n1), (0, 0), (n0, n1))
+    work = o.partition(ROW, (n0, n1), (2, 3), (n0 - 1, n1 - 4))
+    X = o.create("X", dtype, (n0, n1))
+    Y = o.create("Y", dtype, (n0, n1))
+    R = o.create("R", "double", (n0, n1))
+    o.write(X, x.astype(np.float64 if dtype == "double" else np.float32), full)
+    o.write(Y, y.astype(np.float64 if dtype == "double" else np.float32), full)
+    o.apply("sqdiff", work, [X, Y, R], compute=True)
+    want = np.zeros((n0, n1))
+    want[2:n0 - 1, 3:n1 - 4] = ((3 * i - j) ** 2)[2:n0 - 1, 3:n1 - 4]
+    assert np.array_equal(R.G.reshape(n0, n1), want)
+    s, _ = o.reduce(R, SUM, work)
+    assert s == float(((3 * i - j) ** 2)[2:n0 - 1, 3:n1 - 4].sum())
+
+
 def test_bf16_rounding_matches_torch():
     torch = pytest.importorskip("torch")
     x = np.concatenate([
