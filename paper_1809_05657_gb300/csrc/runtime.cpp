@@ -85,6 +85,7 @@ struct Ctx {
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
+    int snake = 1;          // alternate the tile order of X -> Y and Y -> X launches (L2 reuse)
     int gemm_parts = 2;     // binary32 GEMM on tensor cores: 2 bf16 parts (bf16x3) or 3 (bf16x6)
     int row_align = 16;     // bytes: device buffer rows start and end on this boundary (16 .. 1024)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
@@ -981,6 +982,9 @@ int compile_plan(Plan &pl)
             for (StenTile2D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
             if (sx) add_moves(*sx);
         }
+        // one launch for every device: the tiles of the calls X -> Y and Y -> X run in opposite
+        // orders, so an iteration starts on the rows the previous one wrote last, still in L2
+        if (!plain && g->snake && X->uid > Y->uid) std::reverse(h.tiles.begin(), h.tiles.end());
         blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart2D)});
         blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile2D)});
@@ -1055,6 +1059,7 @@ int compile_plan(Plan &pl)
             for (StenTile3D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
             if (sx) add_moves(*sx);
         }
+        if (!plain && g->snake && X->uid > Y->uid) std::reverse(h.tiles.begin(), h.tiles.end());
         blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart3D)});
         blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile3D)});
@@ -1850,7 +1855,12 @@ int flush_batch()
         std::vector<CopyTask> copies;
         std::map<std::tuple<int, int, int>, Sten2DHost> sten;  // (dtype, variant, warps)
         std::vector<LaunchRec> rest;
-        for (auto &p : plans) {
+        // the calls X -> Y and Y -> X of a batch run their instances in opposite orders (each
+        // plan's own tiles are reversed already), so an iteration starts where the last one ended
+        std::vector<std::shared_ptr<Plan>> order(plans);
+        if (g->snake && !order.empty() && order[0]->args.size() >= 2 && order[0]->args[0]->uid > order[0]->args[1]->uid)
+            std::reverse(order.begin(), order.end());
+        for (auto &p : order) {
             if (p->k->kind == K_JACOBI2D && g->mode == HDARRAY_MODE_FUSED) {
                 copies.insert(copies.end(), p->copy_host.begin(), p->copy_host.end());
                 Sten2DHost &h = sten[std::make_tuple(p->s2.dtype, p->s2.variant, p->s2.warps)];
@@ -2308,6 +2318,8 @@ int init_impl(int ndev, unsigned flags)
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
         if (vv && atoi(vv) >= 0 && atoi(vv) <= 4) g->variant = atoi(vv);
+        const char *sn = getenv("HDARRAY_SNAKE");
+        if (sn && (atoi(sn) == 0 || atoi(sn) == 1)) g->snake = atoi(sn);
         const char *ra = getenv("HDARRAY_ROW_ALIGN");
         if (ra && atoi(ra) >= 16 && atoi(ra) <= 1024 && (atoi(ra) & (atoi(ra) - 1)) == 0) g->row_align = atoi(ra);
         const char *b2 = getenv("HDARRAY_BAND2");
