@@ -974,7 +974,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("8192x8192", "%dx%d" % (N, N)), "grid": [N, N], "logical_devices": P,
                        "iterations_per_step": ITERS, "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "l2": "inputs 2 x %d MB %s 129 MB L2 (no flush)" % (N * N * 4 // 2 ** 20, ">" if N * N * 4 > 129e6 else "<=")},
+                       "l2": "inputs 2 x %d MiB %s 129 MB L2 (no flush)" % (N * N * 4 // 2 ** 20, ">" if N * N * 4 > 129e6 else "<=")},
             "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES_2D[variant] + ", fused exchange + stencil",
                          "achieved": r["achieved"], "peak": r["hbm"], "unit": "GB/s",
                          "frac": r["achieved"] / r["hbm"], "peak_source": r["src"],
