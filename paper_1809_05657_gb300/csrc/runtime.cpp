@@ -1577,9 +1577,13 @@ int compile_tuned(Plan &pl)
                     cands.push_back(Ctx::Shape{saved.variant, rows, saved.warps, saved.tile_z, fu, saved.variant3,
                                                saved.band3, saved.cta3, band});
     } else {
+        int64_t cells = 0;  // short tiles (more warps) are candidates for small grids only
+        for (int p = 0; p < g->parts[pl.part].nparts; p++) cells += g->parts[pl.part].box[p].volume();
+        const std::vector<int> row_cands = cells < (1 << 22) ? std::vector<int>{4, 8, 16, 32, 64}
+                                                              : std::vector<int>{16, 32, 64};
         for (int fu : {1, 0}) {
             for (int v : {0, 1})
-                for (int rows : {4, 8, 16, 32, 64})  // short tiles: more warps for small grids
+                for (int rows : row_cands)
                     for (int w : {4, 8})
                         cands.push_back(Ctx::Shape{v, rows, w, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
                                                    saved.band2});
