@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
 #pragma unroll
     for (int k = 0; k < 9; k++) w[k] = OP == OP_CONV ? (A)wts[k] : A(0);
 
-    receive_segments_cta<E>(segs, t.seg0, t.nseg);
+    receive_segments_cta<E, DT != DT_BF16>(segs, t.seg0, t.nseg);
 
     const int nch = t.nch, rw = nch + 2, G = t.ns, SL = t.sl;
     const int SS = G * rw;                        // 16-byte slots used per stage

@@ -110,6 +110,111 @@ __device__ __forceinline__ void receive_flat(const Seg *__restrict__ segs, int s
         if (u < nb) *dst[u] = v[u];
 }
 
+// A receive segment whose rows are contiguous runs at the same 16-byte phase in the sender's and
+// the receiver's buffer (row faces in 2-D, y and z faces in 3-D): h0 elements up to the first
+// 16-byte boundary, then nc whole 16-byte chunks, then the tail.  nc = 0: copied element-wise.
+template <typename E>
+__device__ __forceinline__ void run_split(const Seg &g, int &h0, int &nc)
+{
+    constexpr int VEC = 16 / (int)sizeof(E);
+    h0 = 0;
+    nc = 0;
+    const uintptr_t sa = reinterpret_cast<uintptr_t>(g.src), da = reinterpret_cast<uintptr_t>(g.dst);
+    if (g.ss != 1 || g.ds != 1 || g.n < 2 * VEC || ((sa ^ da) & 15) != 0) return;
+    if (g.m > 1 && ((((int64_t)sizeof(E) * g.sso) & 15) != 0 || (((int64_t)sizeof(E) * g.dso) & 15) != 0)) return;
+    h0 = (int)(((16 - (sa & 15)) & 15) / sizeof(E));
+    nc = (g.n - h0) / VEC;
+}
+
+// The same copy for a whole CTA, with the contiguous runs moved in 16-byte chunks: this thread's
+// share of items first, first + stride, ... of every segment, first the chunks of the contiguous
+// runs, then the remaining elements, each pass with four copies in flight per thread.  (The warp
+// kernels keep the element-wise form: the chunk pass costs them registers in their march.)
+template <typename E>
+__device__ __forceinline__ void receive_flat_vec(const Seg *__restrict__ segs, int seg0, int nseg, int first, int stride)
+{
+    constexpr int VEC = 16 / (int)sizeof(E);
+    {  // 16-byte chunks
+        uint4 v[4];
+        uint4 *dst[4];
+        int nb = 0;
+        for (int s = 0; s < nseg; s++) {
+            const Seg g = segs[seg0 + s];
+            int h0, nc;
+            run_split<E>(g, h0, nc);
+            if (nc == 0) continue;
+            const int total = nc * g.m;
+            const E *src = reinterpret_cast<const E *>(g.src) + h0;
+            E *d0 = reinterpret_cast<E *>(g.dst) + h0;
+            int o = first / nc, c = first - (first / nc) * nc;
+            const int dof = stride / nc, dc = stride - dof * nc;
+            for (int i = first; i < total; i += stride) {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u == nb) {
+                        v[u] = *reinterpret_cast<const uint4 *>(src + o * g.sso + c * VEC);
+                        dst[u] = reinterpret_cast<uint4 *>(d0 + o * g.dso + c * VEC);
+                    }
+                if (++nb == 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) *dst[u] = v[u];
+                    nb = 0;
+                }
+                o += dof;
+                c += dc;
+                if (c >= nc) {
+                    c -= nc;
+                    o += 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (u < nb) *dst[u] = v[u];
+    }
+    {  // elements: whole segments that are not contiguous runs, heads and tails of those that are
+        E v[4];
+        E *dst[4];
+        int nb = 0;
+        for (int s = 0; s < nseg; s++) {
+            const Seg g = segs[seg0 + s];
+            int h0, nc;
+            run_split<E>(g, h0, nc);
+            const int per = g.n - nc * VEC;  // elements per row left to this pass
+            if (per == 0) continue;
+            const int skip = nc * VEC;       // element q of a row's share is element q (< h0) or q + skip
+            const int total = per * g.m;
+            const E *src = reinterpret_cast<const E *>(g.src);
+            E *d0 = reinterpret_cast<E *>(g.dst);
+            int o = first / per, q = first - (first / per) * per;
+            const int dof = stride / per, dq = stride - dof * per;
+            for (int i = first; i < total; i += stride) {
+                const int k = q < h0 ? q : q + skip;
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u == nb) {
+                        v[u] = src[o * g.sso + k * g.ss];
+                        dst[u] = d0 + o * g.dso + k * g.ds;
+                    }
+                if (++nb == 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) *dst[u] = v[u];
+                    nb = 0;
+                }
+                o += dof;
+                q += dq;
+                if (q >= per) {
+                    q -= per;
+                    o += 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (u < nb) *dst[u] = v[u];
+    }
+}
+
 // The warp's receive phase, then __syncwarp orders the copies before the warp's loads: the
 // barrier orders memory among the threads that take part in it, and cp.async reads are memory
 // operations of the issuing thread, so they see the other lanes' stores.
@@ -227,11 +332,16 @@ __device__ __forceinline__ typename Elem<DT>::A edge_read(const uint4 *slot, boo
 
 
 // Receive segments copied by a whole CTA, then a barrier orders them before the CTA's loads (as
-// for the warp form above, at CTA scope).
-template <typename E>
+// for the warp form above, at CTA scope).  RUNS: contiguous runs in 16-byte chunks (measured
+// faster for the 3-D and binary32/binary64 2-D CTA kernels; the bfloat16 2-D kernel keeps the
+// element form, whose registers fit its march better).
+template <typename E, bool RUNS = true>
 __device__ __forceinline__ void receive_segments_cta(const Seg *__restrict__ segs, int seg0, int nseg)
 {
-    if (nseg > 0) receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
+    if (nseg > 0) {
+        if (RUNS) receive_flat_vec<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
+        else receive_flat<E>(segs, seg0, nseg, threadIdx.x, blockDim.x);
+    }
     __syncthreads();
 }
 
