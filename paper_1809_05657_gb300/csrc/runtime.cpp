@@ -1603,7 +1603,7 @@ int compile_tuned(Plan &pl)
     for (const Ctx::Shape &c : cands) {
         apply_shape(c, threed);
         if (compile_plan(pl) != HDARRAY_OK) continue;
-        const float ms = time_plan(pl, 3);
+        const float ms = time_plan(pl, 7);
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
