@@ -992,6 +992,12 @@ int compile_plan(Plan &pl)
         double wts[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < 9 && conv; i++) wts[i] = i < (int)pl.scal.size() ? pl.scal[i] : 0.0;
         blobs.push_back({wts, conv ? sizeof(wts) : 0});
+        // a convolution repeated on the same input (no dependency across iterations): every other
+        // call runs the tiles in the reverse order, starting on the rows the previous call read last
+        std::vector<StenTile2D> rtiles;
+        const bool alternate = conv && !plain && g->snake && !h.tiles.empty();
+        if (alternate) rtiles.assign(h.tiles.rbegin(), h.tiles.rend());
+        blobs.push_back({rtiles.data(), rtiles.size() * sizeof(StenTile2D)});
         std::vector<const char *> addr;
         int rc = upload(blobs, pl.tables, addr);
         if (rc) return rc;
@@ -1018,6 +1024,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
+                if (alternate) L.p1_alt = addr[5];
                 L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
@@ -1424,6 +1431,7 @@ int issue_recorded(const LaunchRec &L)
 int run_plan(const std::shared_ptr<Plan> &pl)
 {
     if (g->host_only) return HDARRAY_OK;
+    bool alternated = false;
     for (const LaunchRec &L : pl->launches) {
         if (L.kind == L_SPLIT) {  // panels of an operand whose content has not changed are reused
             const int which = (int)L.n3;
@@ -1431,9 +1439,19 @@ int run_plan(const std::shared_ptr<Plan> &pl)
             if (!g->recording && pl->split_version[which] == v) continue;
             pl->split_version[which] = v;
         }
-        int rc = issue_recorded(L);
+        int rc;
+        if (L.p1_alt) {  // every other call of the plan takes its reversed tile table
+            LaunchRec M = L;
+            if (pl->alt) M.p1 = L.p1_alt;
+            M.p1_alt = nullptr;
+            rc = issue_recorded(M);
+            alternated = true;
+        } else {
+            rc = issue_recorded(L);
+        }
         if (rc) return rc;
     }
+    if (alternated) pl->alt = !pl->alt;
     if (g->recording) g->rec_refs.push_back(pl);
     return HDARRAY_OK;
 }

@@ -75,6 +75,7 @@ struct LaunchRec {
     int kind = 0;
     int dtype = 0;
     const void *p0 = nullptr, *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+    const void *p1_alt = nullptr;  // a second tile table (the same tiles reversed), taken by every other call
     int64_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     double f0 = 0, f1 = 0;
 };
@@ -140,6 +141,7 @@ struct Plan {
     std::shared_ptr<DevMem> extra_tables;  // descriptor tables of the panel launches
     uint64_t split_version[2] = {~0ull, ~0ull};  // content versions of A and B the panels hold
     std::vector<HDArrayWork_t> user_work;         // a user kernel's per-device work
+    bool alt = false;                             // next call takes the launches' p1_alt tables
 };
 
 // Device memory: cudaMalloc / cudaFree, or the allocator set with HDArraySetAllocator (each
