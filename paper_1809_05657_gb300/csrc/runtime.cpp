@@ -992,10 +992,12 @@ int compile_plan(Plan &pl)
         double wts[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int i = 0; i < 9 && conv; i++) wts[i] = i < (int)pl.scal.size() ? pl.scal[i] : 0.0;
         blobs.push_back({wts, conv ? sizeof(wts) : 0});
-        // a convolution repeated on the same input (no dependency across iterations): every other
-        // call runs the tiles in the reverse order, starting on the rows the previous call read last
+        // the same tiles in the reverse order: a convolution repeated on the same input (no
+        // dependency across iterations) runs every other call with them, starting on the rows the
+        // previous call read last, and the autotuner times candidate shapes that way (a ping-pong's
+        // calls X -> Y and Y -> X get opposite orders from the rule above)
         std::vector<StenTile2D> rtiles;
-        const bool alternate = conv && !plain && g->snake && !h.tiles.empty();
+        const bool alternate = !plain && g->snake && !h.tiles.empty();
         if (alternate) rtiles.assign(h.tiles.rbegin(), h.tiles.rend());
         blobs.push_back({rtiles.data(), rtiles.size() * sizeof(StenTile2D)});
         std::vector<const char *> addr;
@@ -1024,7 +1026,10 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
-                if (alternate) L.p1_alt = addr[5];
+                if (alternate) {
+                    L.p1_alt = addr[5];
+                    L.alt_calls = conv;
+                }
                 L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
@@ -1440,7 +1445,7 @@ int run_plan(const std::shared_ptr<Plan> &pl)
             pl->split_version[which] = v;
         }
         int rc;
-        if (L.p1_alt) {  // every other call of the plan takes its reversed tile table
+        if (L.p1_alt && L.alt_calls) {  // every other call of the plan takes its reversed tile table
             LaunchRec M = L;
             if (pl->alt) M.p1 = L.p1_alt;
             M.p1_alt = nullptr;
@@ -1533,13 +1538,16 @@ float time_plan(const Plan &pl, int reps)
     float best = 1e30f;
     for (int r = 0; r < reps + 1; r++) {
         cudaEventRecord(a, g->stream);
-        for (const LaunchRec &L : pl.launches)
+        for (const LaunchRec &L0 : pl.launches) {
+            LaunchRec L = L0;  // successive runs alternate the tile order, as iterations do
+            if (L.p1_alt && (r & 1)) L.p1 = L.p1_alt;
             if (issue(L, g->stream) != cudaSuccess) {
                 cudaGetLastError();
                 best = 1e30f;
                 r = reps + 1;
                 break;
             }
+        }
         cudaEventRecord(b, g->stream);
         cudaEventSynchronize(b);
         float ms = 0.0f;
