@@ -1076,6 +1076,10 @@ int compile_plan(Plan &pl)
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart3D)});
         blobs.push_back({h.tiles.data(), h.tiles.size() * sizeof(StenTile3D)});
         blobs.push_back({h.segs.data(), h.segs.size() * sizeof(Seg)});
+        std::vector<StenTile3D> rtiles;  // the same tiles reversed: the autotuner's alternating runs
+        const bool alternate = !plain && g->snake && !h.tiles.empty();
+        if (alternate) rtiles.assign(h.tiles.rbegin(), h.tiles.rend());
+        blobs.push_back({rtiles.data(), rtiles.size() * sizeof(StenTile3D)});
         std::vector<const char *> addr;
         int rc = upload(blobs, pl.tables, addr);
         if (rc) return rc;
@@ -1101,6 +1105,7 @@ int compile_plan(Plan &pl)
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
+                if (alternate) L.p1_alt = addr[4];
                 L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
