@@ -75,9 +75,9 @@ struct Ctx {
     double *host_result = nullptr;
     int red_blocks = 0;
     // tunables
-    int tile_rows = 64;     // 2-D tile height (rows per warp)
+    int tile_rows = 32;     // 2-D tile height (rows per warp)
     int warps_per_cta = 8;  // 2-D warps per CTA
-    int variant = 1;        // 2-D kernel variant (0 registers, 1 cp.async ring)
+    int variant = 0;        // 2-D kernel variant (0 registers, 1 cp.async ring, 2 flat, 3 packed streams)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
     int band2 = 32;         // 2-D packed-stream variant: most 16-byte chunks per band
