@@ -36,8 +36,28 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_ALL INT32_MIN /* the '*' offset: every element of that dimension (Sec. 3) */
+
+/* Threads of the stencil value loops (orc_jacobi2d, orc_stencil3d).  Every output element is a
+ * function of the input array alone, so the loops give the same bits with any number of threads;
+ * the default is one.  Without OpenMP at build time the loops always run on one thread. */
+static int orc_nthreads = 1;
+
+/* Set the value loops' thread count (clamped to >= 1); returns the count the loops will use. */
+int orc_set_threads(int n)
+{
+    orc_nthreads = n < 1 ? 1 : n;
+#ifdef _OPENMP
+    return orc_nthreads;
+#else
+    orc_nthreads = 1;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------------------------ */
 /* Partitions: HDArrayPartition splits a work region evenly over the devices (Sec. 3.1).        */
@@ -395,10 +415,14 @@ static double load_as_double(int prec, const void *X, int64_t i)
  * Returns -1 if a work element lacks a neighbour inside the array. */
 int orc_jacobi2d(int prec, int64_t n0, int64_t n1, const void *B, void *A, const uint8_t *work)
 {
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad) num_threads(orc_nthreads)
     for (int64_t i = 0; i < n0; i++)
         for (int64_t j = 0; j < n1; j++)
-            if (work[i * n1 + j] && (i == 0 || j == 0 || i == n0 - 1 || j == n1 - 1)) return -1;
-    for (int64_t i = 1; i + 1 < n0; i++) {
+            if (work[i * n1 + j] && (i == 0 || j == 0 || i == n0 - 1 || j == n1 - 1)) bad = 1;
+    if (bad) return -1;
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads)
+    for (int64_t i = 1; i < n0 - 1; i++) {
         for (int64_t j = 1; j + 1 < n1; j++) {
             int64_t c = i * n1 + j;
             if (!work[c]) continue;
@@ -472,13 +496,17 @@ int orc_stencil3d(int prec, int64_t n0, int64_t n1, int64_t n2, const void *B, v
                   const uint8_t *work)
 {
     int64_t sz = n2, sy = n1 * n2;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad) num_threads(orc_nthreads)
     for (int64_t z = 0; z < n0; z++)
         for (int64_t y = 0; y < n1; y++)
             for (int64_t x = 0; x < n2; x++)
                 if (work[z * sy + y * sz + x] &&
                     (z == 0 || y == 0 || x == 0 || z == n0 - 1 || y == n1 - 1 || x == n2 - 1))
-                    return -1;
-    for (int64_t z = 1; z + 1 < n0; z++) {
+                    bad = 1;
+    if (bad) return -1;
+#pragma omp parallel for schedule(static) num_threads(orc_nthreads)
+    for (int64_t z = 1; z < n0 - 1; z++) {
         for (int64_t y = 1; y + 1 < n1; y++) {
             for (int64_t x = 1; x + 1 < n2; x++) {
                 int64_t c = z * sy + y * sz + x;

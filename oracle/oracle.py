@@ -72,6 +72,7 @@ def lib():
             "orc_gemm_entries": (None, [i64, i64, ctypes.c_double, ctypes.c_double, P, P, P,
                                         i64, P, P]),
             "orc_reduce": (i32, [i32, i64, P, P, i32, P]),
+            "orc_set_threads": (i32, [i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -79,6 +80,12 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the stencil value loops (same results with any count); returns the count used
+    (1 when the oracle was built without OpenMP)."""
+    return lib().orc_set_threads(int(n))
 
 
 def _p(a):

@@ -299,6 +299,55 @@ def test_stencil3d_eigenmode_decay(shape, modes):
     np.testing.assert_allclose(B.G, lam ** 3 * u0, rtol=0, atol=1e-14)
 
 
+# The printed Jacobi step (Sec. 5) sums the four neighbours left to right: ((W + E) + N) + S with
+# W = B[i][j-1], E = B[i][j+1], N = B[i-1][j], S = B[i+1][j].  With u the unit roundoff (half an
+# ulp of 1), 1 + u is a tie and rounds to 1 (even), so each neighbourhood below has a result that
+# follows from that order by hand; every other order of the four terms (up to swapping the first
+# two, which commute) changes the bits of at least one of the three results.
+#   (W, E, N, S) = (1, u, u, u):  ((1 + u) + u) + u = 1                  -> 1/4
+#   (W, E, N, S) = (1, u, u, -1): ((1 + u) + u) - 1 = 0                  -> 0
+#   (W, E, N, S) = (1, u, -1, u): ((1 + u) - 1) + u = u                  -> u/4
+def _one_cell(dtype, dims, nbrs):
+    """Run one stencil step on a 3 x 3 (x 3) array whose centre is the only work element; its
+    neighbours get the values nbrs (in the kernel's operand order); returns the centre's result."""
+    kname = "jacobi2d" if len(dims) == 2 else "stencil3d"
+    x = np.zeros(dims, np.float64)
+    c = (1,) * len(dims)
+    steps = [(0, -1), (0, 1), (-1, 0), (1, 0)] if len(dims) == 2 else \
+        [(0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)]
+    for (d, v) in zip(steps, nbrs):
+        x[tuple(ci + di for ci, di in zip(c, d))] = v
+    o = Oracle(1)
+    B = o.create("B", dtype, dims)
+    A = o.create("A", dtype, dims)
+    whole = o.partition(ROW, dims, (0,) * len(dims), dims)
+    work = o.partition(ROW, dims, (1,) * len(dims), (2,) * len(dims))
+    o.write(B, synthetic.to_storage(x, dtype), whole)
+    o.apply(kname, work, [B, A])
+    return A.values64()[c]
+
+
+@pytest.mark.parametrize("dtype,u", [("double", 2.0 ** -53), ("float", 2.0 ** -24), ("bf16", 2.0 ** -24)])
+def test_jacobi_summation_order_as_printed(dtype, u):
+    # bfloat16 storage computes in binary32, and u = 2^-24 and the results are bfloat16 numbers
+    assert _one_cell(dtype, (3, 3), (1.0, u, u, u)) == 0.25
+    assert _one_cell(dtype, (3, 3), (1.0, u, u, -1.0)) == 0.0
+    assert _one_cell(dtype, (3, 3), (1.0, u, -1.0, u)) == u / 4
+
+
+# The 3-D step sums the six face neighbours in the order x-, x+, y-, y+, z-, z+ and divides once by 6
+# (correctly rounded).  With u as above:
+#   (u, 1, -1, u, u, 1):    (u + 1) = 1, 1 - 1 = 0, 0 + u = u, u + u = 2u, 2u + 1 = 1 + 2u (exact)
+#   (1, u, 0.5, u, -1, -1): 1 + u = 1, 1.5, 1.5 + u = 1.5 (a tie, even), 0.5, -0.5
+# and every other left-to-right order of the six terms (up to swapping the first two) changes at
+# least one of the two sums.
+@pytest.mark.parametrize("ft,u", [(np.float64, 2.0 ** -53), (np.float32, 2.0 ** -24)])
+def test_stencil3d_summation_order_as_printed(ft, u):
+    dtype = "double" if ft is np.float64 else "float"
+    assert _one_cell(dtype, (3, 3, 3), (u, 1.0, -1.0, u, u, 1.0)) == float(ft(1.0 + 2 * u) / ft(6.0))
+    assert _one_cell(dtype, (3, 3, 3), (1.0, u, 0.5, u, -1.0, -1.0)) == float(ft(-0.5) / ft(6.0))
+
+
 def _conv_program(x, w, P=3, ptype=ROW, dtype="double"):
     o = Oracle(P)
     dims = x.shape
