@@ -297,7 +297,9 @@ int HDArrayReadDeviceBuffer(HDArray_t *hA, int dev, const int64_t *lo, const int
  *   op       HDARRAY_SUM / PROD / MAX / MIN, folded in double, deterministic;
  *   result   device pointer to one double that receives the value (caller-owned);
  *   stream   cudaStream_t to run on (NULL: the default stream); the call is asynchronous.
- * At most 2^31 elements per call (HDARRAY_ERR_RANGE beyond, nothing launched).  The first call on
+ * The box is spread over up to 1024 CTAs whatever its shape (a 1-D box as well as many short rows).
+ * At most 2^31 elements per call (HDARRAY_ERR_RANGE beyond, nothing launched): the limit bounds
+ * one call's run time, not the scratch, whose size is fixed; reduce larger boxes in pieces.  The first call on
  * each device looks up the static array's address (with that device current); make it before any
  * stream capture on that device.  Every call shares the static scratch, which keeps the last call's
  * contents (the counter is cleared at the start of each call): calls that overlap on the GPU race

@@ -23,9 +23,14 @@
 
 namespace {
 
-// At most this many CTAs, one partial each; at most 2^31 elements per call.
+// The scratch holds one partial per CTA, so a call runs at most NOALLOC_MAX_PARTIALS CTAs.  A call
+// reduces at most NOALLOC_MAX_ELEMS elements: the limit keeps one call's run time bounded (16 GiB
+// of binary64 at most, a few milliseconds at HBM rate), so work queued behind it on the stream is
+// not held up for long; larger boxes are reduced in pieces by the caller.  The scratch's size does
+// not depend on the element count.
 constexpr int NOALLOC_MAX_PARTIALS = 1024;
 constexpr int64_t NOALLOC_MAX_ELEMS = (int64_t)1 << 31;
+constexpr int64_t NOALLOC_SEG = 8192;  // elements of one work item (a row, or a piece of a long row)
 constexpr int NOALLOC_COUNTER_OFFSET = NOALLOC_MAX_PARTIALS * 8;
 
 // 8 KiB of partials, then the counter (zeroed before every call).
@@ -57,26 +62,40 @@ __device__ __forceinline__ double fold(double a, double b)
     return b < a ? b : a;
 }
 
-// Rows of the box are split into gridDim.x contiguous ranges, one per CTA; each CTA folds its range
-// (a warp per row, lanes striding the row), then a fixed shuffle / shared-memory tree gives its
-// partial; the last CTA to finish folds the partials in index order.  Deterministic.
+// The box is cut into work items: each row of the box (a run of n_inner contiguous elements) is
+// split into n_seg segments of at most NOALLOC_SEG elements, and the items (row, segment) are
+// numbered row-major.  CTA b folds the contiguous item range [b*per, (b+1)*per): its warps take the
+// items in turn and the lanes of a warp stride the segment, four independent loads in flight per
+// lane.  A fixed shuffle / shared-memory tree gives the CTA's partial, and the last CTA to finish
+// folds the partials in index order.  Item ranges, the fold order in each lane and the trees all
+// depend on the box's shape only, so the result is deterministic.  A 1-D box or a box of a few
+// long rows is spread over all CTAs like any other.
 template <int DT, int OP>
 __global__ void __launch_bounds__(256) k_reduce_box(const void *__restrict__ x, int64_t n_mid, int64_t n_inner,
-                                                    int64_t s_outer, int64_t s_mid, int64_t rows,
-                                                    double ident, double *partials, unsigned *counter,
-                                                    double *result)
+                                                    int64_t s_outer, int64_t s_mid, int64_t n_seg,
+                                                    int64_t items, double ident, double *partials,
+                                                    unsigned *counter, double *result)
 {
     __shared__ double wsum[8];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = (int64_t)blockIdx.x * per;
-    const int64_t r1 = r0 + per < rows ? r0 + per : rows;
+    const int64_t per = (items + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per;
+    const int64_t i1 = i0 + per < items ? i0 + per : items;
     double acc = ident;
-    for (int64_t r = r0 + warp; r < r1; r += nw) {
+    for (int64_t it = i0 + warp; it < i1; it += nw) {
+        const int64_t r = it / n_seg, sg = it - r * n_seg;
         const int64_t o = r / n_mid, m = r - o * n_mid;
+        const int64_t c0 = sg * NOALLOC_SEG;
+        const int64_t c1 = c0 + NOALLOC_SEG < n_inner ? c0 + NOALLOC_SEG : n_inner;
         const int64_t base = o * s_outer + m * s_mid;
-        for (int64_t c = lane; c < n_inner; c += 32) acc = fold<OP>(acc, ld<DT>(x, base + c));
+        int64_t c = c0 + lane;
+        for (; c + 96 < c1; c += 128) {
+            const double v0 = ld<DT>(x, base + c), v1 = ld<DT>(x, base + c + 32);
+            const double v2 = ld<DT>(x, base + c + 64), v3 = ld<DT>(x, base + c + 96);
+            acc = fold<OP>(fold<OP>(fold<OP>(fold<OP>(acc, v0), v1), v2), v3);
+        }
+        for (; c < c1; c += 32) acc = fold<OP>(acc, ld<DT>(x, base + c));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc = fold<OP>(acc, __shfl_xor_sync(0xffffffffu, acc, off));
@@ -102,15 +121,15 @@ __global__ void __launch_bounds__(256) k_reduce_box(const void *__restrict__ x, 
 
 template <int DT>
 void launch_box(int op, int nblocks, cudaStream_t s, const void *x, int64_t n_mid, int64_t n_inner,
-                int64_t s_outer, int64_t s_mid, int64_t rows, double *partials, unsigned *counter,
-                double *result)
+                int64_t s_outer, int64_t s_mid, int64_t n_seg, int64_t items, double *partials,
+                unsigned *counter, double *result)
 {
     const double inf = __builtin_inf();
     switch (op) {
-    case 0: k_reduce_box<DT, 0><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, rows, 0.0, partials, counter, result); break;
-    case 1: k_reduce_box<DT, 1><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, rows, 1.0, partials, counter, result); break;
-    case 2: k_reduce_box<DT, 2><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, rows, -inf, partials, counter, result); break;
-    default: k_reduce_box<DT, 3><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, rows, inf, partials, counter, result); break;
+    case 0: k_reduce_box<DT, 0><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, n_seg, items, 0.0, partials, counter, result); break;
+    case 1: k_reduce_box<DT, 1><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, n_seg, items, 1.0, partials, counter, result); break;
+    case 2: k_reduce_box<DT, 2><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, n_seg, items, -inf, partials, counter, result); break;
+    default: k_reduce_box<DT, 3><<<nblocks, 256, 0, s>>>(x, n_mid, n_inner, s_outer, s_mid, n_seg, items, inf, partials, counter, result); break;
     }
 }
 
@@ -137,7 +156,7 @@ extern "C" int HDArrayReduceBufferNoAlloc(const void *x, const char *type, int d
         if (extent[d] > 0 && elems > NOALLOC_MAX_ELEMS / extent[d]) return HDARRAY_ERR_RANGE;
         elems *= extent[d];
     }
-    if (elems > NOALLOC_MAX_ELEMS) return HDARRAY_ERR_RANGE;  // beyond what the static scratch serves
+    if (elems > NOALLOC_MAX_ELEMS) return HDARRAY_ERR_RANGE;  // beyond the per-call limit
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
@@ -154,20 +173,22 @@ extern "C" int HDArrayReduceBufferNoAlloc(const void *x, const char *type, int d
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = (double *)g_scratch_addr[dev];
     unsigned *counter = (unsigned *)(g_scratch_addr[dev] + NOALLOC_COUNTER_OFFSET);
-    // an empty box runs one CTA over no rows: the result is the operator's identity
-    const int64_t rows = elems == 0 ? 0 : n[0] * n[1];
+    // work items: every row split into n_seg segments; an empty box has no items and one CTA
+    // writes the operator's identity
+    const int64_t n_seg = (n[2] + NOALLOC_SEG - 1) / NOALLOC_SEG;
+    const int64_t items = elems == 0 ? 0 : n[0] * n[1] * n_seg;
     int64_t nb = (elems + 65535) / 65536;
     if (nb > NOALLOC_MAX_PARTIALS) nb = NOALLOC_MAX_PARTIALS;
-    if (nb > rows) nb = rows;
+    if (nb > items) nb = items;
     if (nb < 1) nb = 1;
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) {
         cudaGetLastError();
         return HDARRAY_ERR_CUDA;
     }
     switch (dt) {
-    case hda::DT_F64: launch_box<hda::DT_F64>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], rows, partials, counter, result); break;
-    case hda::DT_F32: launch_box<hda::DT_F32>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], rows, partials, counter, result); break;
-    default: launch_box<hda::DT_BF16>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], rows, partials, counter, result); break;
+    case hda::DT_F64: launch_box<hda::DT_F64>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], n_seg > 0 ? n_seg : 1, items, partials, counter, result); break;
+    case hda::DT_F32: launch_box<hda::DT_F32>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], n_seg > 0 ? n_seg : 1, items, partials, counter, result); break;
+    default: launch_box<hda::DT_BF16>((int)op, (int)nb, s, x, n[1], n[2], st[0], st[1], n_seg > 0 ? n_seg : 1, items, partials, counter, result); break;
     }
     if (cudaGetLastError() != cudaSuccess) return HDARRAY_ERR_CUDA;
     return HDARRAY_OK;
