@@ -1,13 +1,20 @@
 """Benchmark of the HDArray hot path on GB300.
 
-Workload (one "step"): 2-D 5-point Jacobi on an 8192 x 8192 binary32 grid split 4 x 4 (BLOCK) over
-16 logical devices, the paper's data/work partition pair (whole grid / interior), 100 Jacobi
-iterations (exchange of the +-1 halo fused into the stencil launch, all 16 devices in one launch
-per iteration, replayed from a CUDA graph of two iterations), then the binary64 residual
-sum((A - B)^2) via HDArrayReduce.  Inputs (2 x 268 MB) exceed the 129 MB L2, so no flush is needed
-between steps.
+Headline workload (one "step"): 2-D 5-point Jacobi on an 8192 x 8192 binary32 grid split 4 x 4
+(BLOCK) over 16 logical devices, the paper's data/work partition pair (whole grid / interior),
+100 Jacobi iterations (exchange of the +-1 halo fused into the stencil launch, all 16 devices in
+one launch per iteration, replayed from a CUDA graph of two iterations), then the binary64
+residual sum((A - B)^2) via HDArrayReduce.  Inputs (2 x 268 MB) exceed the 129 MB L2, so no flush
+is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same JSON line carries one sub-record per other workload (key "workloads"): the 256^2 binary64
+Jacobi (ROW 4, 10 iterations + residual), the 512^3 3-D 7-point stencil over 37 uneven boxes
+(50 iterations), the triangular GEMM tril(A) 8192^2 x B 8192x4096 over 8 row partitions (binary64
+DFMA, bf16x3 and bf16x6 on the tensor cores, the B all-gather alone), and the batch of 512 Jacobi
+instances (200 iterations, one launch per iteration).  Each has its CUDA-event time, its roofline
+and a parity check against an independent numpy evaluation run in the same process.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
 Prints one JSON line.  With N > 1 (torchrun) every rank runs an independent replica (the
 single-GPU partitions do not span GPUs); the value is the sum over ranks of the work divided by
@@ -33,33 +40,43 @@ CELLS = (N - 2) * (N - 2)
 WORKLOAD = ("2-D 5-point Jacobi 8192x8192 FP32, 4x4 BLOCK = 16 logical devices, +-1 halo, "
             "100 iterations per step (exchange fused, one launch per iteration, CUDA graph) "
             "+ FP64 residual via HDArrayReduce")
-PROFILE = os.path.join(ROOT, "profiles", "jacobi2d_fp32_8192_block16.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1809_05657_gb300", "csrc", "k_stencil2d.cu")
+PROFILES = os.path.join(ROOT, "profiles")
+CSRC = os.path.join(ROOT, "paper_1809_05657_gb300", "csrc")
 
+
+# ---------------------------------------------------------------------------------------------
+# peaks, profiles, clocks
+# ---------------------------------------------------------------------------------------------
 
 def peaks():
+    """Measured denominators: HBM copy GB/s and cuBLAS bf16 TFLOP/s (burst, sustained)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return {"hbm": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
-def profiled_traffic(variant):
-    """DRAM bytes per launch of the fused kernel variant `variant` from the committed ncu summary,
-    or None when the kernel source changed since the capture or the variant was not captured."""
+def profiled(name, key, sources):
+    """A figure from the committed ncu summary profiles/<name>: the value of `- key: value` in its
+    "Values read by bench.py" list, or None when any of the kernel sources changed since the capture
+    (the summary records their hash) or the key is absent."""
     try:
-        txt = open(PROFILE).read()
-        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        txt = open(os.path.join(PROFILES, name)).read()
+        h = hashlib.sha256()
+        for s in sources:
+            h.update(open(os.path.join(CSRC, s), "rb").read())
         vals = {}
         for line in txt.splitlines():
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha256_16") != sha:
+        if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
             return None
-        return float(vals["dram_bytes_per_launch_v%d" % variant])
+        return float(vals[key])
     except Exception:
         return None
 
@@ -69,8 +86,8 @@ KERNEL_NAMES_2D = {0: "k_jacobi2d<f32,6> (register ring)", 1: "k_jacobi2d_async<
 
 
 def jacobi_variant(tuned):
-    """The 2-D kernel variant the default workload ran: the tuner's choice, else the environment's
-    or the library default."""
+    """The 2-D kernel variant the headline workload ran: the tuner's choice, else the
+    environment's or the library default."""
     for t in tuned or []:
         if t.get("kernel") == "jacobi2d":
             return int(t["variant"])
@@ -139,10 +156,64 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-# the GPU arm
+# independent numpy evaluations for the in-run parity checks (not the oracle)
 # ---------------------------------------------------------------------------------------------
 
-def setup_jacobi(H, x, dtype, pingpong=True):
+def stencil_steps(w, iters, ft):
+    """`iters` steps of the printed stencil on the array w in arithmetic type ft, updating every
+    cell that is not on w's outer ring: 2-D ((W + E) + N) + S, times 1/4 (Sec. 5); 3-D the six
+    face neighbours x-, x+, y-, y+, z-, z+ summed in that order, then one division by 6."""
+    import numpy as np
+    w = np.array(w, dtype=ft)
+    for _ in range(iters):
+        new = w.copy()
+        if w.ndim == 2:
+            s = w[1:-1, :-2] + w[1:-1, 2:]
+            s = s + w[:-2, 1:-1]
+            s = s + w[2:, 1:-1]
+            new[1:-1, 1:-1] = s * ft(0.25)
+        else:
+            s = w[1:-1, 1:-1, :-2] + w[1:-1, 1:-1, 2:]
+            s = s + w[1:-1, :-2, 1:-1]
+            s = s + w[1:-1, 2:, 1:-1]
+            s = s + w[:-2, 1:-1, 1:-1]
+            s = s + w[2:, 1:-1, 1:-1]
+            new[1:-1, 1:-1, 1:-1] = s / ft(6.0)
+        w = new
+    return w
+
+
+def light_cone(x0, pt, iters, ft):
+    """Value at pt after `iters` stencil steps of the whole array x0 (its outer ring fixed),
+    evaluated on the window of cells within `iters` + 1 of pt: the window's edge cells are never
+    updated, and what that gets wrong moves inward one cell per step, never reaching pt."""
+    lo = [max(0, p - iters - 1) for p in pt]
+    hi = [min(n, p + iters + 2) for p, n in zip(pt, x0.shape)]
+    w = stencil_steps(x0[tuple(slice(a, b) for a, b in zip(lo, hi))], iters, ft)
+    return w[tuple(p - a for p, a in zip(pt, lo))]
+
+
+def cone_check(x0, got, pts, iters, ft32):
+    """Bit-exact comparison of sampled cells with the same-precision evaluation, and the relative
+    error (max |x - x*| / max |x*|) against binary64."""
+    import numpy as np
+    exact, err, mag = 0, 0.0, 0.0
+    for pt in pts:
+        g = got[tuple(pt)]
+        exact += int(np.array(light_cone(x0, pt, iters, ft32), ft32).tobytes() == np.array(g, ft32).tobytes())
+        r64 = float(light_cone(x0, pt, iters, np.float64))
+        err = max(err, abs(float(g) - r64))
+        mag = max(mag, abs(r64))
+    return {"samples": len(pts), "bit_exact_same_precision": exact,
+            "err_vs_binary64": err / mag if mag else err,
+            "reference": "numpy light-cone evaluation in the same precision and in binary64"}
+
+
+# ---------------------------------------------------------------------------------------------
+# the headline workload
+# ---------------------------------------------------------------------------------------------
+
+def setup_jacobi(H, dtype):
     B = H.HDArrayCreate("B", dtype, None, N, N)
     A = H.HDArrayCreate("A", dtype, None, N, N)
     R = H.HDArrayCreate("R", "double", None, N, N)
@@ -210,7 +281,7 @@ def gpu_arm(args, rank, world):
     H.HDArraySetStream(stream.cuda_stream)
     x = synthetic.jacobi_field((N, N), stream=1, dtype="float")
     xh = torch.from_numpy(x).pin_memory()
-    B, A, R, D, W = setup_jacobi(H, x, "float")
+    B, A, R, D, W = setup_jacobi(H, "float")
     H.HDArrayWrite(B, xh, D)
 
     def warm_iters(b, a):
@@ -265,74 +336,63 @@ def gpu_arm(args, rank, world):
     launches = c1["launches"] - c0["launches"]
     per_launch_ms = kernel_ms / (args.steps * ITERS)
     algo_bytes = CELLS * 8 + 2 * xbytes
-    hbm, src = peaks()
+    pk = peaks()
     achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
     value = replica_rate(CELLS * ITERS * args.steps, world, ms) / 1e9
+    residual_us = (t0.elapsed_time(t1) - kernel_ms) / args.steps * 1e3
 
-    # end to end: inputs from pinned host memory, the residual back to the host
-    e2e = None
+    e2e, parity = None, None
     if rank == 0 and not args.quick:
         e2e = e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args)
+        got = np.zeros((N, N), np.float32)
+        H.HDArrayRead(B, got, D)  # the field after exactly 100 iterations from the input
+        parity = cone_check(x, got, sample_points_2d(N), ITERS, np.float32)
     H.HDArrayExit()
     extra = {}
     if rank == 0 and not args.quick:
         extra = extra_forms(H, torch, stream, args)
-    return dict(tuned=None, ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
-                algo_bytes=algo_bytes, xbytes=xbytes, achieved=achieved, hbm=hbm, src=src,
-                clocks=clk.summary(), residual=res, extra=extra, e2e=e2e)
+    return dict(ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
+                algo_bytes=algo_bytes, xbytes=xbytes, achieved=achieved, peaks=pk,
+                clocks=clk.summary(), residual=res, extra=extra, e2e=e2e, parity=parity,
+                residual_us=residual_us)
+
+
+def sample_points_2d(n):
+    """Cells for the light-cone checks: next to the 4 x 4 block boundaries, the corners of the
+    interior and a few seeded interior cells."""
+    import synthetic
+    b = [n * k // 4 for k in range(1, 4)]
+    pts = [(b[0] - 1, b[0]), (b[1], b[1] - 1), (b[2], b[2]), (1, 1), (n - 2, n - 2), (1, n - 2),
+           (b[1] - 1, 1), (n - 2, b[0])]
+    u = synthetic.uniform(8, stream=901)
+    pts += [(1 + int(u[i] * (n - 2)), 1 + int(u[i + 1] * (n - 2))) for i in range(0, 8, 2)]
+    return pts
 
 
 def e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args):
-    """Same step through the public API with the input coming from pinned host memory and the
-    residual read back to the host in every step.  The next step's host->device copy runs on a
-    side stream while this step computes (two device staging buffers, events between the
-    streams); HDArrayWrite then loads the staged field into the partitions' buffers."""
-    flat = xh.reshape(-1)
-    stage = [torch.empty(N * N, dtype=torch.float32, device="cuda") for _ in range(2)]
-    side = torch.cuda.Stream()
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    used = [torch.cuda.Event(), torch.cuda.Event()]
-    for e in used:
-        e.record(stream)
-
-    def prefetch(k):
-        slot = k % 2
-        side.wait_event(used[slot])                    # the Write that last read this buffer is done
-        with torch.cuda.stream(side):
-            stage[slot].copy_(flat, non_blocking=True)  # host -> device, 268 MB
-        copied[slot].record(side)
-
-    def step(k):
-        slot = k % 2
-        stream.wait_event(copied[slot])
-        H.HDArrayWrite(B, stage[slot], D)              # device -> partitions
-        used[slot].record(stream)
-        prefetch(k + 1)                                # overlaps this step's compute
-        for _ in range(2):                             # back into the periodic state
+    """The step through the C ABI with host buffers: HDArrayWrite of the input from pinned host
+    memory into the 16 devices' buffers, the 100 iterations, the residual back to the host
+    (HDArrayReduce).  Timed on the host around whole steps (the Reduce synchronises)."""
+    def step():
+        H.HDArrayWrite(B, xh, D)                       # host -> device, 268 MB
+        for _ in range(2):                             # back into the graph's periodic state
             H.HDArrayApplyKernel("jacobi2d", W, B, A)
             H.HDArrayApplyKernel("jacobi2d", W, A, B)
         H.HDArrayGraphLaunch(gid, (ITERS - 4) // 2)
         H.HDArrayApplyKernel("sqdiff", W, B, A, R)
         return H.HDArrayReduce(R, H.SUM, W)            # device -> host, 8 bytes
-    prefetch(0)
-    k = 0
     for _ in range(max(1, args.warmup)):
-        step(k)
-        k += 1
+        step()
     torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = max(1, args.steps // 2)
-    t0.record(stream)
+    steps = max(2, args.steps // 2)
+    t0 = time.perf_counter()
     for _ in range(steps):
-        step(k)
-        k += 1
-    stream.wait_event(copied[k % 2])  # the timed region holds every copy issued inside it
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    return {"value": CELLS * ITERS / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+        step()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    return {"value": CELLS * ITERS / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "h2d_bytes_per_step": N * N * 4, "d2h_bytes_per_step": 8,
-            "note": "the next step's host->device copy overlaps this step's compute (side stream)"}
+            "path": "HDArrayWrite(B, pinned host array, data partition) -> 100 iterations -> "
+                    "HDArrayApplyKernel(sqdiff) -> HDArrayReduce (host double); host wall clock"}
 
 
 def extra_forms(H, torch, stream, args):
@@ -342,10 +402,11 @@ def extra_forms(H, torch, stream, args):
     import numpy as np
     import synthetic
     out = {}
+    pk = peaks()
     H.HDArrayInit(ndev=P)
     H.HDArraySetStream(stream.cuda_stream)
     xb = synthetic.jacobi_field((N, N), stream=1, dtype="bf16")
-    B, A, R, D, W = setup_jacobi(H, xb, "bf16")
+    B, A, R, D, W = setup_jacobi(H, "bf16")
     H.HDArrayWrite(B, torch.from_numpy(xb.view(np.int16)).pin_memory(), D)
     for _ in range(2):
         H.HDArrayApplyKernel("jacobi2d", W, B, A)
@@ -355,22 +416,16 @@ def extra_forms(H, torch, stream, args):
     H.HDArrayApplyKernel("jacobi2d", W, A, B)
     gid = H.HDArrayGraphEnd()
     H.HDArrayGraphLaunch(gid, 10)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    H.HDArrayGraphLaunch(gid, 50)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / 100
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, 50), 1) / 100
     out["bf16_fused"] = {"gcells_per_s": CELLS / (ms * 1e-3) / 1e9, "us_per_iter": ms * 1e3,
-                         "hbm_frac": CELLS * 4 / (ms * 1e-3) / 1e9 / peaks()[0]}
+                         "hbm_frac": CELLS * 4 / (ms * 1e-3) / 1e9 / pk["hbm"]}
     H.HDArrayExit()
     # plain binary64 form
     H.HDArrayInit(ndev=P)
     H.HDArraySetStream(stream.cuda_stream)
     H.HDArraySetMode(H.HDARRAY_MODE_PLAIN)
     x64 = synthetic.jacobi_field((N, N), stream=1, dtype="double")
-    B, A, R, D, W = setup_jacobi(H, x64, "double")
+    B, A, R, D, W = setup_jacobi(H, "double")
     H.HDArrayWrite(B, torch.from_numpy(x64).pin_memory(), D)
     for _ in range(2):
         H.HDArrayApplyKernel("jacobi2d", W, B, A)
@@ -378,16 +433,21 @@ def extra_forms(H, torch, stream, args):
     torch.cuda.synchronize()
     it = 10
     c0 = H.HDArrayGetCounters()
-    t0.record(stream)
-    for _ in range(it):
-        H.HDArrayApplyKernel("jacobi2d", W, B, A)
-        H.HDArrayApplyKernel("copy", W, A, B)
-    t1.record(stream)
-    torch.cuda.synchronize()
+
+    def plain():
+        for _ in range(it):
+            H.HDArrayApplyKernel("jacobi2d", W, B, A)
+            H.HDArrayApplyKernel("copy", W, A, B)
+    ms = _events(torch, stream, plain, 1) / it
     c1 = H.HDArrayGetCounters()
-    ms = t0.elapsed_time(t1) / it
+    # traffic of one plain iteration: the step (read B, write A) and the copy back (read A,
+    # write B), 8 bytes each per cell
+    gbs = CELLS * 32 / (ms * 1e-3) / 1e9
     out["plain_fp64"] = {"gcells_per_s": CELLS / (ms * 1e-3) / 1e9, "us_per_iter": ms * 1e3,
-                         "launches_per_iter": (c1["launches"] - c0["launches"]) / it}
+                         "launches_per_iter": (c1["launches"] - c0["launches"]) / it,
+                         "hbm_frac_of_its_traffic": gbs / pk["hbm"],
+                         "fp64_tflops": 5 * CELLS / (ms * 1e-3) / 1e12,
+                         "note": "5 binary64 flops per cell update; traffic 32 B per cell (step + copy)"}
     H.HDArrayExit()
     return out
 
@@ -399,13 +459,14 @@ def extra_forms(H, torch, stream, args):
 SAMPLE_N = 2048
 
 
-def oracle_sample(iters):
-    """The oracle on a bounded sample of the workload: a 2048 x 2048 binary32 grid with the same
-    4 x 4 BLOCK data/work partition pair over 16 devices, `iters` ping-pong Jacobi iterations
-    with per-element message generation.  Returns (seconds, cell updates)."""
+def _oracle_program(n, threads):
+    """The Jacobi program of the headline workload on an n x n binary32 grid in the oracle:
+    16-device BLOCK data/work partitions, the input written.  Returns (oracle, B, A, W, work mask,
+    threads used)."""
+    import numpy as np
     import oracle
     import synthetic
-    n = SAMPLE_N
+    used = oracle.set_threads(threads)
     o = oracle.Oracle(P)
     x = synthetic.jacobi_field((n, n), stream=1, dtype="float")
     B = o.create("B", "float", (n, n))
@@ -413,49 +474,104 @@ def oracle_sample(iters):
     D = o.partition(oracle.BLOCK, (n, n), (0, 0), (n, n))
     W = o.partition(oracle.BLOCK, (n, n), (1, 1), (n - 1, n - 1))
     o.write(B, x, D)
+    work = np.zeros(n * n, np.uint8)
+    for box in o.parts[W]:
+        if box is not None:
+            B.mask_box(box[0], box[1], work)
+    return o, B, A, W, work, used
+
+
+def _value_loops(n, iters, threads):
+    """The oracle's Jacobi value loops (the compute of each apply) alone, ping-pong, `iters`
+    iterations on the n x n grid.  Returns (seconds, cell updates, threads used)."""
+    import ctypes
+    import oracle
+    o, B, A, W, work, used = _oracle_program(n, threads)
+    L = oracle.lib()
+    wp = work.ctypes.data_as(ctypes.c_void_p)
+    b, a = B.G, A.G
+    t = time.perf_counter()
+    for _ in range(iters):
+        L.orc_jacobi2d(1, n, n, b.ctypes.data_as(ctypes.c_void_p), a.ctypes.data_as(ctypes.c_void_p), wp)
+        a, b = b, a
+    sec = time.perf_counter() - t
+    oracle.set_threads(1)
+    return sec, (n - 2) * (n - 2) * iters, used
+
+
+def _set_enumeration(n, iters):
+    """The oracle's per-element def/use bookkeeping alone (messages of Eq. 1-2, GDEF update of
+    Eq. 3-4, no values), `iters` ping-pong iterations on the n x n grid.  Returns seconds."""
+    o, B, A, W, work, used = _oracle_program(n, 1)
+    t = time.perf_counter()
+    for _ in range(iters):
+        o.apply("jacobi2d", W, [B, A], compute=False)
+        A, B = B, A
+    return time.perf_counter() - t
+
+
+def cpu_baseline():
+    """The oracle on the host cores: its Jacobi value loops on the full 8192 x 8192 grid on all
+    cores (OpenMP) and on one core, and its per-element set enumeration timed separately."""
+    ncores = os.cpu_count() or 1
+    s_all, c_all, used = _value_loops(N, 12, ncores)
+    s_one, c_one, _ = _value_loops(N, 3, 1)
+    s_set = _set_enumeration(SAMPLE_N, 2)
+    return {"value": c_all / s_all / 1e9, "unit": UNIT, "cores": used, "kind": "oracle", "nproc": ncores,
+            "sample": "%dx%d FP32, the oracle's Jacobi value loops over the 16 devices' work regions, "
+                      "12 iterations on %d threads (%.1f s)" % (N, N, used, s_all),
+            "single_thread": {"value": c_one / s_one / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": "the same loops, 3 iterations on one thread (%.1f s)" % s_one},
+            "set_enumeration": {"seconds_per_iteration": s_set / 2, "cells_per_s": (SAMPLE_N - 2) ** 2 * 2 / s_set,
+                                "sample": "%dx%d, 16 devices, per-element messages and GDEF update "
+                                          "(Eq. 1-4), 2 iterations, one thread" % (SAMPLE_N, SAMPLE_N)}}
+
+
+def oracle_sample(iters, threads):
+    """The whole oracle program on a bounded sample of the headline workload: a 2048 x 2048
+    binary32 grid with the same 16-device BLOCK data/work partitions, `iters` ping-pong Jacobi
+    iterations with per-element message generation and the value loops on `threads` threads.
+    Returns (seconds, cell updates, threads used)."""
+    o, B, A, W, work, used = _oracle_program(SAMPLE_N, threads)
     t = time.perf_counter()
     for _ in range(iters):
         o.apply("jacobi2d", W, [B, A])
         A, B = B, A
-    return time.perf_counter() - t, (n - 2) * (n - 2) * iters
-
-
-def cpu_baseline(iters=8):
-    sec, cells = oracle_sample(iters)
-    return {"value": cells / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%dx%d FP32 grid, same 16-device BLOCK data/work partitions, %d iterations, "
-                      "per-element message generation + Jacobi, single thread (%.1f s)"
-                      % (SAMPLE_N, SAMPLE_N, iters, sec)}
+    sec = time.perf_counter() - t
+    import oracle
+    oracle.set_threads(1)
+    return sec, (SAMPLE_N - 2) * (SAMPLE_N - 2) * iters, used
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
+    ncores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample(1)
-    tot_s, tot_c = 0.0, 0
+        oracle_sample(1, ncores)
+    tot_s, tot_c, used = 0.0, 0, 1
     for _ in range(args.steps):
-        s, c = oracle_sample(1)
+        s, c, used = oracle_sample(1, ncores)
         tot_s += s
         tot_c += c
     value = tot_c / tot_s / 1e9
+    sample = ("%dx%d FP32, 16-device BLOCK partitions, 1 Jacobi iteration per step: per-element "
+              "messages (one thread) + value loops (%d threads)" % (SAMPLE_N, SAMPLE_N, used))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD + " (reference: the CPU oracle on a %dx%d sample, one "
                                               "iteration per step)" % (SAMPLE_N, SAMPLE_N)},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                             "sample": "%dx%d FP32, 16-device BLOCK partitions, 1 Jacobi iteration "
-                                       "per step, single thread" % (SAMPLE_N, SAMPLE_N)},
+            "cpu_baseline": {"kind": "oracle", "cores": used, "nproc": ncores, "value": value, "unit": UNIT,
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ---------------------------------------------------------------------------------------------
-# the other workloads (not the default line): 3-D, the instance batch, the triangular GEMM and
-# the B all-gather alone.  Each prints its own JSON line.
+# the other workloads: sub-records of the default line, or one line each with --workload
 # ---------------------------------------------------------------------------------------------
 
 def _events(torch, stream, fn, reps):
@@ -469,25 +585,41 @@ def _events(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps
 
 
+def _roofline_hbm(kernel, algo_bytes, per_launch_ms, traffic=None):
+    pk = peaks()
+    ach = algo_bytes / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+            "frac": ach / pk["hbm"], "peak_source": pk["source"], "traffic": traffic,
+            "algo_bytes_per_launch": algo_bytes, "launch_us": per_launch_ms * 1e3}
+
+
+def _moved(H, arrs, esize):
+    import numpy as np
+    return sum(int(np.prod(np.subtract(hi, lo))) for a in arrs for _, _, lo, hi in H.HDArrayGetPlan(a)) * esize
+
+
 def workload_stencil3d(H, torch, stream, args):
+    """512^3 binary32 7-point stencil over 37 uneven manual boxes (seeded k-d cuts, extents
+    16-256), +-1 faces, 50 iterations per step, one fused launch per iteration (graph)."""
+    import numpy as np
     import synthetic
     n, nb, iters = args.n3, args.nb3, 50
     boxes = synthetic.kd_boxes(n, nb, stream=3) if nb > 1 else [((0, 0, 0), (n, n, n))]
     work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
     x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
+    xh = torch.from_numpy(x).pin_memory()
     H.HDArrayInit(ndev=nb)
     H.HDArraySetStream(stream.cuda_stream)
     B = H.HDArrayCreate("B", "float", None, n, n, n)
     A = H.HDArrayCreate("A", "float", None, n, n, n)
     D = H.HDArrayPartitionManual((n, n, n), boxes)
     W = H.HDArrayPartitionManual((n, n, n), work)
-    H.HDArrayWrite(B, torch.from_numpy(x).pin_memory(), D)
+    H.HDArrayWrite(B, xh, D)
     for _ in range(2):
         H.HDArrayApplyKernel("stencil3d", W, B, A)
         H.HDArrayApplyKernel("stencil3d", W, A, B)
     H.HDArrayApplyKernel("stencil3d", W, B, A)
-    import numpy as np
-    xbytes = sum(int(np.prod(np.subtract(hi, lo))) for _, _, lo, hi in H.HDArrayGetPlan(B)) * 4
+    xbytes = _moved(H, [B], 4)
     H.HDArrayApplyKernel("stencil3d", W, A, B)
     H.HDArrayGraphBegin()
     H.HDArrayApplyKernel("stencil3d", W, B, A)
@@ -495,24 +627,41 @@ def workload_stencil3d(H, torch, stream, args):
     gid = H.HDArrayGraphEnd()
     for _ in range(args.warmup):
         H.HDArrayGraphLaunch(gid, iters // 2)
-    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
+    steps = max(2, args.steps)
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), steps)
     cells = sum(int(np.prod(np.subtract(hi, lo))) for lo, hi in work)
     per = ms / iters
     algo = cells * 8 + 2 * xbytes
-    hbm, src = peaks()
+    parity = None
+    if not args.quick:
+        # a fresh run of exactly 50 iterations from the input, sampled cells checked
+        H.HDArrayWrite(B, xh, D)
+        for _ in range(2):
+            H.HDArrayApplyKernel("stencil3d", W, B, A)
+            H.HDArrayApplyKernel("stencil3d", W, A, B)
+        H.HDArrayGraphLaunch(gid, (iters - 4) // 2)
+        got = np.zeros((n, n, n), np.float32)
+        H.HDArrayRead(B, got, D)
+        u = synthetic.uniform(9, stream=903)
+        pts = [tuple(1 + int(u[3 * i + d] * (n - 2)) for d in range(3)) for i in range(3)]
+        for lo, hi in boxes[:5]:  # cells at box corners: T-junctions of uneven faces
+            pts.append(tuple(min(n - 2, max(1, v)) for v in lo))
+        parity = cone_check(x, got, pts, iters, np.float32)
     H.HDArrayExit()
-    return {"workload": "3-D 7-point %d^3 FP32, %d uneven manual partitions, 50 iterations per step" % (n, nb),
-            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9,
-            "ms_per_step": ms, "us_per_iter": per * 1e3,
-            "roofline": {"bound": "hbm", "kernel": "k_stencil3d<f32>", "achieved": algo / (per * 1e-3) / 1e9,
-                         "peak": hbm, "frac": algo / (per * 1e-3) / 1e9 / hbm, "peak_source": src,
-                         "algo_bytes_per_launch": algo}}
+    traffic = profiled("stencil3d_cta_fp32_512_37boxes.md", "dram_bytes_per_launch",
+                       ["k_stencil3d.cu", "stencil_common.cuh"]) if (n, nb) == (512, 37) else None
+    return {"workload": "3-D 7-point %d^3 FP32, %d uneven manual partitions (extents 16-256), +-1 faces, "
+                        "50 iterations per step, one fused launch per iteration (graph)" % (n, nb),
+            "metric": UNIT, "value": cells * iters / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32",
+            "steps": steps, "ms_per_step": ms, "us_per_iter": per * 1e3,
+            "exchange_bytes_per_iteration": 2 * xbytes,
+            "roofline": _roofline_hbm("k_stencil3d (fused exchange + stencil)", algo, per, traffic),
+            "parity": parity}
 
 
 def workload_conv2d(H, torch, stream, args):
     """The 2-D convolution of Sec. 5 (eight neighbours and the centre, seeded weights) on the
     8192^2 binary32 grid, BLOCK 4 x 4; no dependency between iterations, so the halo moves once."""
-    import numpy as np
     import synthetic
     N, P, iters = args.grid, 16, 100
     x = synthetic.jacobi_field((N, N), stream=6, dtype="float")
@@ -535,22 +684,18 @@ def workload_conv2d(H, torch, stream, args):
     ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
     cells = (N - 2) * (N - 2)
     per = ms / iters
-    hbm, src = peaks()
     H.HDArrayExit()
     return {"workload": "2-D convolution (3 x 3 weights) %d^2 FP32, BLOCK 4x4 = 16 logical devices, "
                         "%d iterations per step" % (N, iters),
-            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9,
+            "metric": UNIT, "value": cells * iters / (ms * 1e-3) / 1e9, "unit": UNIT,
             "ms_per_step": ms, "us_per_iter": per * 1e3,
-            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d_cta<f32,8,OP_CONV> (packed row streams)",
-                         "achieved": cells * 8 / (per * 1e-3) / 1e9, "peak": hbm,
-                         "frac": cells * 8 / (per * 1e-3) / 1e9 / hbm, "peak_source": src}}
+            "roofline": _roofline_hbm("k_jacobi2d_cta<f32,8,OP_CONV> (packed row streams)", cells * 8, per)}
 
 
 def workload_2mm(H, torch, stream, args):
     """2MM (Sec. 5.1): D = A B, then E = C D, every iteration, on 8 logical devices with row
     blocks and with column blocks -- the same products, different exchanges (Table 3's
     partitioning study).  binary32 arrays on the tensor cores (bf16x3)."""
-    import numpy as np
     import synthetic
     n, P, iters = args.n2mm, 8, 4
     host = {x: torch.from_numpy(synthetic.to_storage(synthetic.normal(n * n, stream=7 * 10 + i).reshape(n, n),
@@ -567,10 +712,9 @@ def workload_2mm(H, torch, stream, args):
 
         def iteration():
             H.HDArrayApplyKernel("gemm", Q, arr["A"], arr["B"], arr["D"], 1.0, 0.0, n, n, n)
-            moved = sum(int(np.prod(np.subtract(hi, lo))) for x in "AB" for _, _, lo, hi in H.HDArrayGetPlan(arr[x]))
+            moved = _moved(H, [arr["A"], arr["B"]], 4)
             H.HDArrayApplyKernel("gemm", Q, arr["C"], arr["D"], arr["E"], 1.0, 0.0, n, n, n)
-            moved += sum(int(np.prod(np.subtract(hi, lo))) for x in "CD" for _, _, lo, hi in H.HDArrayGetPlan(arr[x]))
-            return moved * 4
+            return moved + _moved(H, [arr["C"], arr["D"]], 4)
 
         first = iteration()
         steady = iteration()
@@ -584,11 +728,7 @@ def workload_2mm(H, torch, stream, args):
         forms[form] = {"ms_per_iteration": per, "tflops_algorithmic": flops / (per * 1e-3) / 1e12,
                        "exchange_bytes_first_iteration": first, "exchange_bytes_per_iteration": steady}
         H.HDArrayExit()
-    peak = None
-    try:
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-    except Exception:
-        pass
+    peak = peaks()["bf16"]
     best = forms["col"]
     return {"workload": "2MM (D = A B, E = C D) %d^2 FP32 on tensor cores (bf16x3), 8 logical devices, "
                         "row vs column blocks, %d iterations per step" % (n, iters),
@@ -596,7 +736,7 @@ def workload_2mm(H, torch, stream, args):
             "ms_per_step": best["ms_per_iteration"] * iters, "forms": forms,
             "roofline": {"bound": "tensor", "kernel": "bf16x3 tcgen05 GEMM",
                          "achieved": 3 * best["tflops_algorithmic"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": 3 * best["tflops_algorithmic"] / peak if peak else None,
+                         "frac": 3 * best["tflops_algorithmic"] / peak,
                          "note": "issued MMA flops (3 products per bf16x3 step) of the column form"}}
 
 
@@ -605,7 +745,6 @@ def workload_cov(H, torch, stream, args):
     cores, bf16x3), 32 logical devices: column means, centring, the upper-triangular product with
     absolute use / trapezoid definition sections, the symmetric copy.  Row blocks of C split
     evenly and balanced by the upper triangle's area (a manual partition)."""
-    import numpy as np
     import synthetic
     from paper_1809_05657_gb300.partitions import even_rows, triangle_balanced_rows as balanced_rows
     n = m = args.ncov
@@ -636,19 +775,16 @@ def workload_cov(H, torch, stream, args):
                 H.HDArraySetAbsoluteDef("symmetrize", PC, C, p, (0, 0), (0, 0))
         H.HDArrayWrite(X, x, DX)
 
-        def moved(arrs):
-            return sum(int(np.prod(np.subtract(hi, lo))) for a in arrs for _, _, lo, hi in H.HDArrayGetPlan(a)) * 4
-
         def iteration():
             v = 0
             H.HDArrayApplyKernel("colmean", PM, X, M)
-            v += moved([X])
+            v += _moved(H, [X], 4)
             H.HDArrayApplyKernel("center", DX, X, M, Xc)
-            v += moved([X, M])
+            v += _moved(H, [X, M], 4)
             H.HDArrayApplyKernel("syrk", PC, Xc, C, 1.0 / (n - 1))
-            v += moved([Xc])
+            v += _moved(H, [Xc], 4)
             H.HDArrayApplyKernel("symmetrize", PC, C)
-            v += moved([C])
+            v += _moved(H, [C], 4)
             return v
 
         first = iteration()
@@ -678,11 +814,14 @@ def workload_small(H, torch, stream, args):
     then the copy back), one launch per device and kernel, no graph.  Fused form: the step alone
     with the arrays' roles swapped every iteration (the same values and messages), one launch per
     iteration, the 10 iterations replayed as a CUDA graph.  Both end with the residual of the last
-    iteration, sum((new - old)^2), and must agree bit for bit."""
+    iteration, sum((new - old)^2), and must agree bit for bit; the final field and residual are
+    checked against a numpy binary64 evaluation of the same number of iterations."""
+    import numpy as np
     import synthetic
     N, P, iters = 256, 4, 10
     x = synthetic.jacobi_field((N, N), stream=0, dtype="double")
     out = {}
+    steps = max(2, args.steps)
     for form, mode in (("plain", H.HDARRAY_MODE_PLAIN), ("fused", H.HDARRAY_MODE_FUSED)):
         H.HDArrayInit(ndev=P)
         H.HDArraySetStream(stream.cuda_stream)
@@ -728,27 +867,42 @@ def workload_small(H, torch, stream, args):
             step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             res = step()
-        dt = (time.perf_counter() - t0) / args.steps
+        dt = (time.perf_counter() - t0) / steps
+        res_iters = setup + (args.warmup + steps) * iters  # the last residual's iteration
         out[form] = {"ms_per_step": dt * 1e3, "us_per_iteration": dt * 1e6 / iters, "residual": res}
         if form == "fused":  # the iterations alone, on the device (the graph replays, no residual)
             out[form]["device_us_per_iteration"] = _events(
-                torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps) * 1e3 / iters
+                torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), steps) * 1e3 / iters
+            field_iters = res_iters + steps * iters
+            got = np.zeros((N, N), np.float64)
+            H.HDArrayRead(B, got, D)  # a use by the data partition: after the last graph replay
         H.HDArrayExit()
+    # numpy binary64 evaluation of the same iterations and the last residual
+    prev = stencil_steps(x, res_iters - 1, np.float64)
+    last = stencil_steps(prev, 1, np.float64)
+    res_ref = float(np.sum((last[1:-1, 1:-1] - prev[1:-1, 1:-1]) ** 2))
+    field = stencil_steps(last, field_iters - res_iters, np.float64)
     cells = (N - 2) * (N - 2)
     best = out["fused"]
-    return {"workload": "Jacobi 256^2 FP64, ROW 4, 10 iterations + FP64 residual (HDArrayReduce, "
-                        "synchronous) per step; host wall clock per step (plain: the paper's step and "
-                        "copy kernels; fused: the step with roles swapped, in a graph)",
-            "metric": "Gcell-updates/s", "value": cells * iters / (best["ms_per_step"] * 1e-3) / 1e9,
-            "ms_per_step": best["ms_per_step"], "forms": out,
-            "residuals_equal": out["plain"]["residual"] == out["fused"]["residual"],
+    return {"workload": "Jacobi 256^2 FP64, ROW 4 = 4 logical devices, 10 iterations + FP64 residual "
+                        "(HDArrayReduce, synchronous) per step; host wall clock per step (plain: the paper's "
+                        "step and copy kernels; fused: the step with roles swapped, in a graph)",
+            "metric": UNIT, "value": cells * iters / (best["ms_per_step"] * 1e-3) / 1e9, "unit": UNIT,
+            "dtype": "f64", "steps": steps, "ms_per_step": best["ms_per_step"], "forms": out,
+            "parity": {"residuals_equal_plain_fused": out["plain"]["residual"] == out["fused"]["residual"],
+                       "field_bit_exact_vs_numpy_binary64": bool(np.array_equal(got, field)),
+                       "residual_rel_err_vs_numpy": abs(best["residual"] - res_ref) / abs(res_ref),
+                       "iterations": field_iters},
             "roofline": {"bound": "launch latency", "note": "fits in L2; reported in microseconds per iteration",
                          "frac": None}}
 
 
 def workload_batch(H, torch, stream, args):
+    """512 independent Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL partitions each,
+    binary32), all instances' exchanges and stencils in one launch per iteration (a batch),
+    200 iterations per step replayed from a graph."""
     import numpy as np
     import synthetic
     insts = synthetic.jacobi_instances(args.ninst, stream=5)
@@ -766,20 +920,23 @@ def workload_batch(H, torch, stream, args):
         D = H.HDArrayPartition(t, (r, c), (0, 0), (r, c), P)
         W = H.HDArrayPartition(t, (r, c), (1, 1), (r - 1, c - 1), P)
         H.HDArrayWrite(B, x, D)
-        arrs.append((B, A, W))
+        arrs.append((B, A, W, D))
         cells += (r - 2) * (c - 2)
 
     def iteration(flip):
         H.HDArrayBatchBegin()
-        for B, A, W in arrs:
+        for B, A, W, _ in arrs:
             if flip:
                 H.HDArrayApplyKernel("jacobi2d", W, A, B)
             else:
                 H.HDArrayApplyKernel("jacobi2d", W, B, A)
         H.HDArrayBatchEnd()
 
-    for _ in range(2):
+    xbytes = 0
+    for k in range(2):
         iteration(False)
+        if k == 1:
+            xbytes = _moved(H, [B for B, _, _, _ in arrs], 4)
         iteration(True)
     H.HDArrayGraphBegin()
     iteration(False)
@@ -787,24 +944,67 @@ def workload_batch(H, torch, stream, args):
     gid = H.HDArrayGraphEnd()
     for _ in range(args.warmup):
         H.HDArrayGraphLaunch(gid, iters // 2)
-    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), args.steps)
+    steps = max(2, args.steps)
+    ms = _events(torch, stream, lambda: H.HDArrayGraphLaunch(gid, iters // 2), steps)
     per = ms / iters
-    hbm, src = peaks()
+    total_iters = 6 + (args.warmup + steps) * iters
+    parity = None
+    if not args.quick:
+        # the three smallest instances against a numpy binary32 evaluation of every iteration
+        small = sorted(range(len(insts)), key=lambda i: insts[i][0] * insts[i][1])[:3]
+        exact = 0
+        for i in small:
+            r, c, _, _ = insts[i]
+            B, A, W, D = arrs[i]
+            got = np.zeros((r, c), np.float32)
+            H.HDArrayRead(B, got, D)
+            ref = stencil_steps(synthetic.jacobi_field((r, c), stream=1000 + i, dtype="float"), total_iters, np.float32)
+            exact += int(np.array_equal(got.view(np.uint32), ref.view(np.uint32)))
+        parity = {"instances_checked": len(small), "bit_exact_binary32": exact, "iterations": total_iters,
+                  "shapes": [list(insts[i]) for i in small], "reference": "numpy binary32, every iteration"}
     H.HDArrayExit()
-    return {"workload": "batch of %d Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL parts, "
-                        "FP32), all instances in one launch per iteration, 200 iterations per step" % len(insts),
-            "metric": "Gcell-updates/s", "value": cells * iters / (ms * 1e-3) / 1e9, "cells": cells,
-            "ms_per_step": ms, "us_per_iter": per * 1e3,
-            "roofline": {"bound": "hbm", "kernel": "k_jacobi2d<f32> (batched)",
-                         "achieved": cells * 8 / (per * 1e-3) / 1e9, "peak": hbm,
-                         "frac": cells * 8 / (per * 1e-3) / 1e9 / hbm, "peak_source": src}}
+    traffic = profiled("jacobi2d_batch512_fp32.md", "dram_bytes_per_launch",
+                       ["k_stencil2d.cu", "stencil_common.cuh"]) if args.ninst == 512 else None
+    return {"workload": "batch of %d Jacobi instances (sides log-uniform 64..2048, 2-16 ROW/COL partitions "
+                        "each, FP32), all instances in one launch per iteration, 200 iterations per step "
+                        "(graph)" % len(insts),
+            "metric": UNIT, "value": cells * iters / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32",
+            "cells": cells, "steps": steps, "ms_per_step": ms, "us_per_iter": per * 1e3,
+            "exchange_bytes_per_iteration": 2 * xbytes,
+            "roofline": _roofline_hbm("k_jacobi2d (batched, fused exchange)", cells * 8 + 2 * xbytes, per, traffic),
+            "parity": parity}
+
+
+def fp64_peak(torch):
+    """Measured FP64 matrix-multiply rate of this GPU: cuBLAS DGEMM (torch.matmul) 8192^3,
+    best of 5.  The denominator of the DFMA GEMM's fraction."""
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
 
 
 def workload_trmm(H, torch, stream, args):
+    """tril(A) 8192 x 8192 times B 8192 x 4096 over 8 row partitions (trapezoid use of A, B used
+    whole): the binary64 form (DFMA), and binary32 arrays on the bf16 tensor cores in the bf16x6
+    form (three-way split, meets the binary32 accuracy bound componentwise; the value) and the
+    bf16x3 form; the all-gather of B alone."""
     import numpy as np
     import synthetic
     n, m, P = 8192, 4096, 8
     a, b = synthetic.tri_gemm_inputs(n, m, stream=4, dtype="double")
+    pk = peaks()
     H.HDArrayInit(ndev=P)
     H.HDArraySetStream(stream.cuda_stream)
     A = H.HDArrayCreate("A", "double", None, n, n)
@@ -821,39 +1021,55 @@ def workload_trmm(H, torch, stream, args):
     H.HDArrayWrite(A, torch.from_numpy(a).pin_memory(), RA)
     # the all-gather of B alone (7/8 of B to each of 8 devices), timed from freshly written B
     ex = []
-    for _ in range(max(2, args.steps // 2)):
+    for _ in range(max(3, args.steps // 4)):
         H.HDArrayWrite(B, bh, R)
         ex.append(_events(torch, stream, lambda: H.HDArrayApplyKernel("exchange", R, B), 1))
     moved = 7 * n * m * 8
-    exch_ms = min(ex[1:]) if len(ex) > 1 else ex[0]
+    exch_ms = statistics.median(ex[1:])
     H.HDArrayWrite(B, bh, R)
     H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)  # first call carries the all-gather
     H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)
-    ms = _events(torch, stream, lambda: H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0), max(1, args.steps // 4))
+    reps64 = max(2, args.steps // 8)
+    ms = _events(torch, stream, lambda: H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0), reps64)
     flops = 2.0 * m * (n * (n + 1) / 2)
     H.HDArrayExit()
-    hbm, src = peaks()
-    out = {"workload": "tril(A) 8192x8192 x B 8192x4096, 8 row partitions; FP64 plain form (DFMA) and "
-                       "FP32 arrays on BF16 tensor cores (bf16x3, and bf16x6 for binary32 accuracy)",
-           "metric": "TFLOP/s (algorithmic)", "fp64": {"value": flops / (ms * 1e-3) / 1e12, "ms_per_call": ms},
+    f64peak = fp64_peak(torch)
+    out = {"workload": "tril(A) 8192x8192 x B 8192x4096 (N(0,1)), 8 row partitions with trapezoid use of A, "
+                       "B used whole (all-gather once); FP32 arrays on BF16 tensor cores (bf16x6 = the value, "
+                       "bf16x3) and the FP64 plain form (DFMA)",
+           "metric": "TFLOP/s (algorithmic)", "unit": "TFLOP/s",
+           "fp64": {"tflops_algorithmic": flops / (ms * 1e-3) / 1e12, "ms_per_call": ms, "calls": reps64,
+                    "roofline": {"bound": "fp64", "achieved": flops / (ms * 1e-3) / 1e12, "peak": f64peak,
+                                 "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / f64peak,
+                                 "peak_source": "measured in this run: cuBLAS DGEMM 8192^3 (torch.matmul)",
+                                 "frac_of_nominal": flops / (ms * 1e-3) / 1e12 / 1.25,
+                                 "nominal": "1.25 TFLOP/s FP64 (GB300 data sheet)"}},
            "exchange": {"bytes": moved, "ms": exch_ms, "GB_s": 2 * moved / (exch_ms * 1e-3) / 1e9,
-                        "hbm_frac": 2 * moved / (exch_ms * 1e-3) / 1e9 / hbm, "peak_source": src}}
-    if not args.quick:
-        out["bf16x3"] = trmm_tc(H, torch, stream, args, a, b, 2)
-        out["bf16x6"] = trmm_tc(H, torch, stream, args, a, b, 3)
-        out["value"] = out["bf16x3"]["tflops_algorithmic"]
-    else:
-        out["value"] = out["fp64"]["value"]
+                        "hbm_frac": 2 * moved / (exch_ms * 1e-3) / 1e9 / pk["hbm"], "peak_source": pk["source"]}}
+    out["bf16x6"] = trmm_tc(H, torch, stream, args, a, b, 3)
+    out["bf16x3"] = trmm_tc(H, torch, stream, args, a, b, 2)
+    x6 = out["bf16x6"]
+    out["value"] = x6["tflops_algorithmic"]
+    out["ms_per_step"] = x6["ms_per_call"]
+    out["steps"] = x6["calls"]
+    out["dtype"] = "bf16 (x6 split of f32)"
+    traffic = None
+    out["roofline"] = {"bound": "tensor", "kernel": "k_gemm_bf16x3_panels<3> (bf16x6, tcgen05)",
+                       "achieved": x6["tflops_mma_issued"], "peak": pk["bf16"], "unit": "TFLOP/s",
+                       "frac": x6["tflops_mma_issued"] / pk["bf16"], "peak_source": pk["source"],
+                       "traffic": traffic, "frac_algorithmic": x6["tflops_algorithmic"] / pk["bf16"],
+                       "note": "achieved counts issued MMA flops (6 products per K step over whole tiles); "
+                               "frac_algorithmic counts the triangle's 2.75e11 flops once"}
     return out
 
 
 def trmm_tc(H, torch, stream, args, a64, b64, split):
-    """The same triangular product on binary32 arrays on the tensor cores, in the bf16x3 (split 2)
-    or bf16x6 (split 3) form; error against binary64 on sampled entries (the binary64 product of
-    the binary32 inputs), among them the first rows, where few terms leave the split's error
-    unaveraged."""
+    """The triangular product on binary32 arrays on the tensor cores, in the bf16x3 (split 2) or
+    bf16x6 (split 3) form.  Times the call with its operands' split panels reused (A and B
+    unchanged) and, separately, the call right after B was rewritten (B's split included); the
+    componentwise error against a numpy binary64 product of the binary32 inputs on sampled
+    entries, among them the first rows, where few terms leave the split's error unaveraged."""
     import numpy as np
-    import oracle
     n, m, P = 8192, 4096, 8
     a = a64.astype(np.float32)
     b = b64.astype(np.float32)
@@ -868,13 +1084,18 @@ def trmm_tc(H, torch, stream, args, a64, b64, split):
     for p in range(P):
         r0, r1 = n * p // P, n * (p + 1) // P
         H.HDArraySetTrapezoidUse("trmm", R, A, p, (r0, 0, r0, r0, r1 - 1, 0, r1 - 1, r1 - 1))
+    bh = torch.from_numpy(b).pin_memory()
     H.HDArrayWrite(A, torch.from_numpy(a).pin_memory(), RA)
-    H.HDArrayWrite(B, torch.from_numpy(b).pin_memory(), R)
+    H.HDArrayWrite(B, bh, R)
     H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)
     for _ in range(args.warmup):
         H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0)
     reps = max(2, args.steps)
     ms = _events(torch, stream, lambda: H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0), reps)
+    with_split = []
+    for _ in range(3):  # B rewritten: the call re-splits B's panels (the copy itself is not timed)
+        H.HDArrayWrite(B, bh, R)
+        with_split.append(_events(torch, stream, lambda: H.HDArrayApplyKernel("trmm", R, A, B, C, 1.0, 0.0), 1))
     got = np.zeros((n, m), np.float32)
     H.HDArrayRead(C, got, R)
     H.HDArrayExit()
@@ -882,9 +1103,9 @@ def trmm_tc(H, torch, stream, args, a64, b64, split):
     ij = np.stack([rng.integers(0, n, 256), rng.integers(0, m, 256)], 1)
     ij = np.concatenate([ij, [[0, 0], [1, 5], [127, 4095], [128, 1], [8191, 4095], [4095, 2048]],
                          [[i, j] for i in range(4) for j in rng.integers(0, m, 64)]])
-    ref = oracle.gemm_entries(np.tril(a.astype(np.float64)), b.astype(np.float64), None, 1.0, 0.0, ij)
-    mag = np.array([np.abs(a[i, :i + 1].astype(np.float64)) @ np.abs(b[:i + 1, j].astype(np.float64))
-                    for i, j in ij])
+    a64f, b64f = a.astype(np.float64), b.astype(np.float64)
+    ref = np.array([a64f[i, :i + 1] @ b64f[:i + 1, j] for i, j in ij])
+    mag = np.array([np.abs(a64f[i, :i + 1]) @ np.abs(b64f[:i + 1, j]) for i, j in ij])
     g = got[ij[:, 0], ij[:, 1]].astype(np.float64)
     flops = 2.0 * m * (n * (n + 1) / 2)
     products = 3 if split == 2 else 6
@@ -892,16 +1113,23 @@ def trmm_tc(H, torch, stream, args, a64, b64, split):
     for ti in range(0, n, 128):
         kend = min(n, ti + 128)
         issued += products * 2.0 * 128 * m * ((kend + 63) // 64 * 64)
-    try:
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
-    except Exception:
-        peak = 1900.0
-    return {"ms_per_call": ms, "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
+    peak = peaks()["bf16"]
+    split_ms = statistics.median(with_split) - ms
+    return {"ms_per_call": ms, "calls": reps, "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
             "tflops_mma_issued": issued / (ms * 1e-3) / 1e12,
             "tensor_frac": issued / (ms * 1e-3) / 1e12 / peak, "peak_tflops": peak,
+            "ms_per_call_with_b_split": statistics.median(with_split), "b_split_ms": split_ms,
             "err_componentwise_max": float((np.abs(g - ref) / mag).max()),
             "err_normwise": float(np.abs(g - ref).max() / np.abs(ref).max()),
-            "samples": int(len(ij)), "products_per_k_step": products}
+            "samples": int(len(ij)), "products_per_k_step": products,
+            "reference": "numpy binary64 dot products of the binary32 inputs"}
+
+
+WORKLOADS = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
+             "conv2d": workload_conv2d, "2mm": workload_2mm, "cov": workload_cov, "small": workload_small}
+# the default line's sub-records: the workloads the benchmark's configurations name
+DEFAULT_SUB = [("jacobi2d_256_fp64_row4", "small"), ("stencil3d_512_fp32_37boxes", "stencil3d"),
+               ("trmm_8192x4096_8parts", "trmm"), ("batch512_jacobi2d_fp32", "batch")]
 
 
 def run_workload(args):
@@ -911,16 +1139,35 @@ def run_workload(args):
     build_library()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    fn = {"stencil3d": workload_stencil3d, "batch": workload_batch, "trmm": workload_trmm,
-          "conv2d": workload_conv2d, "2mm": workload_2mm, "cov": workload_cov,
-          "small": workload_small}[args.workload]
     tpath = tune_setup(args)
-    out = fn(H, torch, stream, args)
+    out = WORKLOADS[args.workload](H, torch, stream, args)
     out["autotuned"] = tune_report(tpath)
-    out["steps"] = args.steps
+    out["steps"] = out.get("steps", args.steps)
     out["warmup"] = args.warmup
     print(json.dumps(out))
     return 0
+
+
+def sub_workloads(args):
+    """The other workloads as sub-records of the default line (each on its own context)."""
+    import torch
+    from paper_1809_05657_gb300 import hdarray as H
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {}
+    for key, name in DEFAULT_SUB:
+        t = time.perf_counter()
+        try:
+            r = WORKLOADS[name](H, torch, stream, args)
+        except Exception as e:  # a failing sub-workload is reported, the headline still prints
+            r = {"error": "%s: %s" % (type(e).__name__, e)}
+            try:
+                H.HDArrayExit()
+            except Exception:
+                pass
+        r["wall_s"] = time.perf_counter() - t
+        out[key] = r
+    return out
 
 
 def main():
@@ -929,7 +1176,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--quick", action="store_true", help="skip the comparison forms and e2e")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: skip the comparison forms, e2e, parity checks and sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shapes")
     ap.add_argument("--grid", type=int, default=8192,
@@ -960,13 +1208,18 @@ def main():
         dist.init_process_group("nccl")
     tpath = tune_setup(args)
     r = gpu_arm(args, rank, world)
-    r["tuned"] = tune_report(tpath)
+    tuned = tune_report(tpath)
+    subs = None
+    if rank == 0 and not args.quick:
+        subs = sub_workloads(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     if rank == 0:
-        variant = jacobi_variant(r["tuned"])
-        traffic = profiled_traffic(variant) if N == 8192 else None  # the capture is of 8192^2
+        variant = jacobi_variant(tuned)
+        traffic = profiled("jacobi2d_fp32_8192_block16.md", "dram_bytes_per_launch_v%d" % variant,
+                           ["k_stencil2d.cu", "stencil_common.cuh"]) if N == 8192 else None
+        pk = r["peaks"]
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
@@ -976,18 +1229,21 @@ def main():
                        "iterations_per_step": ITERS, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs 2 x %d MiB %s 129 MB L2 (no flush)" % (N * N * 4 // 2 ** 20, ">" if N * N * 4 > 129e6 else "<=")},
             "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES_2D[variant] + ", fused exchange + stencil",
-                         "achieved": r["achieved"], "peak": r["hbm"], "unit": "GB/s",
-                         "frac": r["achieved"] / r["hbm"], "peak_source": r["src"],
+                         "achieved": r["achieved"], "peak": pk["hbm"], "unit": "GB/s",
+                         "frac": r["achieved"] / pk["hbm"], "peak_source": pk["source"],
                          "traffic": traffic, "algo_bytes_per_launch": r["algo_bytes"],
                          "launch_us": r["per_launch_ms"] * 1e3},
             "exchange": {"bytes_per_iteration": r["xbytes"] * 2, "note": "halo read+write, fused"},
+            "residual_us_per_step": r["residual_us"],
             "cpu_baseline": cpu,
             "e2e": r["e2e"],
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "residual": r["residual"],
-            "autotuned": r["tuned"],
+            "parity": r["parity"],
+            "autotuned": tuned,
             "forms": r["extra"],
+            "workloads": subs,
         }
         print(json.dumps(line))
     if world > 1:
