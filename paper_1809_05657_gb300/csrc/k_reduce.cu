@@ -11,6 +11,31 @@
 
 namespace hda {
 
+// binary32 -> binary64 by integer operations (exact, like the conversion instruction, which on
+// this GPU runs in the slow binary64 pipe): a normal number keeps its sign and significand and
+// moves its exponent bias from 127 to 1023; a subnormal is normalised; infinities and NaNs keep
+// their payload (NaNs made quiet).
+__device__ __forceinline__ double f32_bits_to_f64(unsigned u)
+{
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e - 1u < 254u)  // normal: exponent field e + (1023 - 127)
+        return __longlong_as_double((long long)(sign | (((unsigned long long)(u & 0x7fffffffu) << 29) +
+                                                        (896ull << 52))));
+    unsigned long long bits;
+    if (e == 0xffu) {
+        bits = sign | 0x7ff0000000000000ull | ((unsigned long long)m << 29);
+        if (m) bits |= 0x0008000000000000ull;
+    } else if (m == 0) {
+        bits = sign;
+    } else {  // m * 2^-149 with the top bit of m at position k: exponent field k - 149 + 1023
+        const int k = 31 - __clz(m);
+        bits = sign | ((unsigned long long)(k + 874) << 52) |
+               (((unsigned long long)m << (52 - k)) & 0x000fffffffffffffull);
+    }
+    return __longlong_as_double((long long)bits);
+}
+
 template <int DT>
 __device__ __forceinline__ double ldd(const void *p, int64_t i);
 template <>
@@ -21,12 +46,12 @@ __device__ __forceinline__ double ldd<DT_F64>(const void *p, int64_t i)
 template <>
 __device__ __forceinline__ double ldd<DT_F32>(const void *p, int64_t i)
 {
-    return (double)reinterpret_cast<const float *>(p)[i];
+    return f32_bits_to_f64(reinterpret_cast<const unsigned *>(p)[i]);
 }
 template <>
 __device__ __forceinline__ double ldd<DT_BF16>(const void *p, int64_t i)
 {
-    return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
+    return f32_bits_to_f64((unsigned)reinterpret_cast<const unsigned short *>(p)[i] << 16);
 }
 
 template <int OP>
@@ -98,6 +123,184 @@ __global__ void __launch_bounds__(256) k_reduce(const RedTask *__restrict__ task
         *result = s;
         *counter = 0u;  // ready for the next launch
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// R = (X - Y)^2 in binary64 over boxes (the residual field of the Jacobi program), optionally
+// folding the stored values' sum on the way (SUM partials per CTA, the last CTA folds them into
+// `result`): HDArrayReduce(R, SUM) over the same boxes then needs no second pass over R.
+//
+// Work: CTA b takes tasks b, b + G, ...; a warp per row.  Every buffer's rows share one 16-byte
+// phase (element c is 16-byte aligned in x, y and r alike once the head is done), so a row is a
+// scalar head up to x's first 16-byte boundary, then 16-byte vectors of x and y (V elements)
+// with V doubles of r stored per vector, two vectors in flight per lane, then a scalar tail.  A
+// row whose y or r does not share x's phase runs scalar.  Each lane folds its elements in a
+// fixed order and the trees are fixed, so the sum is the same on every run of a plan.
+// ------------------------------------------------------------------------------------------
+template <int DT>
+struct Vec16;
+template <>
+struct Vec16<DT_F64> {
+    static constexpr int V = 2;
+    __device__ static void load(const void *p, double *out)
+    {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+    }
+};
+template <>
+struct Vec16<DT_F32> {
+    static constexpr int V = 4;
+    __device__ static void load(const void *p, double *out)
+    {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        out[0] = f32_bits_to_f64(v.x);
+        out[1] = f32_bits_to_f64(v.y);
+        out[2] = f32_bits_to_f64(v.z);
+        out[3] = f32_bits_to_f64(v.w);
+    }
+};
+template <>
+struct Vec16<DT_BF16> {
+    static constexpr int V = 8;
+    __device__ static void load(const void *p, double *out)
+    {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {  // bfloat16 -> binary32 is exact: the bits move up 16 places
+            out[2 * k] = f32_bits_to_f64(w[k] << 16);
+            out[2 * k + 1] = f32_bits_to_f64(w[k] & 0xffff0000u);
+        }
+    }
+};
+
+template <int DT, bool SUM>
+__global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks, int ntasks, double *partials,
+                                                unsigned *counter, double *result)
+{
+    constexpr int V = Vec16<DT>::V;
+    constexpr int ES = 16 / V;  // bytes per stored element of x and y
+    __shared__ double wsum[8];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double acc = 0.0;
+    for (int ti = blockIdx.x; ti < ntasks; ti += gridDim.x) {
+        const PwTask t = tasks[ti];
+        const int n = t.n_inner;
+        for (int row = t.row_begin + warp; row < t.row_end; row += nw) {
+            const int o = row / t.n_mid, m = row - o * t.n_mid;
+            const char *x = reinterpret_cast<const char *>(t.x) + (o * t.xs_outer + m * t.xs_mid) * ES;
+            const char *y = reinterpret_cast<const char *>(t.y) + (o * t.ys_outer + m * t.ys_mid) * ES;
+            double *r = t.r + o * t.rs_outer + m * t.rs_mid;
+            int head = (int)(((16 - ((uintptr_t)x & 15)) & 15) / ES);
+            if (head > n) head = n;
+            const bool vec = (((uintptr_t)(y + head * ES) | (uintptr_t)(r + head)) & 15) == 0;
+            const int nv = vec ? (n - head) / V : 0;
+            const int vend = vec ? head + nv * V : 0;
+            auto scalar = [&](int c) {
+                const double d = ldd<DT>(x, c) - ldd<DT>(y, c);
+                const double q = d * d;
+                r[c] = q;
+                if (SUM) acc += q;
+            };
+            // scalar head (head < V <= 8 elements), then the tail after the vectors; a row
+            // without a common phase is all tail (vend = 0)
+            if (vec && lane < head) scalar(lane);
+            for (int c = vend + lane; c < n; c += 32) scalar(c);
+            int v = lane;
+            for (; v + 32 < nv; v += 64) {  // two vectors in flight per lane
+                double a0[V], b0[V], a1[V], b1[V];
+                Vec16<DT>::load(x + (head + v * V) * ES, a0);
+                Vec16<DT>::load(y + (head + v * V) * ES, b0);
+                Vec16<DT>::load(x + (head + (v + 32) * V) * ES, a1);
+                Vec16<DT>::load(y + (head + (v + 32) * V) * ES, b1);
+                double q0[V], q1[V];
+#pragma unroll
+                for (int k = 0; k < V; k++) {
+                    const double d0 = a0[k] - b0[k], d1 = a1[k] - b1[k];
+                    q0[k] = d0 * d0;
+                    q1[k] = d1 * d1;
+                }
+                double2 *r0 = reinterpret_cast<double2 *>(r + head + v * V);
+                double2 *r1 = reinterpret_cast<double2 *>(r + head + (v + 32) * V);
+#pragma unroll
+                for (int k = 0; k < V / 2; k++) {
+                    r0[k] = make_double2(q0[2 * k], q0[2 * k + 1]);
+                    r1[k] = make_double2(q1[2 * k], q1[2 * k + 1]);
+                }
+                if (SUM) {
+#pragma unroll
+                    for (int k = 0; k < V; k++) acc += q0[k];
+#pragma unroll
+                    for (int k = 0; k < V; k++) acc += q1[k];
+                }
+            }
+            for (; v < nv; v += 32) {
+                double a0[V], b0[V], q0[V];
+                Vec16<DT>::load(x + (head + v * V) * ES, a0);
+                Vec16<DT>::load(y + (head + v * V) * ES, b0);
+#pragma unroll
+                for (int k = 0; k < V; k++) {
+                    const double d0 = a0[k] - b0[k];
+                    q0[k] = d0 * d0;
+                }
+                double2 *r0 = reinterpret_cast<double2 *>(r + head + v * V);
+#pragma unroll
+                for (int k = 0; k < V / 2; k++) r0[k] = make_double2(q0[2 * k], q0[2 * k + 1]);
+                if (SUM) {
+#pragma unroll
+                    for (int k = 0; k < V; k++) acc += q0[k];
+                }
+            }
+        }
+    }
+    if (!SUM) return;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = wsum[0];
+        for (int w = 1; w < nw; w++) b += wsum[w];
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double *vp = partials;
+        double s = vp[0];
+        for (unsigned b = 1; b < gridDim.x; b++) s += vp[b];
+        *result = s;
+        *counter = 0u;  // ready for the next launch
+    }
+}
+
+cudaError_t launch_sqdiff(int dtype, const PwTask *tasks, int ntasks, int nblocks, double *partials,
+                          unsigned *counter, double *result, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    const bool sum = partials != nullptr;
+    if (!sum || nblocks < 1) nblocks = ntasks;
+    switch (dtype) {
+    case DT_F64:
+        if (sum) k_sqdiff<DT_F64, true><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        else k_sqdiff<DT_F64, false><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        break;
+    case DT_F32:
+        if (sum) k_sqdiff<DT_F32, true><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        else k_sqdiff<DT_F32, false><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        break;
+    case DT_BF16:
+        if (sum) k_sqdiff<DT_BF16, true><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        else k_sqdiff<DT_BF16, false><<<nblocks, 256, 0, s>>>(tasks, ntasks, partials, counter, result);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 template <int DT>

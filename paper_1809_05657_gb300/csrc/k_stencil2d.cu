@@ -415,52 +415,4 @@ cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------------
-// R = (X - Y)^2 in binary64 (a residual field for HDArrayReduce).
-// ------------------------------------------------------------------------------------------
-template <int DT>
-__global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks)
-{
-    using E = typename Elem<DT>::E;
-    const PwTask t = tasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int n = t.n_inner;
-    for (int row = t.row_begin + warp; row < t.row_end; row += nw) {  // a warp per row
-        const int o = row / t.n_mid, m = row - o * t.n_mid;
-        const E *x = reinterpret_cast<const E *>(t.x) + o * t.xs_outer + m * t.xs_mid;
-        const E *y = reinterpret_cast<const E *>(t.y) + o * t.ys_outer + m * t.ys_mid;
-        double *r = t.r + o * t.rs_outer + m * t.rs_mid;
-        int c = lane;
-        for (; c + 96 < n; c += 128) {  // four independent loads in flight per lane
-            double a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                a[u] = (double)Elem<DT>::load1(x + c + 32 * u);
-                b[u] = (double)Elem<DT>::load1(y + c + 32 * u);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const double d = a[u] - b[u];
-                r[c + 32 * u] = d * d;
-            }
-        }
-        for (; c < n; c += 32) {
-            const double d = (double)Elem<DT>::load1(x + c) - (double)Elem<DT>::load1(y + c);
-            r[c] = d * d;
-        }
-    }
-}
-
-cudaError_t launch_sqdiff(int dtype, const PwTask *tasks, int ntasks, cudaStream_t s)
-{
-    if (ntasks <= 0) return cudaSuccess;
-    switch (dtype) {
-    case DT_F64: k_sqdiff<DT_F64><<<ntasks, 256, 0, s>>>(tasks); break;
-    case DT_F32: k_sqdiff<DT_F32><<<ntasks, 256, 0, s>>>(tasks); break;
-    case DT_BF16: k_sqdiff<DT_BF16><<<ntasks, 256, 0, s>>>(tasks); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
 }  // namespace hda

@@ -126,7 +126,10 @@ struct PwTask {
     int32_t n_mid, n_inner;
     int32_t row_begin, row_end;
 };
-cudaError_t launch_sqdiff(int dtype, const PwTask *tasks, int ntasks, cudaStream_t s);
+// With partials == nullptr: one CTA per task, R only.  Otherwise `nblocks` CTAs also fold the sum of
+// the stored values: partials (nblocks doubles), counter (zero on entry, left zero), result.
+cudaError_t launch_sqdiff(int dtype, const PwTask *tasks, int ntasks, int nblocks, double *partials,
+                          unsigned *counter, double *result, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Reduction of boxes to one double (HDArrayReduce, Table 2).  Deterministic: the task list and

@@ -31,6 +31,7 @@ struct GraphRec {
     std::vector<ArrInfo> arrays;
     std::vector<std::shared_ptr<Plan>> refs;
     std::vector<std::shared_ptr<DevMem>> mems;
+    std::vector<HDArray *> defined;  // arrays the recorded calls define (their versions move on)
     int64_t nkernels = 0;
 };
 
@@ -65,8 +66,24 @@ struct Ctx {
     std::vector<std::shared_ptr<Plan>> rec_refs;
     std::vector<std::shared_ptr<DevMem>> rec_mems;
     std::map<HDArray *, std::pair<int, uint64_t>> rec_pre;  // state id, generation at first touch
+    std::set<HDArray *> rec_defined;                         // arrays the recorded calls define
     std::map<int, GraphRec> graphs;
     int next_graph = 1;
+    // the sum of the last residual launch's values (HDArrayReduce(R, SUM) over the same boxes,
+    // while R is unchanged, reads it instead of folding R again)
+    struct SqSum {
+        HDArray *R = nullptr;
+        uint64_t version = 0;
+        std::vector<Box> boxes;
+        std::shared_ptr<Plan> pl;  // keeps the scratch alive
+        const double *sum = nullptr;
+    } sq_sum;
+    // reduction task tables per (array, partition, buffer epoch)
+    struct RedPlan {
+        std::shared_ptr<DevMem> mem;
+        int ntasks = 0, nblocks = 0;
+    };
+    std::map<std::tuple<uint64_t, int, uint64_t>, RedPlan> red_plans;
     // reduction scratch
     double *red_partials = nullptr;
     unsigned *red_counter = nullptr;
@@ -1283,13 +1300,28 @@ int compile_plan(Plan &pl)
         pl.launches.push_back(L);
     }
     if (!pw.empty()) {
-        auto add = [&](int b, int e) {
+        auto add = [&](int b, int e, const void *red, int64_t nblocks) {
             LaunchRec L; L.kind = L_SQDIFF; L.dtype = pl.args[0]->dtype;
             L.p0 = (const PwTask *)addr[2] + b; L.n0 = e - b;
+            L.p1 = red; L.n1 = nblocks;
             pl.launches.push_back(L);
         };
-        if (plain) for (auto &gr : pw_groups) add(gr.first, gr.second);
-        else add(0, (int)pw.size());
+        if (plain) {
+            for (auto &gr : pw_groups) add(gr.first, gr.second, nullptr, 0);
+        } else {  // one launch that also folds the sum of R (read back by HDArrayReduce)
+            const int64_t nb = std::min<int64_t>((int64_t)pw.size(), 4 * (int64_t)g->nsm);
+            if (!pl.red || pl.red->bytes < red_bytes(nb)) {
+                pl.red = std::make_shared<DevMem>();
+                const int arc = dev_alloc(&pl.red->ptr, red_bytes(nb));
+                if (arc) {
+                    pl.red->ptr = nullptr;
+                    return arc;
+                }
+                pl.red->bytes = red_bytes(nb);
+                CUDA_TRY(cudaMemset(pl.red->ptr, 0, red_bytes(nb)));
+            }
+            add(0, (int)pw.size(), pl.red->ptr, nb);
+        }
     }
     if (!gp.empty()) {
         auto add = [&](int b, int e, int mr, int mc) {
@@ -1861,6 +1893,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
     // bookkeeping moves on; the GPU work is issued now or at the end of the batch
     for (ArrStep &st : pl->steps) {
         if (g->recording && !g->rec_pre.count(st.a)) g->rec_pre[st.a] = {st.a->cur, st.a->generation};
+        if (g->recording && st.defined) g->rec_defined.insert(st.a);
         st.a->cur = st.post;
         if (st.defined) st.a->version++;
         if (st.used) st.a->last_moves = st.moves;
@@ -1870,7 +1903,20 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
         g->batch.push_back(pl);
         return HDARRAY_OK;
     }
-    return run_plan(pl);
+    rc = run_plan(pl);
+    if (rc) return rc;
+    if (k.kind == K_SQDIFF && pl->red && !g->host_only) {
+        // the launch left the sum of R's new values over the work boxes in the plan's scratch
+        for (const LaunchRec &L : pl->launches) {
+            if (L.kind != L_SQDIFF || !L.p1) continue;
+            g->sq_sum.R = args[2];
+            g->sq_sum.version = args[2]->version;
+            g->sq_sum.boxes = pt.box;
+            g->sq_sum.pl = pl;
+            g->sq_sum.sum = (const double *)((const char *)L.p1 + red_counter_offset(L.n1) + 128);
+        }
+    }
+    return HDARRAY_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -2175,39 +2221,59 @@ int reduce_impl(HDArray *a, double *res, int op, int part)
         *res = 0.0;
         return HDARRAY_OK;
     }
-    std::vector<RedTask> tasks;
-    for (int p = 0; p < pt.nparts; p++) {
-        const Box &W = pt.box[p];
-        if (W.empty()) continue;
-        const DevBuf &b = a->buf[p];
-        View3 v = view_of(a, b, W);
-        RedTask t;
-        t.x = b.ptr + elem_off(b, W.lo) * a->esize;
-        t.s_outer = v.s_outer;
-        t.s_mid = v.s_mid;
-        t.n_mid = (int32_t)v.n_mid;
-        t.n_inner = (int32_t)v.n_inner;
-        const int64_t rows = v.n_outer * v.n_mid;
-        const int64_t per = std::max<int64_t>(1, 65536 / std::max<int64_t>(1, v.n_inner));
-        for (int64_t r = 0; r < rows; r += per) {
-            t.row_begin = (int32_t)r;
-            t.row_end = (int32_t)std::min(rows, r + per);
-            tasks.push_back(t);
-        }
+    const Ctx::SqSum &sq = g->sq_sum;
+    if (op == HDARRAY_SUM && sq.R == a && sq.sum && sq.version == a->version && sq.boxes == pt.box &&
+        a->last_moves.empty()) {
+        // R is unchanged since the residual launch that defined it on exactly these boxes, and
+        // that launch folded the sum of the values it stored: read it back
+        CUDA_TRY(cudaMemcpyAsync(g->host_result, sq.sum, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+        *res = *g->host_result;
+        return check_device_error();
     }
+    const auto key = std::make_tuple(a->uid, part, a->epoch);
+    auto pit = g->red_plans.find(key);
+    if (pit == g->red_plans.end()) {  // the task table of this (array, partition, buffers)
+        std::vector<RedTask> tasks;
+        for (int p = 0; p < pt.nparts; p++) {
+            const Box &W = pt.box[p];
+            if (W.empty()) continue;
+            const DevBuf &b = a->buf[p];
+            View3 v = view_of(a, b, W);
+            RedTask t;
+            t.x = b.ptr + elem_off(b, W.lo) * a->esize;
+            t.s_outer = v.s_outer;
+            t.s_mid = v.s_mid;
+            t.n_mid = (int32_t)v.n_mid;
+            t.n_inner = (int32_t)v.n_inner;
+            const int64_t rows = v.n_outer * v.n_mid;
+            const int64_t per = std::max<int64_t>(1, 65536 / std::max<int64_t>(1, v.n_inner));
+            for (int64_t r = 0; r < rows; r += per) {
+                t.row_begin = (int32_t)r;
+                t.row_end = (int32_t)std::min(rows, r + per);
+                tasks.push_back(t);
+            }
+        }
+        Ctx::RedPlan rp;
+        rp.ntasks = (int)tasks.size();
+        rp.nblocks = (int)std::min<size_t>(tasks.size(), (size_t)2 * g->nsm);
+        if (!tasks.empty()) {
+            std::vector<const char *> addr;
+            rc = upload({{tasks.data(), tasks.size() * sizeof(RedTask)}}, rp.mem, addr);
+            if (rc) return rc;
+        }
+        if (g->red_plans.size() >= 256) g->red_plans.clear();
+        pit = g->red_plans.emplace(key, std::move(rp)).first;
+    }
+    const Ctx::RedPlan &rp = pit->second;
     const double ident[4] = {0.0, 1.0, -__builtin_inf(), __builtin_inf()};
-    if (tasks.empty()) {
+    if (rp.ntasks == 0) {
         *res = ident[op];
         return HDARRAY_OK;
     }
-    const int nblocks = (int)std::min<size_t>(tasks.size(), (size_t)2 * g->nsm);
-    rc = ensure_reduce_scratch(nblocks);
+    rc = ensure_reduce_scratch(rp.nblocks);
     if (rc) return rc;
-    std::shared_ptr<DevMem> mem;
-    std::vector<const char *> addr;
-    rc = upload({{tasks.data(), tasks.size() * sizeof(RedTask)}}, mem, addr);
-    if (rc) return rc;
-    CUDA_TRY(launch_reduce(a->dtype, op, (const RedTask *)addr[0], (int)tasks.size(), nblocks,
+    CUDA_TRY(launch_reduce(a->dtype, op, (const RedTask *)rp.mem->ptr, rp.ntasks, rp.nblocks,
                            g->red_partials, g->red_counter, g->red_result, g->stream));
     g->counters[0]++;
     CUDA_TRY(cudaMemcpyAsync(g->host_result, g->red_result, sizeof(double), cudaMemcpyDeviceToHost,
@@ -2471,7 +2537,12 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_STENCIL3D:
         return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
                                 (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
-    case L_SQDIFF: return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, s);
+    case L_SQDIFF: {
+        char *red = (char *)const_cast<void *>(L.p1);
+        unsigned *counter = red ? (unsigned *)(red + red_counter_offset(L.n1)) : nullptr;
+        double *sum = red ? (double *)(red + red_counter_offset(L.n1) + 128) : nullptr;
+        return launch_sqdiff(L.dtype, (const PwTask *)L.p0, (int)L.n0, (int)L.n1, (double *)red, counter, sum, s);
+    }
     case L_GEMM64:
         return launch_gemm_f64((const GemmPart *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, L.f0, L.f1, s);
     case L_GEMM_TC:
@@ -2547,6 +2618,8 @@ void HDArrayExit(void)
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     g->graphs.clear();
+    g->sq_sum = Ctx::SqSum();
+    g->red_plans.clear();
     g->memo.clear();
     g->batch.clear();
     g->batch_cache.clear();
@@ -2630,6 +2703,11 @@ int HDArrayFree(HDArray_t *hA)
 {
     if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
     if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->sq_sum.R == hA) g->sq_sum = Ctx::SqSum();
+    for (auto it = g->red_plans.begin(); it != g->red_plans.end();) {
+        if (std::get<0>(it->first) == hA->uid) it = g->red_plans.erase(it);
+        else ++it;
+    }
     drop_plans_of(hA);
     for (auto it = g->abs.begin(); it != g->abs.end();) {
         if (std::get<2>(it->first) == hA->uid) it = g->abs.erase(it);
@@ -2985,6 +3063,7 @@ int HDArrayGraphBegin(void)
     g->rec_refs.clear();
     g->rec_mems.clear();
     g->rec_pre.clear();
+    g->rec_defined.clear();
     return HDARRAY_OK;
 }
 
@@ -3014,6 +3093,7 @@ int HDArrayGraphEnd(int *graphID)
     CUDA_TRY(cudaGraphInstantiate(&gr.exec, gr.graph, 0));
     gr.refs = g->rec_refs;
     gr.mems = g->rec_mems;
+    gr.defined.assign(g->rec_defined.begin(), g->rec_defined.end());
     gr.nkernels = (int64_t)g->rec.size();
     g->rec.clear();
     g->rec_refs.clear();
@@ -3037,8 +3117,10 @@ int HDArrayGraphLaunch(int graphID, int nrep)
         if (nrep > 1 && ai.pre != ai.post) return set_err(HDARRAY_ERR_STATE);
     }
     for (int r = 0; r < nrep; r++) CUDA_TRY(cudaGraphLaunch(gr.exec, g->stream));
-    if (nrep > 0)
+    if (nrep > 0) {
         for (auto &ai : gr.arrays) ai.a->cur = ai.post;
+        for (HDArray *a : gr.defined) a->version += (uint64_t)nrep;  // their contents changed
+    }
     g->counters[0] += gr.nkernels * nrep;
     g->counters[4] += nrep;
     return HDARRAY_OK;

@@ -143,7 +143,13 @@ struct Plan {
     uint64_t split_version[2] = {~0ull, ~0ull};  // content versions of A and B the panels hold
     std::vector<HDArrayWork_t> user_work;         // a user kernel's per-device work
     bool alt = false;                             // next call takes the launches' p1_alt tables
+    std::shared_ptr<DevMem> red;  // residual plans: per-CTA partials, counter and the sum of R
 };
+
+// Layout of a residual plan's `red` scratch for nblocks CTAs: partials, then the counter, then the
+// sum of the values the launch stored.
+inline size_t red_counter_offset(int64_t nblocks) { return (size_t)((nblocks * 8 + 255) / 256 * 256); }
+inline size_t red_bytes(int64_t nblocks) { return red_counter_offset(nblocks) + 256; }
 
 // Device memory: cudaMalloc / cudaFree, or the allocator set with HDArraySetAllocator (each
 // allocation is released by the allocator that provided it).

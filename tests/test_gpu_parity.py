@@ -234,6 +234,82 @@ def test_residual_flow_cfg1(gpu_lib):
     assert w > 0 and abs(g - w) <= 1e-12 * abs(w)
 
 
+@pytest.mark.parametrize("dims,P,ptype,dtype", [((203, 157), 6, BLOCK, "float"), ((131, 267), 5, COL, "bf16"),
+                                              ((97, 141), 3, ROW, "double"), ((37, 45, 61), 4, COL, "float")])
+def test_residual_fused_sum(gpu_lib, dims, P, ptype, dtype):
+    """The fused form's residual: R = (X - Y)^2 stored bit-exact on every device, and
+    HDArrayReduce(R, SUM) over the residual's own boxes (the sum the residual launch folded) and
+    over another partition (a separate fold of R) both within 1e-12 of the oracle, also after R is
+    redefined by a second residual.  The partitions' odd boundaries put rows at every 16-byte
+    phase, so the kernel's scalar heads and tails and its vectors are all exercised."""
+    nd = len(dims)
+    n = int(np.prod(dims))
+    x = synthetic.to_storage(synthetic.uniform(n, stream=31).reshape(dims), dtype)
+    y = synthetic.to_storage(synthetic.uniform(n, stream=32).reshape(dims), dtype)
+    z = synthetic.to_storage(synthetic.uniform(n, stream=33).reshape(dims), dtype)
+    prog = [("create", "X", dtype, dims), ("create", "Y", dtype, dims), ("create", "Z", dtype, dims),
+            ("create", "R", "double", dims),
+            ("part", "D", ptype, dims, (0,) * nd, dims, P),
+            ("part", "W", ptype, dims, (1,) * nd, tuple(k - 2 for k in dims), P),
+            ("part", "V", ROW, dims, (1,) * nd, tuple(k - 2 for k in dims), 2),
+            ("write", "X", "D"), ("write", "Y", "D"), ("write", "Z", "D"),
+            ("apply", "sqdiff", "W", ["X", "Y", "R"]),
+            ("reduce", "R", 0, "W"), ("reduce", "R", 0, "W"), ("reduce", "R", 0, "V"),
+            ("apply", "sqdiff", "W", ["Z", "Y", "R"]),
+            ("reduce", "R", 0, "W"), ("reduce", "R", 2, "W")]
+    lib, orc, lib_out, orc_out, _ = run_program(prog, P, {"X": x, "Y": y, "Z": z}, gpu_lib)
+    nred = 0
+    for lo, oo, op in zip(lib_out, orc_out, prog):
+        if op[0] != "reduce":
+            continue
+        g, w = lo["_value"], oo["_value"]
+        assert w > 0
+        assert (g == w) if op[2] == 2 else abs(g - w) <= 1e-12 * abs(w), (op, g, w)
+        nred += 1
+    assert nred == 5
+
+
+def test_residual_sum_follows_graph_replays(gpu_lib):
+    """A residual recorded in a graph: every replay redefines R, so HDArrayReduce after the
+    replays folds the replays' values (the sum kept from the recorded call is not reused), and
+    the result matches the oracle after the same calls."""
+    torch = pytest.importorskip("torch")
+    dims, P, dtype = (150, 211), 4, "float"
+    x = synthetic.jacobi_field(dims, stream=34, dtype=dtype)
+    gpu_lib(P)
+    B = H.HDArrayCreate("B", dtype, None, *dims)
+    A = H.HDArrayCreate("A", dtype, None, *dims)
+    R = H.HDArrayCreate("R", "double", None, *dims)
+    D = H.HDArrayPartition(BLOCK, dims, (0, 0), dims, P)
+    W = H.HDArrayPartition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1), P)
+    H.HDArrayWrite(B, x, D)
+    for _ in range(2):
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    H.HDArrayApplyKernel("sqdiff", W, B, A, R)  # R defined before the recording: a periodic graph
+    H.HDArrayGraphBegin()
+    H.HDArrayApplyKernel("jacobi2d", W, B, A)
+    H.HDArrayApplyKernel("jacobi2d", W, A, B)
+    H.HDArrayApplyKernel("sqdiff", W, B, A, R)
+    gid = H.HDArrayGraphEnd()
+    H.HDArrayGraphLaunch(gid, 3)
+    got = H.HDArrayReduce(R, 0, W)
+    torch.cuda.synchronize()
+    o = oracle.Oracle(P)
+    ob, oa = o.create("B", dtype, dims), o.create("A", dtype, dims)
+    orr = o.create("R", "double", dims)
+    od = o.partition(BLOCK, dims, (0, 0), dims)
+    ow = o.partition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1))
+    o.write(ob, x, od)
+    for i in range(2 + 1 + 3):  # warm-up, recording, three replays
+        o.apply("jacobi2d", ow, [ob, oa])
+        o.apply("jacobi2d", ow, [oa, ob])
+        if i >= 1:
+            o.apply("sqdiff", ow, [ob, oa, orr])
+    want, _ = o.reduce(orr, 0, ow)
+    assert want > 0 and abs(got - want) <= 1e-12 * want
+
+
 # ---------------------------------------------------------------------------------------------
 # GEMM (binary64)
 # ---------------------------------------------------------------------------------------------
