@@ -7,6 +7,7 @@
 // order.  Nothing depends on scheduling, so the result is reproducible bit for bit.
 #include <cuda_bf16.h>
 
+#include "exact_sqdiff.h"
 #include "kernels.h"
 
 namespace hda {
@@ -137,50 +138,78 @@ __global__ void __launch_bounds__(256) k_reduce(const RedTask *__restrict__ task
 // row whose y or r does not share x's phase runs scalar.  Each lane folds its elements in a
 // fixed order and the trees are fixed, so the sum is the same on every run of a plan.
 // ------------------------------------------------------------------------------------------
+// 16 bytes of a stored row: V elements, as binary64 values (binary64 storage) or as binary32 bit
+// patterns (binary32 and bfloat16 storage; bfloat16 -> binary32 is exact: the bits move up 16
+// places).
 template <int DT>
 struct Vec16;
 template <>
 struct Vec16<DT_F64> {
     static constexpr int V = 2;
+    using T = double;
     __device__ static void load(const void *p, double *out)
     {
         const double2 v = *reinterpret_cast<const double2 *>(p);
         out[0] = v.x;
         out[1] = v.y;
     }
+    __device__ static double one(const void *p, int c) { return reinterpret_cast<const double *>(p)[c]; }
 };
 template <>
 struct Vec16<DT_F32> {
     static constexpr int V = 4;
-    __device__ static void load(const void *p, double *out)
+    using T = unsigned;
+    __device__ static void load(const void *p, unsigned *out)
     {
         const uint4 v = *reinterpret_cast<const uint4 *>(p);
-        out[0] = f32_bits_to_f64(v.x);
-        out[1] = f32_bits_to_f64(v.y);
-        out[2] = f32_bits_to_f64(v.z);
-        out[3] = f32_bits_to_f64(v.w);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
     }
+    __device__ static unsigned one(const void *p, int c) { return reinterpret_cast<const unsigned *>(p)[c]; }
 };
 template <>
 struct Vec16<DT_BF16> {
     static constexpr int V = 8;
-    __device__ static void load(const void *p, double *out)
+    using T = unsigned;
+    __device__ static void load(const void *p, unsigned *out)
     {
         const uint4 v = *reinterpret_cast<const uint4 *>(p);
         const unsigned w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < 4; k++) {  // bfloat16 -> binary32 is exact: the bits move up 16 places
-            out[2 * k] = f32_bits_to_f64(w[k] << 16);
-            out[2 * k + 1] = f32_bits_to_f64(w[k] & 0xffff0000u);
+        for (int k = 0; k < 4; k++) {
+            out[2 * k] = w[k] << 16;
+            out[2 * k + 1] = w[k] & 0xffff0000u;
         }
     }
+    __device__ static unsigned one(const void *p, int c)
+    {
+        return (unsigned)reinterpret_cast<const unsigned short *>(p)[c] << 16;
+    }
 };
+
+// RN64((x - y)^2) of two stored elements
+__device__ __forceinline__ double sq_of(double a, double b)
+{
+    const double d = a - b;
+    return d * d;
+}
+__device__ __forceinline__ double sq_of(unsigned ux, unsigned uy)
+{
+    uint64_t q;
+    if (sqdiff_f32_bits(ux, uy, q)) return __longlong_as_double((long long)q);  // integer path
+    const double d = f32_bits_to_f64(ux) - f32_bits_to_f64(uy);                 // the rest
+    return d * d;
+}
 
 template <int DT, bool SUM>
 __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks, int ntasks, double *partials,
                                                 unsigned *counter, double *result)
 {
-    constexpr int V = Vec16<DT>::V;
+    using VT = Vec16<DT>;
+    using T = typename VT::T;
+    constexpr int V = VT::V;
     constexpr int ES = 16 / V;  // bytes per stored element of x and y
     __shared__ double wsum[8];
     __shared__ bool last;
@@ -200,8 +229,7 @@ __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks
             const int nv = vec ? (n - head) / V : 0;
             const int vend = vec ? head + nv * V : 0;
             auto scalar = [&](int c) {
-                const double d = ldd<DT>(x, c) - ldd<DT>(y, c);
-                const double q = d * d;
+                const double q = sq_of(VT::one(x, c), VT::one(y, c));
                 r[c] = q;
                 if (SUM) acc += q;
             };
@@ -211,17 +239,16 @@ __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks
             for (int c = vend + lane; c < n; c += 32) scalar(c);
             int v = lane;
             for (; v + 32 < nv; v += 64) {  // two vectors in flight per lane
-                double a0[V], b0[V], a1[V], b1[V];
-                Vec16<DT>::load(x + (head + v * V) * ES, a0);
-                Vec16<DT>::load(y + (head + v * V) * ES, b0);
-                Vec16<DT>::load(x + (head + (v + 32) * V) * ES, a1);
-                Vec16<DT>::load(y + (head + (v + 32) * V) * ES, b1);
+                T a0[V], b0[V], a1[V], b1[V];
+                VT::load(x + (head + v * V) * ES, a0);
+                VT::load(y + (head + v * V) * ES, b0);
+                VT::load(x + (head + (v + 32) * V) * ES, a1);
+                VT::load(y + (head + (v + 32) * V) * ES, b1);
                 double q0[V], q1[V];
 #pragma unroll
                 for (int k = 0; k < V; k++) {
-                    const double d0 = a0[k] - b0[k], d1 = a1[k] - b1[k];
-                    q0[k] = d0 * d0;
-                    q1[k] = d1 * d1;
+                    q0[k] = sq_of(a0[k], b0[k]);
+                    q1[k] = sq_of(a1[k], b1[k]);
                 }
                 double2 *r0 = reinterpret_cast<double2 *>(r + head + v * V);
                 double2 *r1 = reinterpret_cast<double2 *>(r + head + (v + 32) * V);
@@ -238,14 +265,12 @@ __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks
                 }
             }
             for (; v < nv; v += 32) {
-                double a0[V], b0[V], q0[V];
-                Vec16<DT>::load(x + (head + v * V) * ES, a0);
-                Vec16<DT>::load(y + (head + v * V) * ES, b0);
+                T a0[V], b0[V];
+                double q0[V];
+                VT::load(x + (head + v * V) * ES, a0);
+                VT::load(y + (head + v * V) * ES, b0);
 #pragma unroll
-                for (int k = 0; k < V; k++) {
-                    const double d0 = a0[k] - b0[k];
-                    q0[k] = d0 * d0;
-                }
+                for (int k = 0; k < V; k++) q0[k] = sq_of(a0[k], b0[k]);
                 double2 *r0 = reinterpret_cast<double2 *>(r + head + v * V);
 #pragma unroll
                 for (int k = 0; k < V / 2; k++) r0[k] = make_double2(q0[2 * k], q0[2 * k + 1]);
@@ -256,26 +281,27 @@ __global__ void __launch_bounds__(256) k_sqdiff(const PwTask *__restrict__ tasks
             }
         }
     }
-    if (!SUM) return;
+    if (SUM) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) wsum[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = wsum[0];
-        for (int w = 1; w < nw; w++) b += wsum[w];
-        partials[blockIdx.x] = b;
-        __threadfence();
-        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const volatile double *vp = partials;
-        double s = vp[0];
-        for (unsigned b = 1; b < gridDim.x; b++) s += vp[b];
-        *result = s;
-        *counter = 0u;  // ready for the next launch
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) wsum[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = wsum[0];
+            for (int w = 1; w < nw; w++) b += wsum[w];
+            partials[blockIdx.x] = b;
+            __threadfence();
+            last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            const volatile double *vp = partials;
+            double s = vp[0];
+            for (unsigned b = 1; b < gridDim.x; b++) s += vp[b];
+            *result = s;
+            *counter = 0u;  // ready for the next launch
+        }
     }
 }
 
