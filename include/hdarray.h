@@ -356,6 +356,57 @@ typedef void *(*HDArrayAlloc_t)(size_t bytes, void *user);
 typedef void (*HDArrayFree_t)(void *ptr, void *user);
 int HDArraySetAllocator(HDArrayAlloc_t alloc, HDArrayFree_t free_fn, void *user);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Logical devices on several processes (extension).  The paper runs one MPI process per device   */
+/* and every process keeps every process's section sets, so all processes compute the same        */
+/* messages (Sec. 2.1); messages between processes travel by MPI, messages within one by a device */
+/* copy (Sec. 3.1, HDArrayApplyKernel; Sec. 4).  Here each process (a "rank", one GPU each) runs  */
+/* the same calls on the same logical devices with the same replicated bookkeeping, holds device  */
+/* buffers and runs kernels only for the devices mapped to it, and moves a section whose source   */
+/* and destination devices sit on different ranks through a transport the caller supplies.        */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Map logical device d (0 <= d < ndev, ndev = HDArrayNumDevices()) to rank rank_of_dev[d]; this
+ * process is rank my_rank.  rank_of_dev NULL (or ndev 0) restores the single-process form, where
+ * every device is local.  Set it after HDArrayInit and before creating arrays.  With a map:
+ *  - buffers exist, kernels run and Write / Read copy only for this rank's devices;
+ *  - HDArrayReduce folds this rank's devices' regions only (combine the ranks' partial results);
+ *  - every call whose exchange has a cross-rank section calls the transport (below) after its
+ *    bookkeeping and before its kernel, which is then refused inside graph recording
+ *    (HDARRAY_ERR_UNSUPPORTED) and without a transport (HDARRAY_ERR_STATE).
+ * HDARRAY_ERR_INVAL for a bad map. */
+int HDArraySetRankMap(int ndev, const int32_t *rank_of_dev, int my_rank);
+
+/* A cross-rank exchange record: 10 int64, (src device, dst device, src rank, dst rank, lo0, lo1,
+ * lo2, hi0, hi1, hi2), the box in the user's dimension order (unused dimensions lo 0, hi 1). */
+#define HDARRAY_RANK_RECORD 10
+
+/* The transport: called once per array and call with the nrec cross-rank records of that array's
+ * exchange (every rank gets the same records in the same order, sorted by source rank, then
+ * destination rank, then the exchange's own order).  It must, before returning, have delivered
+ * every record whose dst rank is this rank into its device buffer (HDArrayUnpackBoxes) from the
+ * record's src rank, which packs it (HDArrayPackBoxes); the library stream is `stream`.  Returns 0,
+ * or a negative code that the call returns. */
+typedef int (*HDArrayTransport_t)(HDArray_t *hA, int64_t nrec, const int64_t *recs, void *stream, void *user);
+int HDArraySetTransport(HDArrayTransport_t fn, void *user);
+
+/* The cross-rank records (format above, same order as the transport's) of the last call that
+ * moved hA's data; up to cap records written, the count returned (which may exceed cap). */
+int64_t HDArrayGetRankPlan(HDArray_t *hA, int64_t *out, int64_t cap);
+
+/* Staging layout of nrec records (format above): record i's box in row-major order, element type
+ * of hA, starting at the first 16-byte boundary after record i-1.  Returns the total bytes. */
+int64_t HDArrayStagingBytes(HDArray_t *hA, int64_t nrec, const int64_t *recs);
+
+/* Pack: copy each record's box from its src device's buffer (a device of this rank) into the
+ * staging buffer (device memory, or host memory the GPU can address; layout above, `bytes` at
+ * least HDArrayStagingBytes).  Unpack: copy each record's box from staging into its dst device's
+ * buffer (a device of this rank), with no bookkeeping (the call that produced the records did it).
+ * Queued on the library stream.  HDARRAY_ERR_INVAL if a device is not local, HDARRAY_ERR_RANGE if a
+ * box lies outside the device's buffer or staging is too small. */
+int HDArrayPackBoxes(HDArray_t *hA, int64_t nrec, const int64_t *recs, void *staging, int64_t bytes);
+int HDArrayUnpackBoxes(HDArray_t *hA, int64_t nrec, const int64_t *recs, const void *staging, int64_t bytes);
+
 /* Counters since HDArrayInit: [0] kernel launches issued by the library, [1] section bytes
  * moved between device buffers, [2] plans computed (cache misses), [3] plan cache hits,
  * [4] graph launches.  n values are written (n <= 5). */

@@ -111,6 +111,11 @@ struct Ctx {
     struct Shape { int variant, rows, warps, tile_z, fuse, variant3, band3, cta3, band2; };
     std::map<std::string, Shape> tuned;
     bool tune_file_loaded = false;  // HDARRAY_TUNE_CACHE read into `tuned` (once per HDArrayInit)
+    // logical devices on several ranks (empty map: every device is local)
+    std::vector<int> rank_of_dev;
+    int my_rank = 0;
+    HDArrayTransport_t transport = nullptr;
+    void *transport_user = nullptr;
     // counters
     int64_t counters[5] = {0, 0, 0, 0, 0};
     int last_error = 0;
@@ -135,6 +140,10 @@ int set_err(int code)
     } while (0)
 
 bool trace() { return getenv("HDARRAY_TRACE") != nullptr; }
+
+// Is logical device p mapped to this rank?
+bool is_local(int p) { return g->rank_of_dev.empty() || g->rank_of_dev[p] == g->my_rank; }
+int rank_of(int p) { return g->rank_of_dev.empty() ? 0 : g->rank_of_dev[p]; }
 
 int dtype_of(const char *t, int *esize)
 {
@@ -510,6 +519,44 @@ int copy_box_d2d(const HDArray *a, const DevBuf &src, const DevBuf &dst, const B
 // come from their last writers.  SEND_{q,p} = sGDEF_{q,p} n LUSE_p = own[q] n stale[p] n LUSE_p
 // (Eq. 1); RECV_{p,q} = SEND_{q,p} (Eq. 2).  Afterwards p holds all of LUSE_p (the subtraction of
 // Eq. 3-4).
+// The cross-rank moves of an exchange as transport records (HDARRAY_RANK_RECORD int64 each), sorted
+// by source rank, then destination rank, then the exchange's order: every rank derives the same list
+// from its replicated bookkeeping.
+void rank_records(const HDArray *a, const std::vector<Move> &moves, std::vector<int64_t> &out)
+{
+    out.clear();
+    if (g->rank_of_dev.empty()) return;
+    std::vector<size_t> idx;
+    for (size_t i = 0; i < moves.size(); i++)
+        if (rank_of(moves[i].src) != rank_of(moves[i].dst)) idx.push_back(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+        const int sx = rank_of(moves[x].src), sy = rank_of(moves[y].src);
+        if (sx != sy) return sx < sy;
+        return rank_of(moves[x].dst) < rank_of(moves[y].dst);
+    });
+    for (size_t i : idx) {
+        const Move &m = moves[i];
+        out.push_back(m.src);
+        out.push_back(m.dst);
+        out.push_back(rank_of(m.src));
+        out.push_back(rank_of(m.dst));
+        for (int d = 0; d < 3; d++) out.push_back(d < a->dim ? m.box.lo[d] : 0);
+        for (int d = 0; d < 3; d++) out.push_back(d < a->dim ? m.box.hi[d] : 1);
+    }
+}
+
+// Hand an exchange's cross-rank moves to the transport (nothing to do without any).
+int run_transport(HDArray *a, const std::vector<Move> &moves)
+{
+    std::vector<int64_t> recs;
+    rank_records(a, moves, recs);
+    if (recs.empty()) return HDARRAY_OK;
+    if (g->recording) return HDARRAY_ERR_UNSUPPORTED;
+    if (!g->transport) return HDARRAY_ERR_STATE;
+    return g->transport(a, (int64_t)(recs.size() / HDARRAY_RANK_RECORD), recs.data(), (void *)g->stream,
+                        g->transport_user);
+}
+
 int use_step(GState &s, const std::vector<BoxSet> &luse, std::vector<Move> &moves)
 {
     const int P = (int)s.own.size();
@@ -941,7 +988,16 @@ int compile_plan(Plan &pl)
     pl.fused = false;
     pl.tables.reset();
     const KernelDef &k = *pl.k;
-    const Part &pt = g->parts[pl.part];
+    // with devices on several ranks this rank compiles its own devices' work (the others' boxes
+    // empty) and the moves between its own devices; cross-rank moves arrive through the transport
+    Part local_part;
+    if (!g->rank_of_dev.empty()) {
+        local_part = g->parts[pl.part];
+        for (int p = 0; p < local_part.nparts; p++)
+            if (!is_local(p)) local_part.box[p] = Box{};
+    }
+    const Part &pt = g->rank_of_dev.empty() ? g->parts[pl.part] : local_part;
+    auto local_move = [](const Move &m) { return is_local(m.src) && is_local(m.dst); };
     const bool plain = g->mode == HDARRAY_MODE_PLAIN;
     std::vector<std::pair<const void *, size_t>> blobs;
 
@@ -950,6 +1006,7 @@ int compile_plan(Plan &pl)
     std::vector<std::pair<int, int>> xfer_groups;  // [begin, end) per move
     auto add_moves = [&](const ArrStep &st) {
         for (const Move &m : st.moves) {
+            if (!local_move(m)) continue;
             int b = (int)xfer.size();
             copy_tasks(st.a, st.a->buf[m.src], st.a->buf[m.dst], m.box, xfer);
             xfer_groups.push_back({b, (int)xfer.size()});
@@ -983,7 +1040,7 @@ int compile_plan(Plan &pl)
             std::vector<Move> recv;
             if (sx)
                 for (const Move &m : sx->moves)
-                    if (m.dst == p) recv.push_back(m);
+                    if (m.dst == p && local_move(m)) recv.push_back(m);
             int t0 = (int)h.tiles.size();
             const bool flat = !conv && g->variant == 2 && X->dtype != DT_BF16;
             h.flat = flat;
@@ -1074,7 +1131,7 @@ int compile_plan(Plan &pl)
             std::vector<Move> recv;
             if (sx)
                 for (const Move &m : sx->moves)
-                    if (m.dst == p) recv.push_back(m);
+                    if (m.dst == p && local_move(m)) recv.push_back(m);
             int t0 = (int)h.tiles.size();
             const bool flat = g->variant3 == 2 && X->dtype != DT_BF16;
             h.flat = flat;
@@ -1872,6 +1929,7 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
     if (!g->host_only) {
         for (size_t i = 0; i < args.size(); i++) {
             for (int p = 0; p < pt.nparts; p++) {
+                if (!is_local(p)) continue;  // another rank's device: no buffer here
                 Box need = box_hull(set_bbox(pl->luse[i][p]), set_bbox(pl->ldef[i][p]));
                 if (need.empty()) continue;
                 if (g->batching && !(args[i]->buf[p].ptr && box_contains(args[i]->buf[p].alloc, need))) {
@@ -1898,6 +1956,10 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
         if (st.defined) st.a->version++;
         if (st.used) st.a->last_moves = st.moves;
         for (const Move &m : st.moves) g->counters[1] += m.box.volume() * st.a->esize;
+    }
+    for (const ArrStep &st : pl->steps) {  // sections that cross ranks arrive before the kernel
+        rc = run_transport(st.a, st.moves);
+        if (rc) return rc;
     }
     if (g->batching) {
         g->batch.push_back(pl);
@@ -2088,11 +2150,13 @@ int use_regions(HDArray *a, const Part &pt)
     if (rc) return rc;
     if (!g->host_only) {
         for (int p = 0; p < pt.nparts; p++) {
+            if (!is_local(p)) continue;
             rc = ensure_buffer(a, p, pt.box[p]);
             if (rc) return rc;
         }
         std::vector<CopyTask> tasks;
-        for (const Move &m : moves) copy_tasks(a, a->buf[m.src], a->buf[m.dst], m.box, tasks);
+        for (const Move &m : moves)
+            if (is_local(m.src) && is_local(m.dst)) copy_tasks(a, a->buf[m.src], a->buf[m.dst], m.box, tasks);
         if (!tasks.empty()) {
             std::shared_ptr<DevMem> mem;
             std::vector<const char *> addr;
@@ -2104,6 +2168,8 @@ int use_regions(HDArray *a, const Part &pt)
             CUDA_TRY(cudaStreamSynchronize(g->stream));  // the tables are freed on return
         }
     }
+    rc = run_transport(a, moves);
+    if (rc) return rc;
     for (const Move &m : moves) g->counters[1] += m.box.volume() * a->esize;
     a->cur = intern(a, std::move(s));
     a->last_moves = moves;
@@ -2131,7 +2197,7 @@ int write_impl(HDArray *a, const void *uA, int part)
     if (rc) return rc;
     if (!g->host_only && uA) {
         for (int p = 0; p < pt.nparts; p++) {
-            if (pt.box[p].empty()) continue;
+            if (pt.box[p].empty() || !is_local(p)) continue;
             rc = ensure_buffer(a, p, pt.box[p]);
             if (rc) return rc;
             rc = memcpy_box(a, a->buf[p], pt.box[p], const_cast<void *>(uA), true);
@@ -2159,7 +2225,7 @@ int read_impl(HDArray *a, void *uA, int part)
     if (rc) return rc;
     if (!g->host_only && uA) {
         for (int p = 0; p < pt.nparts; p++) {
-            if (pt.box[p].empty()) continue;
+            if (pt.box[p].empty() || !is_local(p)) continue;
             rc = memcpy_box(a, a->buf[p], pt.box[p], uA, false);
             if (rc) return rc;
         }
@@ -2237,7 +2303,7 @@ int reduce_impl(HDArray *a, double *res, int op, int part)
         std::vector<RedTask> tasks;
         for (int p = 0; p < pt.nparts; p++) {
             const Box &W = pt.box[p];
-            if (W.empty()) continue;
+            if (W.empty() || !is_local(p)) continue;  // another rank folds its own devices
             const DevBuf &b = a->buf[p];
             View3 v = view_of(a, b, W);
             RedTask t;
@@ -3176,6 +3242,126 @@ static void to_user(const Box &b, int64_t *out)
         out[d] = b.lo[d];
         out[3 + d] = b.hi[d];
     }
+}
+
+int HDArraySetRankMap(int ndev, const int32_t *rank_of_dev, int my_rank)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    if (!g->arrays.empty()) return HDARRAY_ERR_STATE;  // buffers are placed when arrays are used
+    if (!rank_of_dev || ndev == 0) {
+        g->rank_of_dev.clear();
+        g->my_rank = 0;
+        return HDARRAY_OK;
+    }
+    if (ndev != g->ndev || my_rank < 0) return HDARRAY_ERR_INVAL;
+    for (int d = 0; d < ndev; d++)
+        if (rank_of_dev[d] < 0) return HDARRAY_ERR_INVAL;
+    g->rank_of_dev.assign(rank_of_dev, rank_of_dev + ndev);
+    g->my_rank = my_rank;
+    g->memo.clear();  // plans compiled for another placement
+    return HDARRAY_OK;
+}
+
+int HDArraySetTransport(HDArrayTransport_t fn, void *user)
+{
+    if (!g || !g->inited) return HDARRAY_ERR_STATE;
+    g->transport = fn;
+    g->transport_user = user;
+    return HDARRAY_OK;
+}
+
+int64_t HDArrayGetRankPlan(HDArray_t *hA, int64_t *out, int64_t cap)
+{
+    if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
+    std::vector<int64_t> recs;
+    rank_records(hA, hA->last_moves, recs);
+    const int64_t n = (int64_t)(recs.size() / HDARRAY_RANK_RECORD);
+    if (out)
+        for (int64_t i = 0; i < n && i < cap; i++)
+            memcpy(out + HDARRAY_RANK_RECORD * i, recs.data() + HDARRAY_RANK_RECORD * i,
+                   sizeof(int64_t) * HDARRAY_RANK_RECORD);
+    return n;
+}
+
+// Boxes and 16-byte aligned staging offsets of transport records; the total bytes, or < 0.
+static int64_t staging_layout(const HDArray *a, int64_t nrec, const int64_t *recs, std::vector<Box> &boxes,
+                              std::vector<int64_t> &offs)
+{
+    if (nrec < 0 || (nrec > 0 && !recs)) return HDARRAY_ERR_INVAL;
+    int64_t total = 0;
+    for (int64_t i = 0; i < nrec; i++) {
+        const int64_t *r = recs + HDARRAY_RANK_RECORD * i;
+        if (r[0] < 0 || r[0] >= g->ndev || r[1] < 0 || r[1] >= g->ndev) return HDARRAY_ERR_INVAL;
+        Box b;
+        for (int d = 0; d < 3; d++) {
+            b.lo[d] = r[4 + d];
+            b.hi[d] = r[7 + d];
+            const int64_t n = d < a->dim ? a->n[d] : 1;
+            if (b.lo[d] < 0 || b.hi[d] > n || b.hi[d] <= b.lo[d]) return HDARRAY_ERR_RANGE;
+        }
+        total = (total + 15) / 16 * 16;
+        offs.push_back(total);
+        boxes.push_back(b);
+        total += b.volume() * a->esize;
+    }
+    return total;
+}
+
+int64_t HDArrayStagingBytes(HDArray_t *hA, int64_t nrec, const int64_t *recs)
+{
+    if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
+    std::vector<Box> boxes;
+    std::vector<int64_t> offs;
+    return staging_layout(hA, nrec, recs, boxes, offs);
+}
+
+// Copy the records' boxes between the local devices' buffers and the staging buffer.
+static int pack_unpack(HDArray *a, int64_t nrec, const int64_t *recs, char *staging, int64_t bytes, bool pack)
+{
+    if (!g || !g->inited || !a || !g->arrays.count(a)) return HDARRAY_ERR_INVAL;
+    if (g->host_only) return HDARRAY_ERR_UNSUPPORTED;
+    if (g->recording) return HDARRAY_ERR_STATE;
+    std::vector<Box> boxes;
+    std::vector<int64_t> offs;
+    const int64_t total = staging_layout(a, nrec, recs, boxes, offs);
+    if (total < 0) return (int)total;
+    if (nrec == 0) return HDARRAY_OK;
+    if (!staging || bytes < total) return HDARRAY_ERR_RANGE;
+    std::vector<CopyTask> tasks;
+    for (int64_t i = 0; i < nrec; i++) {
+        const int dev = (int)recs[HDARRAY_RANK_RECORD * i + (pack ? 0 : 1)];
+        if (!is_local(dev)) return HDARRAY_ERR_INVAL;
+        const DevBuf &b = a->buf[dev];
+        if (!b.ptr || !box_contains(b.alloc, boxes[i])) return HDARRAY_ERR_RANGE;
+        DevBuf st;  // the record's stretch of staging, seen as a dense buffer over its box
+        st.alloc = boxes[i];
+        set_strides(a, st);
+        st.ptr = staging + offs[i];
+        if (pack) copy_tasks(a, b, st, boxes[i], tasks);
+        else copy_tasks(a, st, b, boxes[i], tasks);
+    }
+    std::shared_ptr<DevMem> mem;
+    std::vector<const char *> addr;
+    int rc = upload({{tasks.data(), tasks.size() * sizeof(CopyTask)}}, mem, addr);
+    if (rc) return rc;
+    LaunchRec L;
+    L.kind = L_COPY;
+    L.p0 = addr[0];
+    L.n0 = (int64_t)tasks.size();
+    rc = issue_recorded(L);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(g->stream));  // the task table is freed on return
+    return HDARRAY_OK;
+}
+
+int HDArrayPackBoxes(HDArray_t *hA, int64_t nrec, const int64_t *recs, void *staging, int64_t bytes)
+{
+    return pack_unpack(hA, nrec, recs, (char *)staging, bytes, true);
+}
+
+int HDArrayUnpackBoxes(HDArray_t *hA, int64_t nrec, const int64_t *recs, const void *staging, int64_t bytes)
+{
+    return pack_unpack(hA, nrec, recs, (char *)const_cast<void *>(staging), bytes, false);
 }
 
 int64_t HDArrayGetPlan(HDArray_t *hA, int64_t *out, int64_t cap)

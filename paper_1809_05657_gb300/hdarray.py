@@ -89,7 +89,15 @@ SIGNATURES = {
                                                   ctypes.c_int, _P, _P]),
     "HDArrayRegisterKernel": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     "HDArraySetAllocator": (ctypes.c_int, [_P, _P, _P]),
+    "HDArraySetRankMap": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]),
+    "HDArraySetTransport": (ctypes.c_int, [_P, _P]),
+    "HDArrayGetRankPlan": (ctypes.c_int64, [_P, _I64P, ctypes.c_int64]),
+    "HDArrayStagingBytes": (ctypes.c_int64, [_P, ctypes.c_int64, _I64P]),
+    "HDArrayPackBoxes": (ctypes.c_int, [_P, ctypes.c_int64, _I64P, _P, ctypes.c_int64]),
+    "HDArrayUnpackBoxes": (ctypes.c_int, [_P, ctypes.c_int64, _I64P, _P, ctypes.c_int64]),
 }
+
+HDARRAY_RANK_RECORD = 10
 
 HDARRAY_MAX_KERNEL_ARRAYS = 8
 
@@ -105,6 +113,8 @@ class HDArrayWork(ctypes.Structure):
 
 LAUNCHER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(HDArrayWork), ctypes.c_int,
                             ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+TRANSPORT = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.c_void_p, ctypes.c_void_p)
 ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _keep = {}  # C callbacks must outlive their registration
@@ -182,10 +192,14 @@ def HDArrayInit(argv=None, kpath=None, dpath=None, ndev=None, host_only=False):
 
 def HDArrayExit():
     lib().HDArrayExit()
+    _arrays.clear()
 
 
 def HDArrayShowDeviceInfo(dev=0):
     lib().HDArrayShowDeviceInfo(dev)
+
+
+_arrays = {}  # handle -> HDArray, for callbacks that receive a handle
 
 
 def HDArrayCreate(sym, dtype, uA, *sizes):
@@ -193,11 +207,14 @@ def HDArrayCreate(sym, dtype, uA, *sizes):
     h = lib().HDArrayCreatev(sym.encode(), dtype.encode(), _ptr(uA), len(sizes), sp)
     if not h:
         raise HDArrayError(lib().HDArrayGetLastError(), "HDArrayCreate")
-    return HDArray(h, sym, dtype, sizes)
+    a = HDArray(h, sym, dtype, sizes)
+    _arrays[h] = a
+    return a
 
 
 def HDArrayFree(h):
     _chk(lib().HDArrayFree(h), "HDArrayFree")
+    _arrays.pop(h.handle if isinstance(h, HDArray) else h, None)
 
 
 def HDArrayPartition(ptype, sizes, lo, hi, nparts=0):
@@ -374,6 +391,60 @@ def HDArrayGetPlan(h):
         r = buf[8 * i: 8 * i + 8]
         out.append((int(r[0]), int(r[1]), tuple(int(v) for v in r[2:5]), tuple(int(v) for v in r[5:8])))
     return out
+
+
+def HDArraySetRankMap(rank_of_dev, my_rank):
+    """Logical device d lives on rank rank_of_dev[d]; this process is my_rank.  None: one process."""
+    if rank_of_dev is None:
+        return _chk(lib().HDArraySetRankMap(0, None, 0), "HDArraySetRankMap")
+    r = np.ascontiguousarray(np.asarray(rank_of_dev, dtype=np.int32))
+    return _chk(lib().HDArraySetRankMap(len(r), r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), my_rank),
+                "HDArraySetRankMap")
+
+
+def HDArraySetTransport(fn):
+    """fn(array, records, stream) -> int: deliver the cross-rank records (an int64 array of shape
+    (n, HDARRAY_RANK_RECORD)) of `array`'s exchange; None removes it."""
+    if fn is None:
+        _keep.pop("transport", None)
+        return _chk(lib().HDArraySetTransport(None, None), "HDArraySetTransport")
+
+    def thunk(h, n, recs, stream, user):
+        try:
+            r = np.ctypeslib.as_array(recs, shape=(n * HDARRAY_RANK_RECORD,)).reshape(n, HDARRAY_RANK_RECORD).copy()
+            return int(fn(_arrays.get(h) or HDArray(h, "?", "?", ()), r, stream or 0) or 0)
+        except Exception:
+            import traceback
+            traceback.print_exc()
+            return -6
+    cb = TRANSPORT(thunk)
+    _keep["transport"] = cb
+    return _chk(lib().HDArraySetTransport(ctypes.cast(cb, _P), None), "HDArraySetTransport")
+
+
+def HDArrayGetRankPlan(h):
+    """Cross-rank records of the last call that moved h: int64 array (n, HDARRAY_RANK_RECORD)."""
+    n = _chk(lib().HDArrayGetRankPlan(h, None, 0), "HDArrayGetRankPlan")
+    buf = np.zeros(max(1, n) * HDARRAY_RANK_RECORD, np.int64)
+    _chk(lib().HDArrayGetRankPlan(h, buf.ctypes.data_as(_I64P), n), "HDArrayGetRankPlan")
+    return buf[: n * HDARRAY_RANK_RECORD].reshape(n, HDARRAY_RANK_RECORD)
+
+
+def HDArrayStagingBytes(h, recs):
+    r, rp = _i64(recs)
+    return _chk(lib().HDArrayStagingBytes(h, len(r) // HDARRAY_RANK_RECORD, rp), "HDArrayStagingBytes")
+
+
+def HDArrayPackBoxes(h, recs, staging, nbytes):
+    r, rp = _i64(recs)
+    return _chk(lib().HDArrayPackBoxes(h, len(r) // HDARRAY_RANK_RECORD, rp, _ptr(staging), nbytes),
+                "HDArrayPackBoxes")
+
+
+def HDArrayUnpackBoxes(h, recs, staging, nbytes):
+    r, rp = _i64(recs)
+    return _chk(lib().HDArrayUnpackBoxes(h, len(r) // HDARRAY_RANK_RECORD, rp, _ptr(staging), nbytes),
+                "HDArrayUnpackBoxes")
 
 
 def HDArrayGetGDEF(h, p, q):
