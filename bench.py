@@ -814,8 +814,10 @@ def workload_small(H, torch, stream, args):
     then the copy back), one launch per device and kernel, no graph.  Fused form: the step alone
     with the arrays' roles swapped every iteration (the same values and messages), one launch per
     iteration, the 10 iterations replayed as a CUDA graph.  Both end with the residual of the last
-    iteration, sum((new - old)^2), and must agree bit for bit; the final field and residual are
-    checked against a numpy binary64 evaluation of the same number of iterations."""
+    iteration, sum((new - old)^2), folded in different orders (a separate reduction launch in the
+    plain form, the residual launch's own fold in the fused form), so they agree to the reduction
+    bound; the final field (bit for bit) and the residual are checked against a numpy binary64
+    evaluation of the same number of iterations."""
     import numpy as np
     import synthetic
     N, P, iters = 256, 4, 10
@@ -891,7 +893,8 @@ def workload_small(H, torch, stream, args):
                         "step and copy kernels; fused: the step with roles swapped, in a graph)",
             "metric": UNIT, "value": cells * iters / (best["ms_per_step"] * 1e-3) / 1e9, "unit": UNIT,
             "dtype": "f64", "steps": steps, "ms_per_step": best["ms_per_step"], "forms": out,
-            "parity": {"residuals_equal_plain_fused": out["plain"]["residual"] == out["fused"]["residual"],
+            "parity": {"residual_rel_diff_plain_fused": abs(out["plain"]["residual"] - out["fused"]["residual"])
+                                                        / abs(out["fused"]["residual"]),
                        "field_bit_exact_vs_numpy_binary64": bool(np.array_equal(got, field)),
                        "residual_rel_err_vs_numpy": abs(best["residual"] - res_ref) / abs(res_ref),
                        "iterations": field_iters},
