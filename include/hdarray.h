@@ -134,7 +134,12 @@ void HDArrayRead(HDArray_t *hA, void *uA, int partID);
 /* HDArrayWrite (Table 2): copy every logical device's region of partition partID from the user
  * array uA (full-size, row-major) into that device's buffer.  This is a definition by each
  * device of its region (it becomes the owner; other copies become stale).  Overlapping regions
- * are a race.  Asynchronous for device pointers; waits for a host pointer to be read. */
+ * are a race.  From pinned (page-locked) host memory into buffers that already cover the regions,
+ * the copies run on the library's own copy stream, after the library's last work on hA and
+ * alongside its work on other arrays; everything the library later does with hA waits for them.
+ * Keep uA unchanged until a synchronising call (Read, Reduce, Sync) has returned.  From pageable
+ * host memory the call returns once uA has been read; device pointers are copied on the library
+ * stream.  HDARRAY_ASYNC_WRITE=0 puts every copy on the library stream. */
 void HDArrayWrite(HDArray_t *hA, void *uA, int partID);
 
 /* HDArrayReduce (Table 2): reduce the regions of partition partID (each element once) to one

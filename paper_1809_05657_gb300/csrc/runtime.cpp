@@ -41,6 +41,8 @@ struct Ctx {
     int ndev = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // asynchronous Write from host memory
+    bool async_write = true;             // HDARRAY_ASYNC_WRITE=0: every Write on the library stream
     int mode = HDARRAY_MODE_FUSED;
     int nsm = 148;
     std::map<std::string, KernelDef> kernels;
@@ -144,6 +146,31 @@ bool trace() { return getenv("HDARRAY_TRACE") != nullptr; }
 // Is logical device p mapped to this rank?
 bool is_local(int p) { return g->rank_of_dev.empty() || g->rank_of_dev[p] == g->my_rank; }
 int rank_of(int p) { return g->rank_of_dev.empty() ? 0 : g->rank_of_dev[p]; }
+
+#define CUDA_OK(x)                           \
+    do {                                     \
+        if ((x) != cudaSuccess) {            \
+            cudaGetLastError();              \
+            return HDARRAY_ERR_CUDA;         \
+        }                                    \
+    } while (0)
+
+// Library-stream work on a's buffers waits for an asynchronous Write of a still in flight.
+int join_write(HDArray *a)
+{
+    if (!a->write_pending) return HDARRAY_OK;
+    CUDA_OK(cudaStreamWaitEvent(g->stream, a->write_ev, 0));
+    a->write_pending = false;
+    return HDARRAY_OK;
+}
+
+// The library stream's work on a so far: the next asynchronous Write of a waits for it.
+int note_use(HDArray *a)
+{
+    if (!a->track_use || g->host_only) return HDARRAY_OK;
+    CUDA_OK(cudaEventRecord(a->use_ev, g->stream));
+    return HDARRAY_OK;
+}
 
 int dtype_of(const char *t, int *esize)
 {
@@ -1845,6 +1872,11 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
     int rc = validate_args(k, pt, args);
     if (rc) return rc;
     for (HDArray *a : args) grow_devices(a, pt.nparts);
+    if (!g->host_only)
+        for (HDArray *a : args) {
+            rc = join_write(a);
+            if (rc) return rc;
+        }
 
     std::vector<uint64_t> absv(args.size(), 0);
     std::vector<const Ctx::AbsSpec *> abss(args.size(), nullptr);
@@ -1967,6 +1999,10 @@ int apply(const char *kname, int part, const std::vector<HDArray *> &args, const
     }
     rc = run_plan(pl);
     if (rc) return rc;
+    for (const ArrStep &st : pl->steps) {
+        rc = note_use(st.a);
+        if (rc) return rc;
+    }
     if (k.kind == K_SQDIFF && pl->red && !g->host_only) {
         // the launch left the sum of R's new values over the work boxes in the plan's scratch
         for (const LaunchRec &L : pl->launches) {
@@ -2077,6 +2113,11 @@ int flush_batch()
         g->rec_mems.push_back(it->second.first);
         for (auto &p : plans) g->rec_refs.push_back(p);
     }
+    for (auto &p : plans)
+        for (const ArrStep &st : p->steps) {
+            int rc = note_use(st.a);
+            if (rc) return rc;
+        }
     return HDARRAY_OK;
 }
 
@@ -2141,6 +2182,10 @@ int memcpy_box(const HDArray *a, const DevBuf &b, const Box &bx, void *user, boo
 int use_regions(HDArray *a, const Part &pt)
 {
     grow_devices(a, pt.nparts);
+    if (!g->host_only) {
+        int jrc = join_write(a);
+        if (jrc) return jrc;
+    }
     std::vector<BoxSet> U(pt.nparts);
     for (int p = 0; p < pt.nparts; p++)
         if (!pt.box[p].empty()) U[p] = BoxSet{pt.box[p]};
@@ -2195,7 +2240,41 @@ int write_impl(HDArray *a, const void *uA, int part)
     GState s = a->states[a->cur];
     rc = def_step(s, D);
     if (rc) return rc;
-    if (!g->host_only && uA) {
+    // From pinned host memory into buffers that already cover the regions: the copies run on the
+    // library's copy stream after the library's last work on this array, so they overlap work on
+    // other arrays; every later use of the array waits for them.
+    bool async = false;
+    if (!g->host_only && uA && g->async_write && !g->recording) {
+        cudaPointerAttributes attr;
+        async = cudaPointerGetAttributes(&attr, uA) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        for (int p = 0; async && p < pt.nparts; p++)
+            if (!pt.box[p].empty() && is_local(p))
+                async = a->buf[p].ptr && box_contains(a->buf[p].alloc, pt.box[p]);
+    }
+    if (async) {
+        if (!g->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+        if (!a->write_ev) CUDA_TRY(cudaEventCreateWithFlags(&a->write_ev, cudaEventDisableTiming));
+        if (!a->use_ev) CUDA_TRY(cudaEventCreateWithFlags(&a->use_ev, cudaEventDisableTiming));
+        if (!a->track_use) {  // no use recorded yet: everything queued so far
+            CUDA_TRY(cudaEventRecord(a->use_ev, g->stream));
+            a->track_use = true;
+        }
+        CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, a->use_ev, 0));
+        if (a->write_pending) CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, a->write_ev, 0));
+        cudaStream_t lib_stream = g->stream;
+        g->stream = g->copy_stream;  // memcpy_box queues on g->stream
+        for (int p = 0; p < pt.nparts && !rc; p++) {
+            if (pt.box[p].empty() || !is_local(p)) continue;
+            rc = memcpy_box(a, a->buf[p], pt.box[p], const_cast<void *>(uA), true);
+        }
+        g->stream = lib_stream;
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(a->write_ev, g->copy_stream));
+        a->write_pending = true;
+    } else if (!g->host_only && uA) {
+        rc = join_write(a);
+        if (rc) return rc;
         for (int p = 0; p < pt.nparts; p++) {
             if (pt.box[p].empty() || !is_local(p)) continue;
             rc = ensure_buffer(a, p, pt.box[p]);
@@ -2203,6 +2282,8 @@ int write_impl(HDArray *a, const void *uA, int part)
             rc = memcpy_box(a, a->buf[p], pt.box[p], const_cast<void *>(uA), true);
             if (rc) return rc;
         }
+        rc = note_use(a);
+        if (rc) return rc;
     }
     a->cur = intern(a, std::move(s));
     a->version++;
@@ -2439,9 +2520,14 @@ int abs_trap(const char *kname, int part, HDArray *a, int dev, const int64_t *c,
 
 void free_array_buffers(HDArray *a)
 {
+    if (a->write_ev) cudaEventSynchronize(a->write_ev);
     for (DevBuf &b : a->buf)
         if (b.ptr) dev_free(b.ptr);
     a->buf.clear();
+    if (a->write_ev) cudaEventDestroy(a->write_ev);
+    if (a->use_ev) cudaEventDestroy(a->use_ev);
+    a->write_ev = a->use_ev = nullptr;
+    a->write_pending = a->track_use = false;
 }
 
 void drop_plans_of(HDArray *a)
@@ -2507,6 +2593,8 @@ int init_impl(int ndev, unsigned flags)
         if (b2 && atoi(b2) > 0) g->band2 = atoi(b2);
         const char *at = getenv("HDARRAY_AUTOTUNE");
         g->autotune = at && atoi(at) != 0;
+        const char *aw = getenv("HDARRAY_ASYNC_WRITE");
+        if (aw) g->async_write = atoi(aw) != 0;
         const char *fx = getenv("HDARRAY_FUSE_EXCHANGE");
         if (fx) g->fuse = atoi(fx) != 0;
         const char *v3 = getenv("HDARRAY_STENCIL3D_VARIANT");
@@ -2678,6 +2766,7 @@ int HDArrayInit(int argc, char *argv[], const char *kpath, const char *dpath)
 void HDArrayExit(void)
 {
     if (!g) return;
+    if (g->copy_stream) cudaStreamSynchronize(g->copy_stream);
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (auto &kv : g->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -2700,6 +2789,7 @@ void HDArrayExit(void)
     if (g->red_counter) cudaFree(g->red_counter);
     if (g->host_result) cudaFreeHost(g->host_result);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
     g = nullptr;
 }
@@ -2768,6 +2858,7 @@ HDArray_t *HDArrayCreate(const char *sym, const char *type, void *uA, int dim, .
 int HDArrayFree(HDArray_t *hA)
 {
     if (!g || !hA || !g->arrays.count(hA)) return HDARRAY_ERR_INVAL;
+    if (g->copy_stream) cudaStreamSynchronize(g->copy_stream);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->sq_sum.R == hA) g->sq_sum = Ctx::SqSum();
     for (auto it = g->red_plans.begin(); it != g->red_plans.end();) {
@@ -3182,9 +3273,17 @@ int HDArrayGraphLaunch(int graphID, int nrep)
             return set_err(HDARRAY_ERR_STATE);
         if (nrep > 1 && ai.pre != ai.post) return set_err(HDARRAY_ERR_STATE);
     }
+    for (auto &ai : gr.arrays) {
+        const int rc = join_write(ai.a);
+        if (rc) return set_err(rc);
+    }
     for (int r = 0; r < nrep; r++) CUDA_TRY(cudaGraphLaunch(gr.exec, g->stream));
     if (nrep > 0) {
-        for (auto &ai : gr.arrays) ai.a->cur = ai.post;
+        for (auto &ai : gr.arrays) {
+            ai.a->cur = ai.post;
+            const int rc = note_use(ai.a);
+            if (rc) return set_err(rc);
+        }
         for (HDArray *a : gr.defined) a->version += (uint64_t)nrep;  // their contents changed
     }
     g->counters[0] += gr.nkernels * nrep;
@@ -3208,6 +3307,7 @@ int HDArraySync(void)
 {
     if (!g || !g->inited) return HDARRAY_ERR_STATE;
     if (g->host_only) return HDARRAY_OK;
+    if (g->copy_stream) CUDA_TRY(cudaStreamSynchronize(g->copy_stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
     return check_device_error();
 }
@@ -3327,6 +3427,8 @@ static int pack_unpack(HDArray *a, int64_t nrec, const int64_t *recs, char *stag
     if (total < 0) return (int)total;
     if (nrec == 0) return HDARRAY_OK;
     if (!staging || bytes < total) return HDARRAY_ERR_RANGE;
+    int jrc = join_write(a);
+    if (jrc) return jrc;
     std::vector<CopyTask> tasks;
     for (int64_t i = 0; i < nrec; i++) {
         const int dev = (int)recs[HDARRAY_RANK_RECORD * i + (pack ? 0 : 1)];
@@ -3390,6 +3492,13 @@ int HDArrayGetDeviceBuffer(HDArray_t *hA, int dev, void **ptr, int64_t *lo, int6
 {
     if (!g || !hA || !g->arrays.count(hA) || dev < 0 || !ptr) return HDARRAY_ERR_INVAL;
     *ptr = nullptr;
+    if (hA->write_pending) {  // the caller may read the memory at once
+        if (cudaEventSynchronize(hA->write_ev) != cudaSuccess) {
+            cudaGetLastError();
+            return HDARRAY_ERR_CUDA;
+        }
+        hA->write_pending = false;
+    }
     if (dev >= (int)hA->buf.size()) return HDARRAY_OK;
     const DevBuf &b = hA->buf[dev];
     *ptr = b.ptr;
@@ -3415,6 +3524,8 @@ int HDArrayReadDeviceBuffer(HDArray_t *hA, int dev, const int64_t *lo, const int
     }
     if (bx.empty()) return HDARRAY_OK;
     if (!box_contains(b.alloc, bx)) return HDARRAY_ERR_RANGE;
+    const int jrc = join_write(hA);
+    if (jrc) return jrc;
     // view `out` as a dense array shaped like the box: a one-box "user array"
     HDArray tmp;
     tmp.dim = hA->dim;

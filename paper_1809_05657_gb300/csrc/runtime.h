@@ -175,4 +175,9 @@ struct HDArray {
     uint64_t version = 0;     // bumps whenever any element is (re)defined
     uint64_t uid = 0;
     std::vector<hda::Move> last_moves;
+    // asynchronous Write from host memory (on the library's copy stream): write_ev marks its end,
+    // which library work on the array waits for; use_ev marks the end of the library stream's last
+    // work on the array, which the next asynchronous Write waits for (recorded once track_use is set)
+    cudaEvent_t write_ev = nullptr, use_ev = nullptr;
+    bool write_pending = false, track_use = false;
 };

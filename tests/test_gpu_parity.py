@@ -310,6 +310,53 @@ def test_residual_sum_follows_graph_replays(gpu_lib):
     assert want > 0 and abs(got - want) <= 1e-12 * want
 
 
+@pytest.mark.parametrize("async_write", ["1", "0"])
+def test_write_from_pinned_memory_is_ordered(gpu_lib, monkeypatch, async_write):
+    """HDArrayWrite from pinned host memory into existing buffers runs on the library's copy
+    stream (HDARRAY_ASYNC_WRITE=1): every later use of the array waits for it, and it waits for
+    the library's earlier work on that array -- here a Write right after a kernel that reads the
+    array, and Writes of one input while the other is being computed on.  Results equal the
+    oracle's after the same calls, bit for bit, with the copy stream and without it."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setenv("HDARRAY_ASYNC_WRITE", async_write)
+    dims, P, dtype = (1030, 770), 4, "float"
+    xs = [synthetic.jacobi_field(dims, stream=35 + i, dtype=dtype) for i in range(3)]
+    pinned = [torch.from_numpy(x).pin_memory() for x in xs]
+    gpu_lib(P)
+    B0 = H.HDArrayCreate("B0", dtype, None, *dims)
+    B1 = H.HDArrayCreate("B1", dtype, None, *dims)
+    A = H.HDArrayCreate("A", dtype, None, *dims)
+    D = H.HDArrayPartition(BLOCK, dims, (0, 0), dims, P)
+    W = H.HDArrayPartition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1), P)
+    o = oracle.Oracle(P)
+    ob = [o.create("B0", dtype, dims), o.create("B1", dtype, dims)]
+    oa = o.create("A", dtype, dims)
+    od = o.partition(BLOCK, dims, (0, 0), dims)
+    ow = o.partition(BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1))
+    lb = [B0, B1]
+    for i in range(2):  # first Writes allocate the buffers
+        H.HDArrayWrite(lb[i], pinned[i], D)
+        o.write(ob[i], xs[i], od)
+    H.HDArrayApplyKernel("jacobi2d", W, lb[0], A)
+    o.apply("jacobi2d", ow, [ob[0], oa])
+    for k in range(6):
+        cur, nxt = k % 2, (k + 1) % 2
+        H.HDArrayApplyKernel("jacobi2d", W, A, lb[cur])         # reads A, writes B_cur
+        o.apply("jacobi2d", ow, [oa, ob[cur]])
+        H.HDArrayWrite(lb[nxt], pinned[(k + 2) % 3], D)           # the other input, while B_cur is used
+        o.write(ob[nxt], xs[(k + 2) % 3], od)
+        H.HDArrayApplyKernel("jacobi2d", W, lb[cur], A)          # reads B_cur
+        o.apply("jacobi2d", ow, [ob[cur], oa])
+        H.HDArrayWrite(lb[cur], pinned[k % 3], D)                 # overwrites B_cur right after that read
+        o.write(ob[cur], xs[k % 3], od)
+        H.HDArrayApplyKernel("jacobi2d", W, lb[nxt], A)
+        o.apply("jacobi2d", ow, [ob[nxt], oa])
+    for h, oarr in ((A, oa), (B0, ob[0]), (B1, ob[1])):
+        got = np.zeros(dims, np.float32)
+        H.HDArrayRead(h, got, D)
+        assert np.array_equal(got, oarr.G)
+
+
 # ---------------------------------------------------------------------------------------------
 # GEMM (binary64)
 # ---------------------------------------------------------------------------------------------
