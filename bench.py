@@ -279,9 +279,11 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_stream(stream)
     H.HDArrayInit(ndev=P)
     H.HDArraySetStream(stream.cuda_stream)
-    x = synthetic.jacobi_field((N, N), stream=1, dtype="float")
-    xh = torch.from_numpy(x).pin_memory()
-    B, A, R, D, W = setup_jacobi(H, "float")
+    storage = args.storage
+    esize = 4 if storage == "float" else 2
+    x = synthetic.jacobi_field((N, N), stream=1, dtype=storage)
+    xh = torch.from_numpy(x if storage == "float" else x.view(np.int16)).pin_memory()
+    B, A, R, D, W = setup_jacobi(H, storage)
     H.HDArrayWrite(B, xh, D)
 
     def warm_iters(b, a):
@@ -300,7 +302,7 @@ def gpu_arm(args, rank, world):
 
     # exchange volume of one iteration (the fused kernel's halo traffic)
     H.HDArrayApplyKernel("jacobi2d", W, B, A)
-    xbytes = sum(int(np.prod(np.subtract(hi, lo))) for _, _, lo, hi in H.HDArrayGetPlan(B)) * 4
+    xbytes = sum(int(np.prod(np.subtract(hi, lo))) for _, _, lo, hi in H.HDArrayGetPlan(B)) * esize
     H.HDArrayApplyKernel("jacobi2d", W, A, B)
     torch.cuda.synchronize()
 
@@ -335,14 +337,14 @@ def gpu_arm(args, rank, world):
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev)
     launches = c1["launches"] - c0["launches"]
     per_launch_ms = kernel_ms / (args.steps * ITERS)
-    algo_bytes = CELLS * 8 + 2 * xbytes
+    algo_bytes = CELLS * 2 * esize + 2 * xbytes
     pk = peaks()
     achieved = algo_bytes / (per_launch_ms * 1e-3) / 1e9
     value = replica_rate(CELLS * ITERS * args.steps, world, ms) / 1e9
     residual_us = (t0.elapsed_time(t1) - kernel_ms) / args.steps * 1e3
 
     e2e, parity = None, None
-    if rank == 0 and not args.quick:
+    if rank == 0 and not args.quick and storage == "float":
         e2e = e2e_run(H, torch, stream, B, A, R, D, W, xh, gid, args)
         # a fresh step from the input: the field after exactly 100 iterations
         H.HDArrayWrite(B, xh, D)
@@ -355,7 +357,7 @@ def gpu_arm(args, rank, world):
         parity = cone_check(x, got, sample_points_2d(N), ITERS, np.float32)
     H.HDArrayExit()
     extra = {}
-    if rank == 0 and not args.quick:
+    if rank == 0 and not args.quick and storage == "float":
         extra = extra_forms(H, torch, stream, args)
     return dict(ms=ms, value=value, launches=launches, per_launch_ms=per_launch_ms,
                 algo_bytes=algo_bytes, xbytes=xbytes, achieved=achieved, peaks=pk,
@@ -1212,6 +1214,8 @@ def main():
                     help="headline only: skip the comparison forms, e2e, parity checks and sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default tile shapes")
+    ap.add_argument("--storage", default="float", choices=["float", "bf16"],
+                    help="headline workload's storage type (bf16 for profiling the BF16 form alone)")
     ap.add_argument("--grid", type=int, default=8192,
                     help="grid side (default 8192; smaller only for profiling captures)")
     ap.add_argument("--n3", type=int, default=512, help="3-D workload: cube side")
@@ -1242,7 +1246,7 @@ def main():
     r = gpu_arm(args, rank, world)
     tuned = tune_report(tpath)
     subs = None
-    if rank == 0 and not args.quick:
+    if rank == 0 and not args.quick and args.storage == "float":
         subs = sub_workloads(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1250,17 +1254,20 @@ def main():
     if rank == 0:
         variant = jacobi_variant(tuned)
         traffic = profiled("jacobi2d_fp32_8192_block16.md", "dram_bytes_per_launch_v%d" % variant,
-                           ["k_stencil2d.cu", "stencil_common.cuh"]) if N == 8192 else None
+                           ["k_stencil2d.cu", "stencil_common.cuh"]) if N == 8192 and args.storage == "float" else None
         pk = r["peaks"]
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "float" else "bf16 storage, f32 arithmetic",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("8192x8192", "%dx%d" % (N, N)), "grid": [N, N], "logical_devices": P,
+            "config": {"workload": WORKLOAD.replace("8192x8192", "%dx%d" % (N, N)).replace(
+                           "FP32", "FP32" if args.storage == "float" else "BF16 storage"),
+                       "grid": [N, N], "logical_devices": P,
                        "iterations_per_step": ITERS, "parallelism": "replicas" if world > 1 else "1 GPU",
                        "l2": "inputs 2 x %d MiB %s 129 MB L2 (no flush)" % (N * N * 4 // 2 ** 20, ">" if N * N * 4 > 129e6 else "<=")},
-            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES_2D[variant] + ", fused exchange + stencil",
+            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES_2D[variant].replace("f32", "f32" if args.storage == "float" else "bf16") + ", fused exchange + stencil",
                          "achieved": r["achieved"], "peak": pk["hbm"], "unit": "GB/s",
                          "frac": r["achieved"] / pk["hbm"], "peak_source": pk["source"],
                          "traffic": traffic, "algo_bytes_per_launch": r["algo_bytes"],
