@@ -90,6 +90,17 @@ __device__ __forceinline__ void split(float x, uint16_t &h, uint16_t &l)
 // Byte offset of 16-byte chunk c of row r in a K-major 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
+// The same for the 64-byte swizzle (rows of 64 bytes, 32 bf16 of K): chunk c of row r stored at
+// chunk c ^ ((r / 2) % 4), the pattern repeating every 8 rows (512 bytes).
+__device__ __forceinline__ uint32_t sw64_off(int r, int c) { return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4)); }
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3(const TcPart *__restrict__ parts,
@@ -271,11 +282,12 @@ cudaError_t launch_gemm_tc(const TcPart *parts, const TcTile *tiles, int ntiles,
 // Pre-split operand panels and the pipelined tensor-core GEMM.
 //
 // Panels: the bf16 parts of A (per device, its 128-row tiles) and of B^T (column tiles of the
-// CTA width), each 128 x 64 (A) or BNp x 64 (B) tile stored contiguously in exactly the K-major
-// 128-byte-swizzled layout the MMA reads, so a K step of a CTA is two contiguous bulk copies.
-// With NSP parts per operand (2: hi, lo -- "bf16x3"; 3: hi, mid, lo -- "bf16x6"), a panel tile
-// (mt, kt) part q sits at ((mt * nkt + kt) * NSP + q) * A_BYTES and a B panel tile (nt, kt) part q
-// at ((nt * nkt + kt) * NSP + q) * BNp * 128.
+// CTA width, 256), each 128 x BKp (A) or 256 x BKp (B) tile stored contiguously in exactly the
+// K-major swizzled layout the MMA reads, so a K step of a CTA is two contiguous bulk copies.
+// With NSP parts per operand (2: hi, lo -- "bf16x3", BKp = 64, 128-byte rows and swizzle; 3: hi,
+// mid, lo -- "bf16x6", BKp = 32, 64-byte rows and swizzle), a panel tile (mt, kt) part q sits at
+// ((mt * nkt + kt) * NSP + q) * 128 * BKp * 2 and a B panel tile (nt, kt) part q at
+// ((nt * nkt + kt) * NSP + q) * 256 * BKp * 2.
 //
 // bf16x6 (the same paper's higher-accuracy form): x = hi + mid + lo with hi = bf16(x),
 // mid = bf16(x - hi), lo = bf16(x - hi - mid) (both differences exact in binary32), and the six
@@ -309,6 +321,8 @@ __device__ __forceinline__ uint4 pack8(const uint16_t *v)
 }
 
 // One CTA per (tile, part set): thread -> 16-byte chunk (row r, 8 consecutive k), every part.
+// Tiles of bk = 64 k are 128-byte rows in the 128-byte swizzle, tiles of bk = 32 64-byte rows in the
+// 64-byte swizzle.
 __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict__ jobs)
 {
     const SplitJob J = jobs[blockIdx.y];
@@ -316,18 +330,20 @@ __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict_
     const int tile = blockIdx.x;      // row tile * nkt + k tile
     if (tile >= J.ntiles) return;
     const int mt = tile / tiles_per_row, kt = tile - mt * tiles_per_row;
-    const int rows = J.rows_per_tile;  // 128 (A) or the CTA width (B)
+    const int rows = J.rows_per_tile;  // 128 (A) or the CTA width (B): powers of two
     const int nsp = J.nparts;          // 2 or 3
+    const int bk = J.bk;               // 64 or 32
+    const int cpr = bk / 8;            // 16-byte chunks per row
     const float *src = reinterpret_cast<const float *>(J.src);
-    uint8_t *part0 = reinterpret_cast<uint8_t *>(J.dst) + (size_t)tile * nsp * rows * 128;
-    for (int q = threadIdx.x; q < rows * 8; q += blockDim.x) {
-        const int r = J.transpose ? (q & (rows - 1)) : (q >> 3);
-        const int c = J.transpose ? (q / rows) : (q & 7);
+    uint8_t *part0 = reinterpret_cast<uint8_t *>(J.dst) + (size_t)tile * nsp * rows * (bk * 2);
+    for (int q = threadIdx.x; q < rows * cpr; q += blockDim.x) {
+        const int r = J.transpose ? (q & (rows - 1)) : (q / cpr);
+        const int c = J.transpose ? (q / rows) : (q - (q / cpr) * cpr);
         const int row = J.row0 + mt * rows + r;  // A: row i; B: column n
         uint16_t h[8], m[8], l[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) {
-            const int k = kt * 64 + c * 8 + e;
+            const int k = kt * bk + c * 8 + e;
             float v = 0.0f;
             if (row < J.row_end && k < J.kend && (!J.lower || k <= row)) {
                 if (J.transpose) v = src[(int64_t)(k - J.lo0) * J.stride + (row - J.lo1)];  // B[k][n]
@@ -336,8 +352,8 @@ __global__ void __launch_bounds__(256) k_split_panel(const SplitJob *__restrict_
             if (nsp == 3) split3(v, h[e], m[e], l[e]);
             else split(v, h[e], l[e]);
         }
-        const uint32_t off = sw_off(r, c);
-        const size_t pb = (size_t)rows * 128;
+        const uint32_t off = bk == 64 ? sw_off(r, c) : sw64_off(r, c);
+        const size_t pb = (size_t)rows * bk * 2;
         *reinterpret_cast<uint4 *>(part0 + off) = pack8(h);
         if (nsp == 3) {
             *reinterpret_cast<uint4 *>(part0 + pb + off) = pack8(m);
@@ -361,18 +377,28 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-constexpr int P_STAGES = 2;
+constexpr int P_STAGES_MAX = 3;
 
-// Panel GEMM geometry for NSP bf16 parts per operand.
+// Panel GEMM geometry for NSP bf16 parts per operand.  Both forms compute 128 x 256 tiles of C.
+// bf16x3: K steps of 64 (128-byte rows, 128-byte swizzle), two stages of 96 KB.  bf16x6: K steps
+// of 32 (64-byte rows, 64-byte swizzle), three stages of 72 KB -- the same MMA work per stage as a
+// 128 x 128 tile with K steps of 64, and a quarter fewer operand bytes streamed per MMA flop.
 template <int NSP>
 struct PanelGeo {
-    static constexpr int BNp = NSP == 3 ? 128 : 256;              // CTA tile width
-    static constexpr int B_BYTESp = BNp * BK * 2;                 // one part of the B slice
-    static constexpr int STAGEp = NSP * A_BYTES + NSP * B_BYTESp;  // 96 KB for both forms
+    static constexpr int BNp = 256;                                 // CTA tile width
+    static constexpr int BKp = NSP == 3 ? 32 : 64;                  // K per stage
+    static constexpr int STAGES = NSP == 3 ? 3 : 2;
+    static constexpr int A_BYTESp = BM * BKp * 2;                   // one part of the A slice
+    static constexpr int B_BYTESp = BNp * BKp * 2;                  // one part of the B slice
+    static constexpr int STAGEp = NSP * A_BYTESp + NSP * B_BYTESp;  // 96 KB (x3), 72 KB (x6)
     static constexpr uint32_t IDESCp = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNp >> 3) << 17) |
                                        ((uint32_t)(BM >> 4) << 24);
+    __device__ static uint64_t desc(uint32_t saddr) { return NSP == 3 ? sw64_desc(saddr) : sw128_desc(saddr); }
 };
-static_assert(PanelGeo<2>::STAGEp == STAGE_BYTES && PanelGeo<3>::STAGEp == STAGE_BYTES, "stage size");
+static_assert(PanelGeo<2>::STAGEp == STAGE_BYTES && PanelGeo<3>::STAGEp == 72 * 1024, "stage size");
+static_assert(PanelGeo<2>::STAGES * PanelGeo<2>::STAGEp + 1024 <= 227 * 1024 &&
+              PanelGeo<3>::STAGES * PanelGeo<3>::STAGEp + 1024 <= 227 * 1024, "shared memory");
+static_assert(PanelGeo<3>::STAGES <= P_STAGES_MAX && PanelGeo<2>::STAGES <= P_STAGES_MAX, "stages");
 
 __device__ __forceinline__ void mma_bf16_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                             uint32_t accumulate)
@@ -403,7 +429,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     constexpr uint32_t TMEM_COLSp = (uint32_t)BNp;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], done;
+    constexpr int P_STAGES = G::STAGES;
+    __shared__ __align__(8) uint64_t full[P_STAGES_MAX], empty[P_STAGES_MAX], done;
     __shared__ uint32_t taddr_s;
     __shared__ volatile int fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -428,12 +455,12 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = taddr_s;
-    const int nkt = (tile.kend + BK - 1) / BK;
+    const int nkt = (tile.kend + G::BKp - 1) / G::BKp;
     const int mt = (tile.i0 - P.row0) / BM, nt = (tile.j0 - P.col0) / BNp;
 
     if (warp == 0 && lane == 0) {  // producer
-        uint32_t ph[P_STAGES] = {0u, 0u};
-        int fills[P_STAGES] = {0, 0};
+        uint32_t ph[P_STAGES] = {};
+        int fills[P_STAGES] = {};
         for (int kt = 0; kt < nkt && !fail; kt++) {
             const int s = kt % P_STAGES;
             if (kt >= P_STAGES) {
@@ -442,18 +469,18 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
             }
             fills[s]++;
             uint8_t *st = smem + s * G::STAGEp;
-            const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * NSP) * A_BYTES;
+            const uint8_t *ap = reinterpret_cast<const uint8_t *>(P.apanel) + (size_t)((mt * P.nkt + kt) * NSP) * G::A_BYTESp;
             const uint8_t *bp = reinterpret_cast<const uint8_t *>(P.bpanel) + (size_t)((nt * P.nkt_b + kt) * NSP) * G::B_BYTESp;
             const uint32_t fb = smem_u32(&full[s]);
             mbar_expect(fb, (uint32_t)G::STAGEp);
-            bulk_g2s(smem_u32(st), ap, NSP * A_BYTES, fb);                     // every part of A
-            bulk_g2s(smem_u32(st + NSP * A_BYTES), bp, NSP * G::B_BYTESp, fb);  // every part of B
+            bulk_g2s(smem_u32(st), ap, NSP * G::A_BYTESp, fb);                     // every part of A
+            bulk_g2s(smem_u32(st + NSP * G::A_BYTESp), bp, NSP * G::B_BYTESp, fb);  // every part of B
         }
         if (fail)  // every bulk copy issued lands before the CTA's shared memory is released
             for (int s = 0; s < P_STAGES; s++)
                 if (fills[s] > 0) mbar_wait(smem_u32(&full[s]), (uint32_t)((fills[s] - 1) & 1));
     } else if (warp == 1 && lane == 0) {  // MMA issuer
-        uint32_t ph[P_STAGES] = {0u, 0u};
+        uint32_t ph[P_STAGES] = {};
         int kt = 0;
         for (; kt < nkt && !fail; kt++) {
             const int s = kt % P_STAGES;
@@ -461,16 +488,16 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16x3_panels(const PanelPart *
             ph[s] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = smem_u32(smem + s * G::STAGEp);
-            const uint32_t a0 = st, b0 = st + NSP * A_BYTES;  // part q at + q * A_BYTES / B_BYTESp
+            const uint32_t a0 = st, b0 = st + NSP * G::A_BYTESp;  // part q at + q * A_BYTESp / B_BYTESp
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; kk++) {
-                const uint32_t off = kk * 32;
+            for (int kk = 0; kk < G::BKp / 16; kk++) {
+                const uint32_t off = kk * 32;  // 16 bf16 of K along the (swizzled) row
                 // (A part, B part) pairs: x3 keeps (0,0) (0,1) (1,0); x6 adds (0,2) (1,1) (2,0)
 #pragma unroll
                 for (int pr = 0; pr < (NSP == 3 ? 6 : 3); pr++) {
                     const int qa = pr == 2 ? 1 : pr == 4 ? 1 : pr == 5 ? 2 : 0;
                     const int qb = pr == 1 ? 1 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
-                    mma_bf16_id(tmem, sw128_desc(a0 + qa * A_BYTES + off), sw128_desc(b0 + qb * G::B_BYTESp + off),
+                    mma_bf16_id(tmem, G::desc(a0 + qa * G::A_BYTESp + off), G::desc(b0 + qb * G::B_BYTESp + off),
                                 G::IDESCp, (kt > 0 || kk > 0 || pr > 0) ? 1u : 0u);
                 }
             }
@@ -541,7 +568,8 @@ cudaError_t launch_gemm_panels(const PanelPart *parts, const TcTile *tiles, int 
     if (ntiles <= 0) return cudaSuccess;
     if (nparts != 2 && nparts != 3) return cudaErrorInvalidValue;
     static bool attr[2] = {false, false};
-    const size_t sm = (size_t)P_STAGES * STAGE_BYTES + 1024;
+    const size_t sm = nparts == 3 ? (size_t)PanelGeo<3>::STAGES * PanelGeo<3>::STAGEp + 1024
+                                  : (size_t)PanelGeo<2>::STAGES * PanelGeo<2>::STAGEp + 1024;
     auto fn = nparts == 3 ? k_gemm_bf16x3_panels<3> : k_gemm_bf16x3_panels<2>;
     if (!attr[nparts - 2]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -199,10 +199,11 @@ struct SplitJob {
     int32_t row0, row_end;     // A: rows of C's row tiles; B: columns of C's column tiles
     int32_t kend;              // K extent
     int32_t nkt, ntiles;       // k tiles per row tile, total tiles
-    int32_t rows_per_tile;     // 128 (A) or the GEMM's CTA width (B: 256 for 2 parts, 128 for 3)
+    int32_t rows_per_tile;     // 128 (A) or the GEMM's CTA width (B: 256)
     int32_t transpose;         // 1 for B (stored as B^T)
     int32_t lower;             // A lower triangular
     int32_t nparts;            // bf16 parts per value: 2 (hi, lo) or 3 (hi, mid, lo)
+    int32_t bk;                // k per tile: 64 (128-byte rows, 2 parts) or 32 (64-byte rows, 3 parts)
 };
 struct PanelPart {
     const void *apanel;  // A panel of this device's rows (row tiles from row0)

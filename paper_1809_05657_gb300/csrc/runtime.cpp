@@ -1323,7 +1323,7 @@ int compile_plan(Plan &pl)
                 t.i1 = q.i1; t.j1 = q.j1; t.lower = q.lower; t.pad = 0;
                 const int pi = (int)tp.size();
                 tp.push_back(t);
-                const int tcbn = g->gemm_parts == 3 ? 128 : 256;  // CTA tile width of the form
+                const int tcbn = 256;  // CTA tile width of both forms
                 for (int ti = q.i0; ti < q.i1; ti += 128)
                     for (int tj = q.j0; tj < q.j1; tj += tcbn) {
                         if (q.upper && tj + tcbn - 1 < ti) continue;  // entirely below the diagonal
@@ -1429,11 +1429,12 @@ int compile_plan(Plan &pl)
     for (const TcPart &t : tp) panel_ok = panel_ok && t.j1 > 0;
     const bool syrk = k.kind == K_SYRK;  // only the panel kernel reads A transposed
     const int nsp = g->gemm_parts;       // bf16 parts per value (3: only the panel kernel has it)
-    const int tcbn = nsp == 3 ? 128 : 256;
+    const int tcbn = 256;                // CTA tile width
+    const int pbk = nsp == 3 ? 32 : 64;  // K per panel tile (64-byte or 128-byte rows)
     if (panel_ok && (syrk || nsp == 3 || getenv("HDARRAY_GEMM_NO_PANELS") == nullptr)) {
         HDArray *A = pl.args[0], *B = syrk ? pl.args[0] : pl.args[1];
         const int64_t nk = syrk ? A->n[0] : A->n[1];
-        const int nkt_b = (int)((nk + 63) / 64);
+        const int nkt_b = (int)((nk + pbk - 1) / pbk);
         std::vector<SplitJob> ajobs, bjobs;
         std::vector<PanelPart> pp;
         std::map<std::pair<int64_t, int64_t>, size_t> aoff, boff;
@@ -1442,12 +1443,12 @@ int compile_plan(Plan &pl)
             const Box &W = pt.box[p];
             if (W.empty()) continue;
             const int64_t kend = (k.kind == K_TRMM) ? std::min<int64_t>(nk, W.hi[0]) : nk;
-            const int nkt = (int)((kend + 63) / 64);
+            const int nkt = (int)((kend + pbk - 1) / pbk);
             const auto ka = std::make_pair(W.lo[0], W.hi[0]), kb = std::make_pair(W.lo[1], W.hi[1]);
             if (!aoff.count(ka)) {
                 const int nmt = (int)((W.hi[0] - W.lo[0] + 127) / 128);
                 aoff[ka] = total;
-                total += (size_t)nmt * nkt * nsp * (128 * 64 * 2);
+                total += (size_t)nmt * nkt * nsp * (128 * pbk * 2);
                 SplitJob J;
                 const DevBuf &ba = A->buf[p];
                 J.src = ba.ptr; J.dst = (void *)(uintptr_t)aoff[ka];  // offset until the panels exist
@@ -1456,12 +1457,13 @@ int compile_plan(Plan &pl)
                 J.nkt = nkt; J.ntiles = nmt * nkt; J.rows_per_tile = 128; J.transpose = syrk ? 1 : 0;
                 J.lower = k.kind == K_TRMM ? 1 : 0;
                 J.nparts = nsp;
+                J.bk = pbk;
                 ajobs.push_back(J);
             }
             if (!boff.count(kb)) {
                 const int nnt = (int)((W.hi[1] - W.lo[1] + tcbn - 1) / tcbn);
                 boff[kb] = total;
-                total += (size_t)nnt * nkt_b * nsp * ((size_t)tcbn * 64 * 2);
+                total += (size_t)nnt * nkt_b * nsp * ((size_t)tcbn * pbk * 2);
                 SplitJob J;
                 const DevBuf &bb = B->buf[p];
                 J.src = bb.ptr; J.dst = (void *)(uintptr_t)boff[kb];
@@ -1469,6 +1471,7 @@ int compile_plan(Plan &pl)
                 J.row0 = (int32_t)W.lo[1]; J.row_end = (int32_t)W.hi[1]; J.kend = (int32_t)nk;
                 J.nkt = nkt_b; J.ntiles = nnt * nkt_b; J.rows_per_tile = tcbn; J.transpose = 1; J.lower = 0;
                 J.nparts = nsp;
+                J.bk = pbk;
                 bjobs.push_back(J);
             }
             PanelPart q;
