@@ -238,11 +238,216 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_cta(const StenPart3D 
     cpa_wait<0>();
 }
 
+// ------------------------------------------------------------------------------------------
+// The CTA variant with its planes staged by the tensor memory accelerator: the same tiles, ring
+// and two output planes per step as above, but entry e (plane z0 - 1 + e of rows y0 - 1 ..
+// y0 + ny and chunks xb - VEC .. of the part's X buffer) arrives as one bulk tensor copy
+// (cp.async.bulk.tensor.3d) issued by thread 0 into its stage, completing a transaction-count
+// mbarrier the computing threads wait on, instead of a cp.async per thread and slot.  The box
+// of a part's tensor map is its tiles' staged plane (rwb chunks x boxh rows; a ragged tile loads
+// rows it does not read, coordinates outside the buffer read zeros).  The receive phase's stores
+// are ordinary (generic) writes to the X buffer, so every thread fences them to the async proxy
+// before the barrier after which the first bulk copy is issued.  Waits are bounded: after
+// spin_limit polls a wait gives up, the tile computes nothing, thread 0 waits (with a fixed limit)
+// for the copies it issued and the error word is set.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+constexpr unsigned TMA_DRAIN_LIMIT = 1u << 22;  // polls when draining after a failed wait
+
+template <int DT, int NS, int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D *__restrict__ parts,
+                                                       const StenTile3D *__restrict__ tiles, int stage_slots,
+                                                       const Seg *__restrict__ segs,
+                                                       const uint8_t *__restrict__ tmaps, unsigned *err,
+                                                       unsigned spin_limit)
+{
+    static_assert((NS & (NS - 1)) == 0 && NS >= 6, "ring depth: a power of two, at least 6");
+    using EL = Elem<DT>;
+    using E = typename EL::E;
+    using A = typename EL::A;
+    using V = typename EL::V;
+    constexpr int VEC = EL::VEC;
+    extern __shared__ uint4 smem_dyn[];
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ int fail;
+    const int lane = threadIdx.x & 31;
+    const StenTile3D t = tiles[blockIdx.x];
+    const StenPart3D P = parts[t.part];
+    // the ring starts on a 128-byte boundary (the launch adds 128 bytes of slack)
+    const uint32_t ring_s = (smem_addr(smem_dyn) + 127u) & ~127u;
+    const uint4 *ring = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(smem_dyn) +
+                                                          (ring_s - smem_addr(smem_dyn)));
+
+    if (t.nseg > 0) receive_flat_vec<E>(segs, t.seg0, t.nseg, threadIdx.x, blockDim.x);
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // the receive's stores, before bulk copies read them
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail = 0;
+    }
+    __syncthreads();
+
+    const int ny = t.ny, nch = t.nch, rw = P.rwb;  // a staged row: halo chunk, nch chunks, halo chunk(s)
+    const int L = t.z1 - t.z0;                      // output planes; entries 0 .. L+1
+    const bool needL = t.x0 == t.xb;              // x0 - 1 lies in the left halo chunk
+    const bool needR = t.x1 == t.xb + nch * VEC;  // x1 lies in the right halo chunk
+    const uint32_t stage_bytes = (uint32_t)stage_slots * 16u;
+    const uint32_t box_bytes = (uint32_t)P.boxh * (uint32_t)rw * 16u;
+    const uint8_t *tmap = tmaps + (size_t)t.part * 128;
+    const int xc = (int)(t.xb - VEC - P.xlo2), yc = (int)(t.y - 1 - P.xlo1), zc = (int)(t.z0 - 1 - P.xlo0);
+    int issued = 0;  // thread 0: entries issued so far
+    auto issue = [&](int e) {
+        if (e > L + 1) return;
+        const uint32_t bar = smem_addr(&full[e & (NS - 1)]);
+        const uint32_t dst = ring_s + (uint32_t)(e & (NS - 1)) * stage_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(box_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+            "l"(tmap), "r"(xc), "r"(yc), "r"(zc + e), "r"(bar)
+            : "memory");
+        issued = e + 1;
+    };
+    if (threadIdx.x == 0)
+        for (int e = 0; e < NS - 2; e++) issue(e);  // entries 0 .. NS-3
+
+    // the chunk this thread computes: row r, chunk c (every chunk of the tile holds outputs)
+    const int r = threadIdx.x / nch, c = threadIdx.x - r * nch;
+    const int x = t.xb + c * VEC;
+    const bool act = r < ny;
+    const bool full_chunk = x >= t.x0 && x + VEC <= t.x1;
+    const int me = (r + 1) * rw + c + 1;
+    const bool shflL = c > 0 && lane > 0, shflR = c < nch - 1 && lane < 31;
+    const bool haveL = c > 0 || needL, haveR = c < nch - 1 || needR;
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.y + r - P.ylo1) * P.ys1 + (x - P.ylo2) +
+            (int64_t)(t.z0 - P.ylo0) * P.ys0;
+
+    auto ld = [&](int e, int off, A (&v)[VEC]) {  // chunk `me + off` of entry e
+        if (act) {
+            EL::unpack(*reinterpret_cast<const V *>(ring + (e & (NS - 1)) * stage_slots + me + off), v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; k++) v[k] = A(1);  // idle threads: sums of ones
+        }
+    };
+    auto plane = [&](int e, const A (&cv)[VEC], const A (&zm)[VEC], const A (&zq)[VEC], E *out_p) {
+        A ym[VEC], yq[VEC];
+        ld(e, -rw, ym);
+        ld(e, rw, yq);
+        A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
+        A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
+        const E *row = reinterpret_cast<const E *>(ring + (e & (NS - 1)) * stage_slots + me);
+        if (!shflL) left = act && haveL ? EL::load1(row - 1) : A(1);
+        if (!shflR) right = act && haveR ? EL::load1(row + VEC) : A(1);
+        A out[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const A wv = k > 0 ? cv[k - 1] : left;
+            const A ev = k < VEC - 1 ? cv[k + 1] : right;
+            A s = wv + ev;
+            s = s + ym[k];
+            s = s + yq[k];
+            s = s + zm[k];
+            s = s + zq[k];
+            out[k] = s;
+        }
+        div6_n(out);
+        if (act) {
+            if (full_chunk) {
+                *reinterpret_cast<V *>(out_p) = EL::pack(out);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; k++)
+                    if (x + k >= t.x0 && x + k < t.x1) EL::store1(out_p + k, out[k]);
+            }
+        }
+    };
+
+    for (int k = 0; k < L; k += 2) {
+        // entries k .. k+3 must have landed; the earlier ones were waited for in earlier steps
+        bool ok = true;
+        for (int e = k == 0 ? 0 : k + 2; e <= k + 3 && e <= L + 1; e++)
+            ok = ok && mbar_wait_bounded(smem_addr(&full[e & (NS - 1)]), (uint32_t)((e / NS) & 1), spin_limit);
+        if (!ok) fail = 1;
+        __syncthreads();  // every thread is done with the stages of entries k-2 and k-1
+        if (fail) break;  // the same for every thread after the barrier
+        if (threadIdx.x == 0) {
+            issue(k + NS - 2);
+            issue(k + NS - 1);
+        }
+        A zm[VEC], cv[VEC], zq[VEC];
+        ld(k, 0, zm);
+        ld(k + 1, 0, cv);
+        ld(k + 2, 0, zq);
+        plane(k + 1, cv, zm, zq, yp);  // output plane z0 + k
+        if (k + 1 < L) {               // output plane z0 + k + 1: centre zq, below cv, above entry k+3
+            A zq2[VEC];
+            ld(k + 3, 0, zq2);
+            plane(k + 2, zq, cv, zq2, yp + P.ys0);
+        }
+        yp += 2 * P.ys0;
+    }
+    if (fail && threadIdx.x == 0) {
+        // the copies issued land before the CTA's shared memory is released: the last one of each
+        // stage completes that stage's latest phase
+        for (int e = issued - 1; e >= 0 && e >= issued - NS; e--)
+            mbar_wait_bounded(smem_addr(&full[e & (NS - 1)]), (uint32_t)((e / NS) & 1), TMA_DRAIN_LIMIT);
+        if (err) atomicOr(err, 1u);
+    }
+}
+
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
                              int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
-                             cudaStream_t s)
+                             cudaStream_t s, const void *tmaps, unsigned *err, unsigned spin_limit)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (variant == 3) {
+        constexpr int NS = STENCIL3D_STAGES;
+        const int T = warps_per_cta == 16 ? 512 : 256;
+        if (!tmaps || smem < 128) return cudaErrorInvalidValue;
+        const int slots = (int)((smem - 128) / ((size_t)NS * 16));
+        if (slots < 1 || slots % 8 != 0 || smem != (size_t)NS * slots * 16 + 128) return cudaErrorInvalidValue;
+        const int which = (dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1);
+        if (which < 0) return cudaErrorInvalidValue;
+        using KFn = void (*)(const StenPart3D *, const StenTile3D *, int, const Seg *, const uint8_t *, unsigned *,
+                             unsigned);
+        const KFn fns[2][3] = {{k_stencil3d_tma<DT_F64, NS, 256>, k_stencil3d_tma<DT_F32, NS, 256>, k_stencil3d_tma<DT_BF16, NS, 256>},
+                               {k_stencil3d_tma<DT_F64, NS, 512>, k_stencil3d_tma<DT_F32, NS, 512>, k_stencil3d_tma<DT_BF16, NS, 512>}};
+        const int wt = T == 512 ? 1 : 0;
+        static bool attr[2][3] = {};
+        if (!attr[wt][which]) {
+            cudaError_t e = cudaFuncSetAttribute(fns[wt][which], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 NS * 768 * 16 + 128);
+            if (e != cudaSuccess) return e;
+            attr[wt][which] = true;
+        }
+        if (smem > (size_t)NS * 768 * 16 + 128) return cudaErrorInvalidValue;
+        fns[wt][which]<<<ntiles, T, smem, s>>>(parts, tiles, slots, segs, reinterpret_cast<const uint8_t *>(tmaps), err,
+                                               spin_limit);
+        return cudaGetLastError();
+    }
     if (variant == 1) {
         constexpr int NS = STENCIL3D_STAGES;
         const int T = warps_per_cta == 16 ? 512 : 256;

@@ -83,6 +83,7 @@ struct StenPart3D {
     void *y;
     int64_t xlo0, xlo1, xlo2, xs0, xs1;  // origin (z, y, x) and strides of z and y (elements)
     int64_t ylo0, ylo1, ylo2, ys0, ys1;
+    int32_t rwb, boxh;  // TMA variant: staged plane box of the part's tiles, 16-byte chunks x rows
 };
 struct StenTile3D {
     int32_t part;
@@ -100,9 +101,12 @@ constexpr int STENCIL3D_STAGES = 8;
 // variant 0: one warp per tile (a row), prefetch in registers (warps_per_cta tiles per CTA);
 // variant 1: one CTA of 32 * warps_per_cta threads (8 or 16 warps) per tile, planes prefetched into
 // shared memory (cp.async), smem bytes as above.
+// variant 3 (the CTA tiles with planes staged by TMA): tmaps holds one 128-byte CUtensorMap per
+// part (its X buffer), err receives a set bit when a bounded wait gave up after spin_limit polls.
 cudaError_t launch_stencil3d(int dtype, const StenPart3D *parts, const StenTile3D *tiles,
                              int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
-                             cudaStream_t s);
+                             cudaStream_t s, const void *tmaps = nullptr, unsigned *err = nullptr,
+                             unsigned spin_limit = 0);
 
 // Flat-block forms (binary32 / binary64): one CTA per block of a work box, the block and its halo
 // staged in shared memory, threads walking the block's cells in row-major order.  2-D tiles use

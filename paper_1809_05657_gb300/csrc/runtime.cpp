@@ -3,6 +3,8 @@
 // C ABI declared in include/hdarray.h.
 #include "runtime.h"
 
+#include <cudaTypedefs.h>
+
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -921,6 +923,35 @@ void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const 
 // of 32 chunks, one row per tile; variant 1: the box's chunks cut into bands of equal width of
 // at most band_chunks, as many rows per tile as `threads` threads hold; variant 2 (flat_cells > 0):
 // balanced widths up to 128 elements, rows so that a plane has about flat_cells cells.
+// A 3-D tensor map over device buffer b of X for tile boxes of box_w elements x box_h rows x one
+// plane (the driver's encoder, found through the runtime; nothing links the driver library).
+bool encode_box_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUtensorMap *out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const CUtensorMapDataType dt = X->dtype == DT_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : X->dtype == DT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)(b.alloc.hi[2] - b.alloc.lo[2]), (cuuint64_t)(b.alloc.hi[1] - b.alloc.lo[1]),
+                                (cuuint64_t)(b.alloc.hi[0] - b.alloc.lo[0])};
+    const cuuint64_t strides[2] = {(cuuint64_t)(b.st[1] * X->esize), (cuuint64_t)(b.st[0] * X->esize)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (box_w < 1 || box_w > 256 || box_h < 1 || box_h > 256 || (box_w * X->esize) % 16 != 0) return false;
+    if (strides[0] % 16 != 0 || strides[1] % 16 != 0 || ((uintptr_t)b.ptr & 15) != 0) return false;
+    return encode(out, dt, 3, b.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                      const std::vector<Move> &recv, bool want_segs, int variant, Sten3DHost &h,
                      int flat_cells = 0, int band_chunks = 32, int threads = 256)
@@ -958,6 +989,25 @@ bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, in
         band = nch * VEC;
         rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(threads / nch, slot_cap / (nch + 2) - 2));
         h.smem = std::max(h.smem, (size_t)STENCIL3D_STAGES * (rows_per_tile + 2) * (nch + 2) * 16);
+    } else if (variant == 3) {
+        // the variant-1 tiles, planes staged by TMA: a box row of nch + 2 chunks holds at most 256
+        // elements; stages padded to 128 bytes, plus 128 bytes to align the ring
+        threads = threads == 512 ? 512 : 256;
+        const int64_t slot_cap = threads == 512 ? 704 : 2 * threads;
+        const int64_t chunks = (W.hi[2] - xb0 + VEC - 1) / VEC;
+        const int64_t cap = std::max<int64_t>(1, std::min<int64_t>({(int64_t)band_chunks, (int64_t)threads,
+                                                                    slot_cap / 3 - 2, (int64_t)(256 / VEC - 2)}));
+        const int64_t nb = (chunks + cap - 1) / cap;
+        const int64_t nch = (chunks + nb - 1) / nb;
+        band = nch * VEC;
+        rows_per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(threads / nch, slot_cap / (nch + 2) - 2));
+        const int64_t slots = ((rows_per_tile + 2) * (nch + 2) + 7) / 8 * 8;
+        h.smem = std::max(h.smem, (size_t)STENCIL3D_STAGES * slots * 16 + 128);
+        h.parts.back().rwb = (int32_t)(nch + 2);
+        h.parts.back().boxh = (int32_t)(rows_per_tile + 2);
+        CUtensorMap m;
+        if (!encode_box_map(X, bx, (int)((nch + 2) * VEC), rows_per_tile + 2, &m)) h.map_error = true;
+        h.maps.push_back(m);
     }
     if (flat_cells > 0) {
         const int64_t width = W.hi[2] - W.lo[2];
@@ -1172,6 +1222,7 @@ int compile_plan(Plan &pl)
             for (StenTile3D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
             if (sx) add_moves(*sx);
         }
+        if (h.map_error) return HDARRAY_ERR_CUDA;
         if (!plain && g->snake && X->uid > Y->uid) std::reverse(h.tiles.begin(), h.tiles.end());
         blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart3D)});
@@ -1181,6 +1232,7 @@ int compile_plan(Plan &pl)
         const bool alternate = !plain && g->snake && !h.tiles.empty();
         if (alternate) rtiles.assign(h.tiles.rbegin(), h.tiles.rend());
         blobs.push_back({rtiles.data(), rtiles.size() * sizeof(StenTile3D)});
+        blobs.push_back({h.maps.data(), h.maps.size() * sizeof(CUtensorMap)});  // 128 bytes each
         std::vector<const char *> addr;
         int rc = upload(blobs, pl.tables, addr);
         if (rc) return rc;
@@ -1194,7 +1246,7 @@ int compile_plan(Plan &pl)
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
-                L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3];
+                L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3]; L.p3 = addr[5];
                 L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
@@ -1205,7 +1257,7 @@ int compile_plan(Plan &pl)
             }
             if (!h.tiles.empty()) {
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
-                L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
+                L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3]; L.p3 = addr[5];
                 if (alternate) L.p1_alt = addr[4];
                 L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
@@ -1712,9 +1764,11 @@ int compile_tuned(Plan &pl)
     if (threed) {
         for (int fu : {1, 0})
             for (int tz : {16, 32, 64}) {
-                for (int band : {16, 32, 64})
-                    for (int cta : {256, 512})
-                        cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, 1, band, cta, saved.band2});
+                for (int v3 : {1, 3})
+                    for (int band : {16, 32, 64})
+                        for (int cta : {256, 512})
+                            cands.push_back(Ctx::Shape{saved.variant, saved.rows, saved.warps, tz, fu, v3, band, cta,
+                                                       saved.band2});
                 if (flat_ok)
                     for (int cells : {16, 32})
                         cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3,
@@ -2601,7 +2655,7 @@ int init_impl(int ndev, unsigned flags)
         const char *fx = getenv("HDARRAY_FUSE_EXCHANGE");
         if (fx) g->fuse = atoi(fx) != 0;
         const char *v3 = getenv("HDARRAY_STENCIL3D_VARIANT");
-        if (v3 && atoi(v3) >= 0 && atoi(v3) <= 2) g->variant3 = atoi(v3);
+        if (v3 && atoi(v3) >= 0 && atoi(v3) <= 3) g->variant3 = atoi(v3);
         const char *tz = getenv("HDARRAY_TILE_Z");
         if (tz && atoi(tz) > 0) g->tile_z = atoi(tz);
         const char *sl = getenv("HDARRAY_SPIN_LIMIT");
@@ -2693,7 +2747,8 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_STENCIL3D:
         return launch_stencil3d(L.dtype, (const StenPart3D *)L.p0, (const StenTile3D *)L.p1, (int)L.n0,
-                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
+                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s, L.p3, g->err_word,
+                                g->spin_limit);
     case L_SQDIFF: {
         char *red = (char *)const_cast<void *>(L.p1);
         unsigned *counter = red ? (unsigned *)(red + red_counter_offset(L.n1)) : nullptr;

@@ -1,6 +1,7 @@
 // runtime.h -- internal structures of the HDArray runtime (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,6 +111,8 @@ struct Sten3DHost {
     std::vector<StenPart3D> parts;
     std::vector<StenTile3D> tiles;
     std::vector<Seg> segs;
+    std::vector<CUtensorMap> maps;  // TMA variant: one per part (its X buffer)
+    bool map_error = false;
 };
 
 struct ArrStep {

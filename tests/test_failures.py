@@ -85,3 +85,45 @@ def test_misaligned_allocation_is_rejected(gpu):
     with pytest.raises(H.HDArrayError) as e:
         H.HDArrayWrite(X, np.zeros((64, 64), np.float32), D)
     assert e.value.code == INVAL
+
+
+@pytest.mark.gpu
+def test_stencil3d_bulk_copy_wait_timeout_is_reported(gpu, monkeypatch):
+    """The 3-D kernel whose planes arrive by bulk tensor copies: with a limit of zero polls every
+    wait on a plane gives up, the tiles compute nothing, the copies already issued are waited for,
+    and the call reports HDARRAY_ERR_TIMEOUT once; then the context computes correctly."""
+    import oracle
+    monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", "3")
+    n = 34
+    boxes = synthetic.kd_boxes(n, 5, stream=87, min_ext=6, max_ext=34)
+    work = [(tuple(max(1, v) for v in lo), tuple(min(n - 1, v) for v in hi)) for lo, hi in boxes]
+    x = synthetic.jacobi_field((n, n, n), stream=88, dtype="float")
+
+    def program():
+        B = H.HDArrayCreate("B", "float", None, n, n, n)
+        A = H.HDArrayCreate("A", "float", None, n, n, n)
+        D = H.HDArrayPartitionManual((n, n, n), boxes)
+        W = H.HDArrayPartitionManual((n, n, n), work)
+        H.HDArrayWrite(B, x, D)
+        H.HDArrayApplyKernel("stencil3d", W, B, A)
+        return A, D
+
+    monkeypatch.setenv("HDARRAY_SPIN_LIMIT", "0")
+    H.HDArrayInit(ndev=len(boxes))
+    program()
+    with pytest.raises(H.HDArrayError) as e:
+        H.HDArraySync()
+    assert e.value.code == TIMEOUT
+    H.HDArraySync()  # reported once
+    H.HDArrayExit()
+    monkeypatch.delenv("HDARRAY_SPIN_LIMIT")
+    H.HDArrayInit(ndev=len(boxes))
+    A, D = program()
+    got = np.zeros((n, n, n), np.float32)
+    H.HDArrayRead(A, got, D)
+    o = oracle.Oracle(len(boxes))
+    ob, oa = o.create("B", "float", (n, n, n)), o.create("A", "float", (n, n, n))
+    od = o.partition_manual(boxes)
+    o.write(ob, x, od)
+    o.apply("stencil3d", o.partition_manual(work), [ob, oa])
+    assert np.array_equal(got, oa.G)

@@ -612,12 +612,14 @@ def test_stencil3d_wide_rows(gpu_lib):
     assert np.array_equal(got, orc.arrays["A"].G)
 
 
-@pytest.mark.parametrize("tile_z", [None, "32"])
-def test_full_size_stencil3d_512_37_boxes(gpu_lib, tile_z, monkeypatch):
+@pytest.mark.parametrize("tile_z,variant", [(None, None), ("32", None), ("32", "3")])
+def test_full_size_stencil3d_512_37_boxes(gpu_lib, tile_z, variant, monkeypatch):
     """512^3 on the 37 k-d boxes, 50 iterations in a graph, with the default tile depth and the
-    one bench.py's autotuner picks (32 planes)."""
+    one bench.py's autotuner picks (32 planes), planes staged by cp.async or by bulk tensor copies."""
     if tile_z:
         monkeypatch.setenv("HDARRAY_TILE_Z", tile_z)
+    if variant:
+        monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", variant)
     n, T = 512, 50
     boxes = synthetic.kd_boxes(n, 37, stream=3)
     x = synthetic.jacobi_field((n, n, n), stream=3, dtype="float")
@@ -798,7 +800,10 @@ def test_jacobi2d_packed_narrow(gpu_lib, monkeypatch, dims, P, ptype, dtype, ban
                                        ({"HDARRAY_STENCIL3D_VARIANT": "0"}, "float"), ({"HDARRAY_TILE_Z": "7"}, "float"),
                                        ({"HDARRAY_STENCIL3D_VARIANT": "2"}, "float"),
                                        ({"HDARRAY_STENCIL3D_VARIANT": "2", "HDARRAY_TILE_ROWS": "1"}, "double"),
-                                       ({"HDARRAY_STENCIL3D_VARIANT": "2", "HDARRAY_TILE_Z": "5"}, "float")])
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "2", "HDARRAY_TILE_Z": "5"}, "float"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "3"}, "float"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "3", "HDARRAY_TILE_Z": "7"}, "double"),
+                                       ({"HDARRAY_STENCIL3D_VARIANT": "3", "HDARRAY_FUSE_EXCHANGE": "0"}, "bf16")])
 def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -812,15 +817,21 @@ def test_stencil3d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     assert np.array_equal(got, orc.arrays[last].G)
 
 
-@pytest.mark.parametrize("band,dtype,cta", [("1", "float", "256"), ("4", "float", "256"), ("16", "float", "256"),
-                                            ("64", "float", "256"), ("3", "bf16", "256"), ("64", "bf16", "256"),
-                                            ("5", "double", "256"), ("64", "double", "256"), ("1", "float", "512"),
-                                            ("32", "float", "512"), ("512", "float", "512"), ("7", "bf16", "512"),
-                                            ("64", "double", "512")])
-def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype, cta):
-    """The CTA kernel's tiles follow the box: narrow bands with many rows, wide bands with few,
-    bands of equal width across a row, ragged last tiles in y and z, with 256 or 512 threads."""
-    monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", "1")
+BAND_SHAPES = [("1", "float", "256"), ("4", "float", "256"), ("16", "float", "256"), ("64", "float", "256"),
+               ("3", "bf16", "256"), ("64", "bf16", "256"), ("5", "double", "256"), ("64", "double", "256"),
+               ("1", "float", "512"), ("32", "float", "512"), ("512", "float", "512"), ("7", "bf16", "512"),
+               ("64", "double", "512")]
+
+
+@pytest.mark.parametrize("variant", ["1", "3"])
+@pytest.mark.parametrize("band,dtype,cta", BAND_SHAPES)
+def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype, cta, variant):
+    """The CTA kernels' tiles follow the box: narrow bands with many rows, wide bands with few,
+    bands of equal width across a row (the last one narrower), ragged last tiles in y and z, with
+    256 or 512 threads; the planes staged by cp.async (variant 1) or by bulk tensor copies of a box
+    per plane (variant 3, whose boxes of a part's ragged tiles reach past the buffer and read
+    zeros)."""
+    monkeypatch.setenv("HDARRAY_STENCIL3D_VARIANT", variant)
     monkeypatch.setenv("HDARRAY_BAND3", band)
     monkeypatch.setenv("HDARRAY_CTA3", cta)
     monkeypatch.setenv("HDARRAY_TILE_Z", "9")
@@ -843,7 +854,7 @@ def test_stencil3d_cta_band_shapes(gpu_lib, monkeypatch, band, dtype, cta):
     assert np.array_equal(got.view(np.uint8), orc.arrays[a].G.view(np.uint8))
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
 def test_stencil3d_special_values(gpu_lib, monkeypatch, variant):
     """Sums outside the fast division's range -- subnormal and tiny values, infinities, signed
     zeros -- are divided exactly as IEEE division does (bit-exact against the oracle's s / 6)."""
