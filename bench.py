@@ -82,7 +82,8 @@ def profiled(name, key, sources):
 
 
 KERNEL_NAMES_2D = {0: "k_jacobi2d<f32,6> (register ring)", 1: "k_jacobi2d_async<f32,8> (cp.async ring)",
-                   2: "k_jacobi2d_flat<f32>", 3: "k_jacobi2d_cta<f32,8> (packed row streams)"}
+                   2: "k_jacobi2d_flat<f32>", 3: "k_jacobi2d_cta<f32,8> (packed row streams)",
+                   5: "k_jacobi2d_tma<f32,4,4> (rows staged by bulk tensor copies)"}
 
 
 def jacobi_variant(tuned):

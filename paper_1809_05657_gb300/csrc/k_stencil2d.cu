@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
         A out[VEC];
         A cl, cr;
         ends(e, cv, cl, cr);
-        if (OP == OP_JACOBI) {
+        if constexpr (OP == OP_JACOBI) {
 #pragma unroll
             for (int k = 0; k < VEC; k++) {
                 const A wv = k > 0 ? cv[k - 1] : cl;
@@ -342,22 +342,32 @@ __global__ void __launch_bounds__(256, 4) k_jacobi2d_cta(const StenPart2D *__res
         }
     };
 
-    for (int k = 0; k < SL; k += 2) {
+    // A step computes output rows r_s + k and r_s + k + 1 from entries k .. k+3.  Entries k and
+    // k + 1 are the previous step's k + 2 and k + 3, still unpacked in registers, so every entry
+    // is read from shared memory and unpacked once; the loop body is two steps with the four row
+    // register sets exchanging roles, so no values move between registers.
+    auto step = [&](int k, A (&e0)[VEC], A (&e1)[VEC], A (&e2)[VEC], A (&e3)[VEC], bool first) {
         cpa_wait<NS - 6>();  // entries up to k + 3 have landed (this thread's copies)
         __syncthreads();     // ... and every other thread's; the stages of k-2 and k-1 are free
         issue();             // entry k + NS - 2
         issue();             // entry k + NS - 1
-        A up[VEC], cv[VEC], dn[VEC];
-        ld(k, up);
-        ld(k + 1, cv);
-        ld(k + 2, dn);
-        row(k + 1, up, cv, dn, yp, k < len);  // output row r_s + k
+        if (first) {
+            ld(k, e0);
+            ld(k + 1, e1);
+        }
+        ld(k + 2, e2);
+        row(k + 1, e0, e1, e2, yp, k < len);  // output row r_s + k
         if (k + 1 < SL) {                     // output row r_s + k + 1
-            A dn2[VEC];
-            ld(k + 3, dn2);
-            row(k + 2, cv, dn, dn2, yp + P.ys, k + 1 < len);
+            ld(k + 3, e3);
+            row(k + 2, e1, e2, e3, yp + P.ys, k + 1 < len);
         }
         yp += 2 * P.ys;
+    };
+    A ra[VEC], rb[VEC], rc[VEC], rd[VEC];
+    step(0, ra, rb, rc, rd, true);
+    for (int k = 2; k < SL; k += 4) {
+        step(k, rc, rd, ra, rb, false);
+        if (k + 2 < SL) step(k + 2, ra, rb, rc, rd, false);
     }
     cpa_wait<0>();
 }
@@ -383,6 +393,187 @@ cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, con
         attr[op][which] = true;
     }
     fns[op][which]<<<ntiles, 256, smem, s>>>(parts, tiles, slots, segs, weights);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// The Jacobi step with its rows staged by the tensor memory accelerator.  A tile is a column band
+// of nch 16-byte chunks by rows r0 .. r1 - 1 of one device, cut into stages of SR = ns * M output
+// rows.  Stage j is one box of the part's 2-D tensor map: the SR + 2 buffer rows
+// r0 - 1 + j * SR .. r0 + (j + 1) * SR (both halo rows included) by rwb chunks (the band with one
+// halo chunk on each side), brought by a single bulk tensor copy (cp.async.bulk.tensor.2d) that
+// thread 0 issues into a ring of NS stages and that completes a transaction-count mbarrier.
+// Thread (g, c) computes chunk c of the M consecutive output rows g * M .. g * M + M - 1 of every
+// stage: it reads its M + 2 staged rows from shared memory once each, the three-row window sliding
+// down in registers, and the copies cost the computing threads no instructions.  Horizontal
+// neighbours come by shuffle, or from the staged halo chunks, which every box holds (coordinates
+// outside the buffer read zeros, never used by an output).  Before its first copy the tile copies
+// its receive segments -- the parts of the sections its device receives in this call (Eq. 1-2)
+// that only this tile reads -- from the senders' buffers into its own, and every thread fences
+// those generic stores to the async proxy.  Waits are bounded: after spin_limit polls a wait gives
+// up, the tile stops, thread 0 waits (with a fixed limit) for the copies it issued and the error
+// word is set.
+// ------------------------------------------------------------------------------------------
+template <int DT, int NS, int M>
+__global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__restrict__ parts,
+                                                         const StenTile2D *__restrict__ tiles,
+                                                         const Seg *__restrict__ segs,
+                                                         const uint8_t *__restrict__ tmaps, unsigned *err,
+                                                         unsigned spin_limit)
+{
+    static_assert((NS & (NS - 1)) == 0 && NS >= 2, "ring depth: a power of two");
+    using EL = Elem<DT>;
+    using E = typename EL::E;
+    using A = typename EL::A;
+    using V = typename EL::V;
+    constexpr int VEC = EL::VEC;
+    extern __shared__ uint4 smem_dyn[];
+    __shared__ __align__(8) uint64_t full[NS];
+    const int lane = threadIdx.x & 31;
+    const StenTile2D t = tiles[blockIdx.x];
+    const StenPart2D P = parts[t.part];
+    // the ring starts on a 128-byte boundary (the launch adds 128 bytes of slack)
+    const uint32_t ring_s = (smem_addr(smem_dyn) + 127u) & ~127u;
+    const char *ring = reinterpret_cast<const char *>(smem_dyn) + (ring_s - smem_addr(smem_dyn));
+
+    if (t.nseg > 0) receive_flat_vec<E>(segs, t.seg0, t.nseg, threadIdx.x, blockDim.x);
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // the receive's stores, before bulk copies read them
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int nch = t.nch, G = t.ns, rw = P.rwb;  // chunks computed, row groups, staged row width
+    const int SR = G * M;                          // output rows per stage
+    const int S = (t.r1 - t.r0 + SR - 1) / SR;     // stages of the tile
+    const uint32_t box_bytes = (uint32_t)(SR + 2) * (uint32_t)rw * 16u;
+    const uint32_t stage_bytes = (box_bytes + 127u) & ~127u;
+    const uint8_t *tmap = tmaps + (size_t)t.part * 128;
+    const int xc = (int)(t.cb - VEC - P.xlo1), yc = (int)(t.r0 - 1 - P.xlo0);
+    int issued = 0;  // thread 0: stages issued so far
+    auto issue = [&](int j) {
+        if (j >= S) return;
+        const uint32_t bar = smem_addr(&full[j & (NS - 1)]);
+        const uint32_t dst = ring_s + (uint32_t)(j & (NS - 1)) * stage_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(box_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+            "l"(tmap), "r"(xc), "r"(yc + j * SR), "r"(bar)
+            : "memory");
+        issued = j + 1;
+    };
+    if (threadIdx.x == 0)
+        for (int j = 0; j < NS; j++) issue(j);
+
+    // this thread: row group gi (output rows gi * M .. of every stage), chunk c
+    const int gi = threadIdx.x / nch, c = threadIdx.x - gi * nch;
+    const bool act = gi < G;
+    const int x = t.cb + c * VEC;
+    const bool full_chunk = x >= t.c0 && x + VEC <= t.c1;
+    const bool shflL = c > 0 && lane > 0, shflR = c < nch - 1 && lane < 31;
+    const int me = gi * M * rw + c + 1;  // slot of the thread's chunk in its first staged row
+    E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.r0 + gi * M - P.ylo0) * P.ys + (x - P.ylo1);
+
+    bool failed = false;
+    for (int j = 0; j < S; j++) {
+        const bool ok = mbar_wait_bounded(smem_addr(&full[j & (NS - 1)]), (uint32_t)((j / NS) & 1), spin_limit);
+        // every thread is done with stage j - 1; a failed wait anywhere stops every thread
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (threadIdx.x == 0 && j > 0) issue(j - 1 + NS);
+        const uint4 *sp = reinterpret_cast<const uint4 *>(ring + (size_t)(j & (NS - 1)) * stage_bytes) + me;
+        const int rbase = t.r0 + j * SR + gi * M;  // the thread's first output row in this stage
+        A rows[M + 2][VEC];
+#pragma unroll
+        for (int q = 0; q < M + 2; q++) {
+            if (act) {
+                EL::unpack(*reinterpret_cast<const V *>(sp + q * rw), rows[q]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; k++) rows[q][k] = A(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < M; u++) {
+            const A(&up)[VEC] = rows[u];
+            const A(&cv)[VEC] = rows[u + 1];
+            const A(&dn)[VEC] = rows[u + 2];
+            A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
+            A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
+            const E *crow = reinterpret_cast<const E *>(sp + (u + 1) * rw);
+            if (!shflL && act) left = EL::load1(crow - 1);
+            if (!shflR && act) right = EL::load1(crow + VEC);
+            A out[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; k++) {
+                const A wv = k > 0 ? cv[k - 1] : left;
+                const A ev = k < VEC - 1 ? cv[k + 1] : right;
+                A sum = wv + ev;
+                sum = sum + up[k];
+                sum = sum + dn[k];
+                out[k] = sum * A(0.25);
+            }
+            if (act && rbase + u < t.r1) {
+                E *op = yp + (int64_t)(j * SR + u) * P.ys;
+                if (full_chunk) {
+                    *reinterpret_cast<V *>(op) = EL::pack(out);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < VEC; k++)
+                        if (x + k >= t.c0 && x + k < t.c1) EL::store1(op + k, out[k]);
+                }
+            }
+        }
+    }
+    if (failed && threadIdx.x == 0) {
+        // the copies issued land before the CTA's shared memory is released: the last one of each
+        // stage completes that stage's latest phase
+        for (int j = issued - 1; j >= 0 && j >= issued - NS; j--)
+            mbar_wait_bounded(smem_addr(&full[j & (NS - 1)]), (uint32_t)((j / NS) & 1), TMA_DRAIN_LIMIT);
+        if (err) atomicOr(err, 1u);
+    }
+}
+
+int jacobi2d_tma_ctas_per_sm(int dtype, size_t smem)
+{
+    constexpr int NS = JACOBI2D_TMA_STAGES, M = JACOBI2D_TMA_ROWS;
+    const void *fn = dtype == DT_F64 ? (const void *)k_jacobi2d_tma<DT_F64, NS, M>
+                     : dtype == DT_F32 ? (const void *)k_jacobi2d_tma<DT_F32, NS, M>
+                                       : (const void *)k_jacobi2d_tma<DT_BF16, NS, M>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
+
+cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
+                                unsigned spin_limit)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    constexpr int NS = JACOBI2D_TMA_STAGES, M = JACOBI2D_TMA_ROWS;
+    if (!tmaps || smem < 128 || smem > JACOBI2D_TMA_SMEM_MAX) return cudaErrorInvalidValue;
+    const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
+    if (which < 0) return cudaErrorInvalidValue;
+    using KFn = void (*)(const StenPart2D *, const StenTile2D *, const Seg *, const uint8_t *, unsigned *, unsigned);
+    const KFn fns[3] = {k_jacobi2d_tma<DT_F64, NS, M>, k_jacobi2d_tma<DT_F32, NS, M>, k_jacobi2d_tma<DT_BF16, NS, M>};
+    static bool attr[3] = {};
+    if (!attr[which]) {
+        cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr[which] = true;
+    }
+    fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, segs, reinterpret_cast<const uint8_t *>(tmaps), err, spin_limit);
     return cudaGetLastError();
 }
 

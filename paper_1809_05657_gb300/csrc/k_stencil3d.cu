@@ -251,30 +251,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_cta(const StenPart3D 
 // spin_limit polls a wait gives up, the tile computes nothing, thread 0 waits (with a fixed limit)
 // for the copies it issued and the error word is set.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned limit)
-{
-    for (unsigned i = 0; i < limit; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        __nanosleep(32);
-    }
-    return false;
-}
-
-constexpr unsigned TMA_DRAIN_LIMIT = 1u << 22;  // polls when draining after a failed wait
 
 template <int DT, int NS, int T>
 __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D *__restrict__ parts,
@@ -291,7 +267,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D 
     constexpr int VEC = EL::VEC;
     extern __shared__ uint4 smem_dyn[];
     __shared__ __align__(8) uint64_t full[NS];
-    __shared__ int fail;
     const int lane = threadIdx.x & 31;
     const StenTile3D t = tiles[blockIdx.x];
     const StenPart3D P = parts[t.part];
@@ -306,7 +281,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D 
         for (int s = 0; s < NS; s++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[s])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fail = 0;
     }
     __syncthreads();
 
@@ -385,14 +359,18 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D 
         }
     };
 
+    bool failed = false;
     for (int k = 0; k < L; k += 2) {
         // entries k .. k+3 must have landed; the earlier ones were waited for in earlier steps
         bool ok = true;
         for (int e = k == 0 ? 0 : k + 2; e <= k + 3 && e <= L + 1; e++)
             ok = ok && mbar_wait_bounded(smem_addr(&full[e & (NS - 1)]), (uint32_t)((e / NS) & 1), spin_limit);
-        if (!ok) fail = 1;
-        __syncthreads();  // every thread is done with the stages of entries k-2 and k-1
-        if (fail) break;  // the same for every thread after the barrier
+        // every thread is done with the stages of entries k-2 and k-1; a failed wait anywhere
+        // stops every thread
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
         if (threadIdx.x == 0) {
             issue(k + NS - 2);
             issue(k + NS - 1);
@@ -409,7 +387,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_stencil3d_tma(const StenPart3D 
         }
         yp += 2 * P.ys0;
     }
-    if (fail && threadIdx.x == 0) {
+    if (failed && threadIdx.x == 0) {
         // the copies issued land before the CTA's shared memory is released: the last one of each
         // stage completes that stage's latest phase
         for (int e = issued - 1; e >= 0 && e >= issued - NS; e--)

@@ -41,6 +41,8 @@ struct StenPart2D {
     void *y;        // Y buffer (defined array) of this device
     int64_t xlo0, xlo1, xs;  // X buffer origin (row, col) and row stride in elements
     int64_t ylo0, ylo1, ys;
+    int32_t rwb;  // TMA variant: width of the part's staged rows in 16-byte chunks (band + 2 halo chunks)
+    int32_t pad_;
 };
 struct StenTile2D {
     int32_t part;
@@ -48,7 +50,8 @@ struct StenTile2D {
     int32_t c0, c1;
     int32_t cb;
     int32_t seg0, nseg;
-    int32_t nch, ns, sl;  // packed-stream variant: chunks per row, streams, rows per stream
+    int32_t nch, ns, sl;  // packed-stream variant: chunks per row, streams, rows per stream;
+                          // TMA variant: chunks per row, row groups of JACOBI2D_TMA_ROWS rows
 };
 struct Seg {  // dst[o * dso + k * ds] = src[o * sso + k * ss], k < n, o < m (element strides)
     const void *src;
@@ -65,6 +68,22 @@ constexpr int JACOBI2D_STAGES = 8;
 cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D *tiles,
                             int ntiles, const Seg *segs, int warps_per_cta, int variant, size_t smem,
                             cudaStream_t s);
+// variant 5: a CTA of 256 threads per tile of nch chunks x rows r0 .. r1 - 1, cut into stages of
+// ns * JACOBI2D_TMA_ROWS output rows (ns * nch <= 256), each stage one bulk tensor copy of its rows
+// and the two halo rows by the part's rwb chunks into a ring of JACOBI2D_TMA_STAGES stages (each
+// padded to 128 bytes; smem = the ring + 128 bytes of alignment slack, at most
+// JACOBI2D_TMA_SMEM_MAX).  tmaps holds one 128-byte CUtensorMap per part (its X buffer, box
+// rwb * 16 bytes x (ns * rows + 2)); err receives a set bit when a bounded wait gave up after
+// spin_limit polls.  jacobi2d_tma_ctas_per_sm: how many such CTAs one SM holds at once.
+constexpr int JACOBI2D_TMA_STAGES = 4;
+constexpr int JACOBI2D_TMA_ROWS = 4;
+constexpr int JACOBI2D_TMA_THREADS = 256;
+constexpr int JACOBI2D_TMA_STAGE_MAX = 20 * 1024;  // largest stage the tile planner makes
+constexpr int JACOBI2D_TMA_SMEM_MAX = JACOBI2D_TMA_STAGES * (JACOBI2D_TMA_STAGE_MAX + 128) + 128;
+int jacobi2d_tma_ctas_per_sm(int dtype, size_t smem);
+cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
+                                unsigned spin_limit);
 // The packed-stream kernel with a chosen point operation: op 0 the Jacobi step, op 1 the 3 x 3
 // convolution with weights[9] (device memory, binary64, row-major over the offsets
 // (-1,-1) (-1,0) (-1,1) (0,-1) ... (1,1)).

@@ -98,7 +98,8 @@ struct Ctx {
     // tunables
     int tile_rows = 32;     // 2-D tile height (rows per warp)
     int warps_per_cta = 8;  // 2-D warps per CTA
-    int variant = 0;        // 2-D kernel variant (0 registers, 1 cp.async ring, 2 flat, 3 packed streams)
+    int variant = 0;        // 2-D kernel variant (0 registers, 1 cp.async ring, 2 flat, 3 packed streams,
+                            // 4 adaptive, 5 rows staged by bulk tensor copies)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
     int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
     int band2 = 32;         // 2-D packed-stream variant: most 16-byte chunks per band
@@ -743,16 +744,47 @@ void tile2d_segments(const HDArray *X, const DevBuf &bx, StenTile2D &t, const st
     }
 }
 
+bool encode_row_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUtensorMap *out);
+
+// Shape of the TMA 2-D kernel's tiles on one device's work box W: bands of equal width of at most
+// band_chunks 16-byte chunks whose staged rows (band + 2 halo chunks) hold at most 256 elements;
+// G row groups of JACOBI2D_TMA_ROWS rows per stage, so that G * nch <= 256 and a stage (its SR
+// rows and 2 halo rows) holds at most JACOBI2D_TMA_STAGE_MAX bytes.
+struct Tma2DGeom {
+    int64_t cb0, nb, nch, rw, G, SR, S;  // first band column, bands, chunks per band, staged row
+                                         // width, row groups, rows per stage, stages down a band
+    size_t stage;                        // bytes of a stage, padded to 128
+};
+Tma2DGeom tma2d_geometry(const HDArray *X, const DevBuf &bx, const Box &W, int band_chunks)
+{
+    Tma2DGeom q;
+    const int VEC = 16 / X->esize, M = JACOBI2D_TMA_ROWS;
+    q.cb0 = bx.alloc.lo[1] + align_down(W.lo[1] - bx.alloc.lo[1], VEC);
+    const int64_t chunks = (W.hi[1] - q.cb0 + VEC - 1) / VEC;
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(band_chunks, 256 / VEC - 2));
+    q.nb = (chunks + cap - 1) / cap;
+    q.nch = (chunks + q.nb - 1) / q.nb;
+    q.rw = q.nch + 2;
+    q.G = std::max<int64_t>(1, std::min<int64_t>({JACOBI2D_TMA_THREADS / q.nch, (int64_t)(254 / M),
+                                                  (JACOBI2D_TMA_STAGE_MAX / (16 * q.rw) - 2) / M}));
+    q.SR = q.G * M;
+    q.S = (W.hi[0] - W.lo[0] + q.SR - 1) / q.SR;
+    q.stage = ((size_t)(q.SR + 2) * (size_t)q.rw * 16 + 127) / 128 * 128;
+    return q;
+}
+
 // Tiles of the fused 2-D kernel for one device.  Warp variants (0, 1): column bands of 32 chunks
 // x tile_rows rows, a warp each.  Packed-stream variant (3): the box's chunks cut into bands of
 // equal width of at most band_chunks (<= 32); per band, tiles of ns streams x sl rows with
 // ns = min(256 / nch, 340 / (nch + 2)) and sl about tile_rows, balanced over the band's rows.
+// TMA variant (5): the bands and stages of tma2d_geometry; tiles of whole stages, about
+// 8 * tile_rows rows; one tensor map per part.
 bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                   const std::vector<Move> &recv, bool want_segs, Sten2DHost &h, int variant = 1,
                   int band_chunks = 32, bool corners = false)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
-    StenPart2D P;
+    StenPart2D P{};
     P.x = bx.ptr;
     P.y = by.ptr;
     P.xlo0 = bx.alloc.lo[0];
@@ -782,6 +814,36 @@ bool jacobi_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
     // with corners every move outside W lies in the 1-ring of W, which the tiles' strips cover
     // (some cells more than once), so the fused form is exact iff no move reaches into W
     auto result = [&]() { return exact && (corners || covered == need); };
+    if (variant == 5) {
+        const Tma2DGeom q = tma2d_geometry(X, bx, W, band_chunks);
+        const int64_t nb = q.nb, nch = q.nch, rw = q.rw, G = q.G, SR = q.SR;
+        // tiles of whole stages, about 8 * tile_rows rows (only a band's last tile ends in a partial stage)
+        const int64_t spt = std::max<int64_t>(1, (8 * (int64_t)H + SR / 2) / SR);
+        const int64_t hr = spt * SR;
+        h.smem = std::max(h.smem, (size_t)JACOBI2D_TMA_STAGES * q.stage + 128);
+        h.parts.back().rwb = (int32_t)rw;
+        CUtensorMap m;
+        // a box's x coordinate (cb - VEC, from the buffer's first column) lies on a 16-byte boundary
+        if ((cb0 - VEC - bx.alloc.lo[1]) % VEC != 0 || !encode_row_map(X, bx, (int)(rw * VEC), (int)(SR + 2), &m))
+            h.map_error = true;
+        h.maps.push_back(m);
+        for (int64_t rb = W.lo[0]; rb < W.hi[0]; rb += hr) {
+            for (int64_t b = 0; b < nb; b++) {
+                const int64_t cb = cb0 + b * nch * VEC;
+                StenTile2D t;
+                t.r0 = (int32_t)rb;
+                t.r1 = (int32_t)std::min<int64_t>(rb + hr, W.hi[0]);
+                t.c0 = (int32_t)std::max<int64_t>(W.lo[1], cb);
+                t.c1 = (int32_t)std::min<int64_t>(W.hi[1], cb + nch * VEC);
+                t.cb = (int32_t)cb;
+                t.nch = (int32_t)((t.c1 - cb + VEC - 1) / VEC);
+                t.ns = (int32_t)G;
+                t.sl = JACOBI2D_TMA_ROWS;
+                add(t);
+            }
+        }
+        return result();
+    }
     if (variant == 3) {
         const int64_t chunks = (W.hi[1] - cb0 + VEC - 1) / VEC;
         const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(band_chunks, 32));
@@ -836,7 +898,7 @@ bool flat2d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int p
                   const std::vector<Move> &recv, bool want_segs, int cells, Sten2DHost &h)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
-    StenPart2D P;
+    StenPart2D P{};
     P.x = bx.ptr; P.y = by.ptr;
     P.xlo0 = bx.alloc.lo[0]; P.xlo1 = bx.alloc.lo[1]; P.xs = bx.st[0];
     P.ylo0 = by.alloc.lo[0]; P.ylo1 = by.alloc.lo[1]; P.ys = by.st[0];
@@ -918,14 +980,12 @@ void box_segments(const HDArray *a, const DevBuf &src, const DevBuf &dst, const 
     out.push_back(sg);
 }
 
-// Tiles of the fused 3-D kernel for one device, in (z chunk, x band, rows) order; the receive
-// segments are the parts of the incoming faces on the tile's six face strips.  variant 0: bands
-// of 32 chunks, one row per tile; variant 1: the box's chunks cut into bands of equal width of
-// at most band_chunks, as many rows per tile as `threads` threads hold; variant 2 (flat_cells > 0):
-// balanced widths up to 128 elements, rows so that a plane has about flat_cells cells.
-// A 3-D tensor map over device buffer b of X for tile boxes of box_w elements x box_h rows x one
-// plane (the driver's encoder, found through the runtime; nothing links the driver library).
-bool encode_box_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUtensorMap *out)
+// A tiled tensor map of `rank` dimensions (innermost first) over device buffer b of X, through the
+// driver's encoder (found through the runtime; nothing links the driver library).  The checks are
+// the encoder's documented rules: a 16-byte aligned base, strides in multiples of 16 bytes, boxes
+// of 1 .. 256 elements per dimension with a whole number of 16-byte units in the inner one.
+bool encode_tiled(const HDArray *X, const DevBuf &b, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
+                  const cuuint32_t *box, CUtensorMap *out)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -941,23 +1001,47 @@ bool encode_box_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUt
     const CUtensorMapDataType dt = X->dtype == DT_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                    : X->dtype == DT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (((uintptr_t)b.ptr & 15) != 0 || (box[0] * X->esize) % 16 != 0) return false;
+    for (int d = 0; d < rank; d++)
+        if (box[d] < 1 || box[d] > 256 || dims[d] < 1) return false;
+    for (int d = 0; d + 1 < rank; d++)
+        if (strides[d] % 16 != 0) return false;
+    return encode(out, dt, rank, b.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D map of a 3-D array's buffer for boxes of box_w elements x box_h rows x one plane.
+bool encode_box_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUtensorMap *out)
+{
     const cuuint64_t dims[3] = {(cuuint64_t)(b.alloc.hi[2] - b.alloc.lo[2]), (cuuint64_t)(b.alloc.hi[1] - b.alloc.lo[1]),
                                 (cuuint64_t)(b.alloc.hi[0] - b.alloc.lo[0])};
     const cuuint64_t strides[2] = {(cuuint64_t)(b.st[1] * X->esize), (cuuint64_t)(b.st[0] * X->esize)};
     const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (box_w < 1 || box_w > 256 || box_h < 1 || box_h > 256 || (box_w * X->esize) % 16 != 0) return false;
-    if (strides[0] % 16 != 0 || strides[1] % 16 != 0 || ((uintptr_t)b.ptr & 15) != 0) return false;
-    return encode(out, dt, 3, b.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return encode_tiled(X, b, 3, dims, strides, box, out);
 }
 
+// 2-D map of a 2-D array's buffer for boxes of box_w elements x box_h rows.
+bool encode_row_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUtensorMap *out)
+{
+    const cuuint64_t dims[2] = {(cuuint64_t)(b.alloc.hi[1] - b.alloc.lo[1]), (cuuint64_t)(b.alloc.hi[0] - b.alloc.lo[0])};
+    const cuuint64_t strides[1] = {(cuuint64_t)(b.st[0] * X->esize)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    return encode_tiled(X, b, 2, dims, strides, box, out);
+}
+
+// Tiles of the fused 3-D kernel for one device, in (z chunk, x band, rows) order; the receive
+// segments are the parts of the incoming faces on the tile's six face strips.  variant 0: bands
+// of 32 chunks, one row per tile; variant 1: the box's chunks cut into bands of equal width of
+// at most band_chunks, as many rows per tile as `threads` threads hold; variant 2 (flat_cells > 0):
+// balanced widths up to 128 elements, rows so that a plane has about flat_cells cells.
 bool stencil3d_tiles(const HDArray *X, const HDArray *Y, int p, const Box &W, int part_index,
                      const std::vector<Move> &recv, bool want_segs, int variant, Sten3DHost &h,
                      int flat_cells = 0, int band_chunks = 32, int threads = 256)
 {
     const DevBuf &bx = X->buf[p], &by = Y->buf[p];
-    StenPart3D P;
+    StenPart3D P{};
     P.x = bx.ptr;
     P.y = by.ptr;
     P.xlo0 = bx.alloc.lo[0]; P.xlo1 = bx.alloc.lo[1]; P.xlo2 = bx.alloc.lo[2];
@@ -1111,22 +1195,33 @@ int compile_plan(Plan &pl)
                 if (!pt.box[p].empty()) widest = std::max<int64_t>(widest, (pt.box[p].hi[1] - pt.box[p].lo[1] + VEC2) / VEC2);
             adaptive = widest < 16 ? 3 : 1;
         }
-        for (int p = 0; p < pt.nparts; p++) {
-            if (pt.box[p].empty()) continue;
-            if ((Y->buf[p].alloc.lo[1] - X->buf[p].alloc.lo[1]) % VEC2 != 0) return HDARRAY_ERR_STATE;
-            std::vector<Move> recv;
-            if (sx)
-                for (const Move &m : sx->moves)
-                    if (m.dst == p && local_move(m)) recv.push_back(m);
-            int t0 = (int)h.tiles.size();
-            const bool flat = !conv && g->variant == 2 && X->dtype != DT_BF16;
-            h.flat = flat;
-            h.variant = conv ? 3 : flat ? 2 : g->variant == 2 ? 1 : g->variant == 4 ? adaptive : g->variant;
-            h.warps = g->warps_per_cta;
-            bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
-                           : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2, conv);
-            if (!ok) fused = false;
-            dev_ranges.push_back({t0, (int)h.tiles.size()});
+        // the TMA variant falls back to the packed-stream tiles where a buffer admits no tensor map
+        const bool fuse0 = fused;
+        for (int attempt = 0; attempt < 2; attempt++) {
+            const int want = attempt ? 3 : g->variant;
+            h = Sten2DHost{};
+            h.dtype = X->dtype;
+            dev_ranges.clear();
+            idx = 0;
+            fused = fuse0;
+            for (int p = 0; p < pt.nparts; p++) {
+                if (pt.box[p].empty()) continue;
+                if ((Y->buf[p].alloc.lo[1] - X->buf[p].alloc.lo[1]) % VEC2 != 0) return HDARRAY_ERR_STATE;
+                std::vector<Move> recv;
+                if (sx)
+                    for (const Move &m : sx->moves)
+                        if (m.dst == p && local_move(m)) recv.push_back(m);
+                int t0 = (int)h.tiles.size();
+                const bool flat = !conv && want == 2 && X->dtype != DT_BF16;
+                h.flat = flat;
+                h.variant = conv ? 3 : flat ? 2 : want == 2 ? 1 : want == 4 ? adaptive : want;
+                h.warps = g->warps_per_cta;
+                bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
+                               : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2, conv);
+                if (!ok) fused = false;
+                dev_ranges.push_back({t0, (int)h.tiles.size()});
+            }
+            if (!(h.variant == 5 && h.map_error)) break;
         }
         if (!fused) {  // drop the segments: the exchange runs as copies
             h.segs.clear();
@@ -1151,11 +1246,13 @@ int compile_plan(Plan &pl)
         const bool alternate = !plain && g->snake && !h.tiles.empty();
         if (alternate) rtiles.assign(h.tiles.rbegin(), h.tiles.rend());
         blobs.push_back({rtiles.data(), rtiles.size() * sizeof(StenTile2D)});
+        blobs.push_back({h.maps.data(), h.maps.size() * sizeof(CUtensorMap)});  // 128 bytes each
         std::vector<const char *> addr;
         int rc = upload(blobs, pl.tables, addr);
         if (rc) return rc;
         const CopyTask *dx = (const CopyTask *)addr[0];
         const int kind2d = conv ? L_CONV2D : h.flat ? L_FLAT2D : L_JACOBI2D;
+        const char *p3 = h.variant == 5 ? addr[6] : addr[4];  // tensor maps, or the convolution's weights
         if (plain) {
             for (auto &gr : xfer_groups)
                 if (gr.second > gr.first) {
@@ -1164,7 +1261,7 @@ int compile_plan(Plan &pl)
                 }
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
-                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
                 L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
@@ -1175,7 +1272,7 @@ int compile_plan(Plan &pl)
                 pl.launches.push_back(L);
             }
             if (!h.tiles.empty()) {
-                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = addr[4];
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
                 if (alternate) {
                     L.p1_alt = addr[5];
@@ -1795,6 +1892,10 @@ int compile_tuned(Plan &pl)
                 for (int rows : {16, 32, 64})
                     cands.push_back(Ctx::Shape{3, rows, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
                                                band});
+            for (int band : {16, 32, 64})  // rows staged by TMA: tiles of about 8 * rows rows
+                for (int rows : {8, 16, 24})
+                    cands.push_back(Ctx::Shape{5, rows, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
+                                               band});
             if (flat_ok)
                 for (int cells : {16, 32, 64})
                     cands.push_back(Ctx::Shape{2, cells, saved.warps, saved.tile_z, fu, saved.variant3, saved.band3, saved.cta3,
@@ -2121,6 +2222,7 @@ int flush_batch()
                 h.smem = std::max(h.smem, p->s2.smem);
                 const int pbase = (int)h.parts.size(), sbase = (int)h.segs.size();
                 h.parts.insert(h.parts.end(), p->s2.parts.begin(), p->s2.parts.end());
+                h.maps.insert(h.maps.end(), p->s2.maps.begin(), p->s2.maps.end());  // TMA: one per part
                 h.segs.insert(h.segs.end(), p->s2.segs.begin(), p->s2.segs.end());
                 for (StenTile2D t : p->s2.tiles) {
                     t.part += pbase;
@@ -2137,6 +2239,7 @@ int flush_batch()
             blobs.push_back({kv.second.parts.data(), kv.second.parts.size() * sizeof(StenPart2D)});
             blobs.push_back({kv.second.tiles.data(), kv.second.tiles.size() * sizeof(StenTile2D)});
             blobs.push_back({kv.second.segs.data(), kv.second.segs.size() * sizeof(Seg)});
+            blobs.push_back({kv.second.maps.data(), kv.second.maps.size() * sizeof(CUtensorMap)});
         }
         std::shared_ptr<DevMem> mem;
         std::vector<const char *> addr;
@@ -2150,12 +2253,12 @@ int flush_batch()
         int ai = 1;
         for (auto &kv : sten) {
             LaunchRec L; L.kind = kv.second.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = kv.second.dtype;
-            L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2];
+            L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2]; L.p3 = addr[ai + 3];
             L.n0 = (int64_t)kv.second.tiles.size();
             L.n1 = kv.second.flat ? (int64_t)kv.second.smem : kv.second.warps;
             L.n2 = kv.second.variant;
             L.n3 = (int64_t)kv.second.smem;
-            ai += 3;
+            ai += 4;
             if (L.n0 > 0) ls.push_back(L);
         }
         ls.insert(ls.end(), rest.begin(), rest.end());
@@ -2641,7 +2744,7 @@ int init_impl(int ndev, unsigned flags)
         const char *wc = getenv("HDARRAY_WARPS_PER_CTA");
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
-        if (vv && atoi(vv) >= 0 && atoi(vv) <= 4) g->variant = atoi(vv);
+        if (vv && atoi(vv) >= 0 && atoi(vv) <= 5) g->variant = atoi(vv);
         const char *sn = getenv("HDARRAY_SNAKE");
         if (sn && (atoi(sn) == 0 || atoi(sn) == 1)) g->snake = atoi(sn);
         const char *ra = getenv("HDARRAY_ROW_ALIGN");
@@ -2743,6 +2846,9 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     switch (L.kind) {
     case L_COPY: return launch_copy((const CopyTask *)L.p0, (int)L.n0, s);
     case L_JACOBI2D:
+        if (L.n2 == 5)
+            return launch_jacobi2d_tma(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, g->err_word, g->spin_limit);
         return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_STENCIL3D:

@@ -96,13 +96,16 @@ struct DevMem {
 // Host copies of a fused stencil plan's tables, kept so that a batch can concatenate them.
 struct Sten2DHost {
     int dtype = 0;
-    int variant = 1;    // kernel variant of the tiles (0, 1 warp tiles; 2 flat; 3 packed streams)
+    int variant = 1;    // kernel variant of the tiles (0, 1 warp tiles; 2 flat; 3 packed streams;
+                        // 5 rows staged by bulk tensor copies)
     int warps = 8;      // warps per CTA of the warp variants
     bool flat = false;  // flat-block tiles (k_jacobi2d_flat)
-    size_t smem = 0;    // dynamic shared memory per CTA (flat and packed-stream forms)
+    size_t smem = 0;    // dynamic shared memory per CTA (flat, packed-stream and TMA forms)
     std::vector<StenPart2D> parts;
     std::vector<StenTile2D> tiles;
     std::vector<Seg> segs;
+    std::vector<CUtensorMap> maps;  // TMA variant: one per part (its X buffer)
+    bool map_error = false;
 };
 struct Sten3DHost {
     int dtype = 0;

@@ -294,6 +294,33 @@ __device__ __forceinline__ void div6_n(double (&s)[N])
     for (int k = 0; k < N; k++) s[k] = s[k] / 6.0;
 }
 
+// Transaction-count mbarriers for bulk tensor copies: a non-blocking probe of a phase, and a wait
+// that gives up after `limit` probes (the caller reports the failure instead of hanging).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+constexpr unsigned TMA_DRAIN_LIMIT = 1u << 22;  // polls when draining after a failed wait
+
 // Asynchronous global -> shared copies (cp.async) and their group waits.
 __device__ __forceinline__ void cpa16(uint32_t saddr, const void *g)
 {

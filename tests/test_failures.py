@@ -127,3 +127,43 @@ def test_stencil3d_bulk_copy_wait_timeout_is_reported(gpu, monkeypatch):
     o.write(ob, x, od)
     o.apply("stencil3d", o.partition_manual(work), [ob, oa])
     assert np.array_equal(got, oa.G)
+
+
+@pytest.mark.gpu
+def test_jacobi2d_bulk_copy_wait_timeout_is_reported(gpu, monkeypatch):
+    """The 2-D kernel whose rows arrive by bulk tensor copies: with a limit of zero polls every wait
+    on a stage gives up, the tiles compute nothing, the copies already issued are waited for, and
+    the call reports HDARRAY_ERR_TIMEOUT once; then the context computes correctly."""
+    import oracle
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "5")
+    dims, P = (200, 330), 6
+    x = synthetic.jacobi_field(dims, stream=89, dtype="float")
+
+    def program():
+        B = H.HDArrayCreate("B", "float", None, *dims)
+        A = H.HDArrayCreate("A", "float", None, *dims)
+        D = H.HDArrayPartition(H.BLOCK, dims, (0, 0), dims, P)
+        W = H.HDArrayPartition(H.BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1), P)
+        H.HDArrayWrite(B, x, D)
+        H.HDArrayApplyKernel("jacobi2d", W, B, A)
+        return A, D
+
+    monkeypatch.setenv("HDARRAY_SPIN_LIMIT", "0")
+    H.HDArrayInit(ndev=P)
+    program()
+    with pytest.raises(H.HDArrayError) as e:
+        H.HDArraySync()
+    assert e.value.code == TIMEOUT
+    H.HDArraySync()  # reported once
+    H.HDArrayExit()
+    monkeypatch.delenv("HDARRAY_SPIN_LIMIT")
+    H.HDArrayInit(ndev=P)
+    A, D = program()
+    got = np.zeros(dims, np.float32)
+    H.HDArrayRead(A, got, D)
+    o = oracle.Oracle(P)
+    ob, oa = o.create("B", "float", dims), o.create("A", "float", dims)
+    od = o.partition(oracle.BLOCK, dims, (0, 0), dims)
+    o.write(ob, x, od)
+    o.apply("jacobi2d", o.partition(oracle.BLOCK, dims, (1, 1), (dims[0] - 1, dims[1] - 1)), [ob, oa])
+    assert np.array_equal(got, oa.G)

@@ -512,16 +512,17 @@ def test_graph_replay(gpu_lib, dtype):
 # ---------------------------------------------------------------------------------------------
 
 # tile shapes: the library's defaults, and the shapes the autotuner picks for bench.py on a GB300
-TUNED_2D = {"float": {"HDARRAY_JACOBI_VARIANT": "0", "HDARRAY_TILE_ROWS": "16", "HDARRAY_WARPS_PER_CTA": "4"},
-            "bf16": {"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_TILE_ROWS": "32", "HDARRAY_WARPS_PER_CTA": "8"}}
+TUNED_2D = {"float": {"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_TILE_ROWS": "8", "HDARRAY_BAND2": "64"},
+            "bf16": {"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_TILE_ROWS": "16", "HDARRAY_BAND2": "32"}}
+TMA_2D = {"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_TILE_ROWS": "16", "HDARRAY_BAND2": "32"}
 
 
-@pytest.mark.parametrize("tuned", [False, True])
+@pytest.mark.parametrize("tuned", [False, True, "tma"])
 @pytest.mark.parametrize("dtype", ["float", "bf16"])
 def test_full_size_8192_block16_graph(gpu_lib, dtype, tuned, monkeypatch):
     """The benchmark workload (8192^2, BLOCK 4 x 4, a 2-iteration graph replayed to 100
     iterations) with the default tile shape and with the one bench.py runs after autotuning."""
-    for k, v in (TUNED_2D[dtype].items() if tuned else ()):
+    for k, v in (TMA_2D.items() if tuned == "tma" else TUNED_2D[dtype].items() if tuned else ()):
         monkeypatch.setenv(k, v)
     n, P, T = 8192, 16, 100
     dims = (n, n)
@@ -760,7 +761,13 @@ def test_gemm_bf16x3_reuses_panels(gpu_lib):
                                        ({"HDARRAY_JACOBI_VARIANT": "3"}, "float"),
                                        ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_BAND2": "3", "HDARRAY_TILE_ROWS": "5"}, "double"),
                                        ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "7"}, "bf16"),
-                                       ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_FUSE_EXCHANGE": "0"}, "float")])
+                                       ({"HDARRAY_JACOBI_VARIANT": "3", "HDARRAY_FUSE_EXCHANGE": "0"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_BAND2": "64"}, "float"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_BAND2": "3", "HDARRAY_TILE_ROWS": "5"}, "double"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "7"}, "bf16"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_TILE_ROWS": "1"}, "bf16"),
+                                       ({"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_FUSE_EXCHANGE": "0"}, "float")])
 def test_jacobi2d_execution_choices(gpu_lib, monkeypatch, env, dtype):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -782,18 +789,52 @@ def test_batch_packed_variant(gpu_lib, monkeypatch):
     test_batch_of_instances(gpu_lib)
 
 
+def test_batch_tma_variant(gpu_lib, monkeypatch):
+    """Rows staged by bulk tensor copies: every instance's parts with their own tensor maps, merged
+    into one launch."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "5")
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", "3")
+    test_batch_of_instances(gpu_lib)
+
+
 @pytest.mark.parametrize("dims,P,ptype,dtype,band", [((150, 70), 7, COL, "float", "32"), ((150, 70), 7, COL, "bf16", "32"),
                                                      ((300, 45), 11, COL, "double", "32"), ((64, 900), 9, ROW, "float", "8"),
                                                      ((97, 131), 16, COL, "float", "2")])
-def test_jacobi2d_packed_narrow(gpu_lib, monkeypatch, dims, P, ptype, dtype, band):
-    """Packed row streams on partitions a few elements wide or a few rows high."""
-    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "3")
+@pytest.mark.parametrize("variant", ["3", "5"])
+def test_jacobi2d_packed_narrow(gpu_lib, monkeypatch, dims, P, ptype, dtype, band, variant):
+    """Packed row streams, and rows staged by bulk tensor copies, on partitions a few elements wide
+    or a few rows high."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", variant)
     monkeypatch.setenv("HDARRAY_BAND2", band)
     monkeypatch.setenv("HDARRAY_TILE_ROWS", "6")
     x = synthetic.jacobi_field(dims, stream=87, dtype=dtype)
     prog, last = jacobi_prog(dims, P, 5, ptype, dtype, True)
     lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
     assert np.array_equal(read_all(lib, last, dims, dtype), orc.arrays[last].G)
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "3", "5"])
+@pytest.mark.parametrize("dtype", ["float", "bf16"])
+def test_jacobi2d_special_values(gpu_lib, monkeypatch, variant, dtype):
+    """Subnormal values and results, infinities, sums that overflow to infinity and signed zeros:
+    every kernel form rounds each cell exactly as the oracle's binary32 arithmetic."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", variant)
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", "10")
+    dims, P = (150, 270), 6
+    x = synthetic.jacobi_field(dims, stream=88, dtype="double")
+    x[1:30, :] *= 2.0 ** -130                 # subnormal binary32 and bfloat16 values and results
+    x[40:43, 100:104] = np.inf
+    x[60, 50:53] = 3.0e38                      # neighbours whose sum overflows
+    x[80:90, 30:40] = -0.0                     # all-negative-zero neighbourhoods: -0 * 0.25 = -0
+    x[100:110, 200:210] = -x[100:110, 200:210]
+    x = synthetic.to_storage(x, dtype)
+    prog, last = jacobi_prog(dims, P, 4, BLOCK, dtype, True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    got = read_all(lib, last, dims, dtype)
+    want = orc.arrays[last].G
+    wf = want.astype(np.float32) if dtype == "float" else oracle.bf16_to_f32(want)
+    assert np.isinf(wf).any() and ((wf != 0) & (np.abs(wf) < 2.0 ** -126)).any() and np.signbit(wf[wf == 0]).any()
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
 
 
 @pytest.mark.parametrize("env,dtype", [({"HDARRAY_FUSE_EXCHANGE": "0"}, "float"), ({"HDARRAY_AUTOTUNE": "1"}, "float"),
