@@ -90,11 +90,23 @@ def jacobi_variant(tuned):
     """The 2-D kernel variant the headline workload ran: the tuner's choice, else the
     environment's or the library default."""
     for t in tuned or []:
-        if t.get("kernel") == "jacobi2d":
+        if t.get("kernel") == "jacobi2d" and t.get("dtype") == "f32":
             return int(t["variant"])
     try:
         v = int(os.environ.get("HDARRAY_JACOBI_VARIANT", "1"))
         return v if v in KERNEL_NAMES_2D else 1
+    except ValueError:
+        return 1
+
+
+def stencil3d_variant():
+    """The 3-D kernel variant this run used: the tuner's choice (from the run's tuning file), else
+    the environment's or the library default (1)."""
+    for t in tune_report(os.environ.get("HDARRAY_TUNE_CACHE")) or []:
+        if t.get("kernel") == "stencil3d" and t.get("dtype") == "f32":
+            return int(t["variant3"])
+    try:
+        return int(os.environ.get("HDARRAY_STENCIL3D_VARIANT", "1"))
     except ValueError:
         return 1
 
@@ -244,7 +256,8 @@ def tune_report(path):
         w = line.split()
         if len(w) == 10:
             key = w[0].split(":")
-            out.append({"kernel": key[0], "variant": int(w[1]), "rows": int(w[2]), "warps": int(w[3]),
+            out.append({"kernel": key[0], "dtype": {"0": "f64", "1": "f32", "2": "bf16"}.get(key[1] if len(key) > 1 else "", "?"),
+                        "variant": int(w[1]), "rows": int(w[2]), "warps": int(w[3]),
                         "tile_z": int(w[4]), "fused_exchange": int(w[5]), "variant3": int(w[6]),
                         "band3": int(w[7]), "cta3": int(w[8]), "band2": int(w[9])})
     return out
@@ -680,7 +693,7 @@ def workload_stencil3d(H, torch, stream, args):
             pts.append(tuple(min(n - 2, max(1, v)) for v in lo))
         parity = cone_check(x, got, pts, iters, np.float32)
     H.HDArrayExit()
-    traffic = profiled("stencil3d_cta_fp32_512_37boxes.md", "dram_bytes_per_launch",
+    traffic = profiled("stencil3d_cta_fp32_512_37boxes.md", "dram_bytes_per_launch_v%d" % stencil3d_variant(),
                        ["k_stencil3d.cu", "stencil_common.cuh"]) if (n, nb) == (512, 37) else None
     return {"workload": "3-D 7-point %d^3 FP32, %d uneven manual partitions (extents 16-256), +-1 faces, "
                         "50 iterations per step, one fused launch per iteration (graph)" % (n, nb),
