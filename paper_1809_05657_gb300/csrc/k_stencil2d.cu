@@ -473,7 +473,10 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     const int x = t.cb + c * VEC;
     const bool full_chunk = x >= t.c0 && x + VEC <= t.c1;
     const bool shflL = c > 0 && lane > 0, shflR = c < nch - 1 && lane < 31;
-    const int me = gi * M * rw + c + 1;  // slot of the thread's chunk in its first staged row
+    // slot of the thread's chunk in its first staged row; the idle threads past the last row group
+    // read the first rows (valid shared memory) and store nothing, so every thread runs the same
+    // instructions (no selects around the loads and unpacking)
+    const int me = (act ? gi * M * rw : 0) + c + 1;
     E *yp = reinterpret_cast<E *>(P.y) + (int64_t)(t.r0 + gi * M - P.ylo0) * P.ys + (x - P.ylo1);
 
     bool failed = false;
@@ -489,14 +492,7 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
         const int rbase = t.r0 + j * SR + gi * M;  // the thread's first output row in this stage
         A rows[M + 2][VEC];
 #pragma unroll
-        for (int q = 0; q < M + 2; q++) {
-            if (act) {
-                EL::unpack(*reinterpret_cast<const V *>(sp + q * rw), rows[q]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < VEC; k++) rows[q][k] = A(0);
-            }
-        }
+        for (int q = 0; q < M + 2; q++) EL::unpack(*reinterpret_cast<const V *>(sp + q * rw), rows[q]);
 #pragma unroll
         for (int u = 0; u < M; u++) {
             const A(&up)[VEC] = rows[u];
@@ -505,8 +501,8 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
             A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
             A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
             const E *crow = reinterpret_cast<const E *>(sp + (u + 1) * rw);
-            if (!shflL && act) left = EL::load1(crow - 1);
-            if (!shflR && act) right = EL::load1(crow + VEC);
+            if (!shflL) left = EL::load1(crow - 1);
+            if (!shflR) right = EL::load1(crow + VEC);
             A out[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; k++) {
