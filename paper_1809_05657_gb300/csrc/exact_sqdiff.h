@@ -15,9 +15,17 @@
 // Anything else -- subnormal, infinite or NaN operands, exponents more than 28 apart -- returns
 // false and the caller takes the binary64 instructions.  The same source compiles for the host,
 // where a test compares it with IEEE binary64 arithmetic.
+//
+// sqdiff_f32_exact serves the common case of a residual, two close values, with fewer integer
+// operations: s = RN32(x - y) and its rounding error by the error-free transformation TwoSum
+// (Knuth, TAOCP vol. 2, 4.2.2; six binary32 additions).  When the error is zero, s is the exact
+// difference d, its 24-bit significand M squares exactly in 48 bits, and d * d = M^2 * 2^(2 e)
+// needs no rounding in binary64: the bits come from one 32 x 32 -> 64-bit product.  A nonzero
+// error, a subnormal, infinite or NaN s returns false (the caller takes sqdiff_f32_bits).
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #ifdef __CUDACC__
 #define HDA_HD __host__ __device__ __forceinline__
@@ -99,5 +107,37 @@ HDA_HD bool sqdiff_f32_bits(uint32_t ux, uint32_t uy, uint64_t &qbits)
     qbits = ((uint64_t)(top + E2 + 1023) << 52) | (M & 0x000fffffffffffffull);
     return true;
 }
+
+#ifdef __CUDA_ARCH__
+#define HDA_FADD(a, b) __fadd_rn((a), (b))
+#else
+#define HDA_FADD(a, b) ((a) + (b))  // the host build compiles without contraction (-ffp-contract=off)
+#endif
+
+// bits of RN64((x - y)^2) when RN32(x - y) is exact and normal or zero; false otherwise
+HDA_HD bool sqdiff_f32_exact(float x, float y, uint64_t &qbits)
+{
+    const float a = x, b = -y;
+    const float s = HDA_FADD(a, b);
+    const float bb = HDA_FADD(s, -a);
+    const float err = HDA_FADD(HDA_FADD(a, -HDA_FADD(s, -bb)), HDA_FADD(b, -bb));
+    if (!(err == 0.0f)) return false;  // inexact, or infinite / NaN operands
+    uint32_t u;
+    memcpy(&u, &s, 4);
+    if ((u & 0x7fffffffu) == 0) {  // x - y = 0: the square is +0
+        qbits = 0;
+        return true;
+    }
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0 || e == 0xffu) return false;  // subnormal or not finite
+    const uint64_t M = (uint64_t)((u & 0x7fffffu) | 0x800000u);
+    const uint64_t P = M * M;                  // 2^46 <= P < 2^48: d^2 = P * 2^(2 (e - 150)), exact
+    const int top = (P >> 47) ? 47 : 46;       // leading bit of P
+    const uint64_t mant = (P << (52 - top)) & 0x000fffffffffffffull;
+    qbits = ((uint64_t)(2 * ((int)e - 150) + top + 1023) << 52) | mant;
+    return true;
+}
+
+#undef HDA_FADD
 
 }  // namespace hda

@@ -198,6 +198,8 @@ __device__ __forceinline__ double sq_of(double a, double b)
 __device__ __forceinline__ double sq_of(unsigned ux, unsigned uy)
 {
     uint64_t q;
+    if (sqdiff_f32_exact(__uint_as_float(ux), __uint_as_float(uy), q))           // exact difference
+        return __longlong_as_double((long long)q);
     if (sqdiff_f32_bits(ux, uy, q)) return __longlong_as_double((long long)q);  // integer path
     const double d = f32_bits_to_f64(ux) - f32_bits_to_f64(uy);                 // the rest
     return d * d;

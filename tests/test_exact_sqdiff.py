@@ -2,7 +2,8 @@
 
 The GPU's binary64 pipe is narrow, so the residual kernel computes d = RN64(x - y) and
 q = RN64(d * d) for binary32 inputs with integer operations (csrc/exact_sqdiff.h), falling back to
-binary64 instructions outside its range.  The header also compiles for the host; this test builds
+binary64 instructions outside its range.  Close pairs first try a shorter path: a binary32
+difference shown exact by TwoSum, squared exactly in 48 bits.  The header also compiles for the host; this test builds
 a small driver with the host compiler and compares the integer path with the host's IEEE binary64
 arithmetic on random pairs (any bits, close values, every exponent gap), on pairs whose D^2 needs a
 round-half-to-even decision, and on special values.
@@ -38,10 +39,20 @@ static uint32_t f32(uint32_t sign, uint32_t e, uint32_t m) { return (sign << 31)
 int main(int argc, char **argv) {
     const uint64_t n = strtoull(argv[1], 0, 10);
     std::mt19937_64 rng(1809);
-    uint64_t total = 0, fast = 0, bad = 0, ties = 0;
+    uint64_t total = 0, fast = 0, bad = 0, ties = 0, exact = 0;
     auto check = [&](uint32_t ux, uint32_t uy) {
         uint64_t q;
         total++;
+        float x, y;
+        memcpy(&x, &ux, 4);
+        memcpy(&y, &uy, 4);
+        if (hda::sqdiff_f32_exact(x, y, q)) {
+            exact++;
+            if (q != ieee(ux, uy)) {
+                if (bad < 5) printf("exact-path mismatch %08x %08x\n", ux, uy);
+                bad++;
+            }
+        }
         if (!hda::sqdiff_f32_bits(ux, uy, q)) return;
         fast++;
         if (q != ieee(ux, uy)) {
@@ -82,8 +93,16 @@ int main(int argc, char **argv) {
                            0xff800000u, 0x7fc00000u, 0x00000001u};
     for (uint32_t a : sp)
         for (uint32_t b : sp) check(a, b);
-    printf("%llu %llu %llu %llu\n", (unsigned long long)total, (unsigned long long)fast,
-           (unsigned long long)bad, (unsigned long long)ties);
+    // residual-like pairs: a value and its neighbour after one more averaging step, the common
+    // case of the exact path
+    for (uint64_t i = 0; i < n / 4; i++) {
+        const uint64_t r = rng();
+        const uint32_t ux = 0x3c000000u + (uint32_t)(r % 0x3000000u);  // about 2^-7 .. 2^-1
+        const uint32_t uy = ux + (uint32_t)((int64_t)((r >> 32) % 4097) - 2048);
+        check(ux, uy);
+    }
+    printf("%llu %llu %llu %llu %llu\n", (unsigned long long)total, (unsigned long long)fast,
+           (unsigned long long)bad, (unsigned long long)ties, (unsigned long long)exact);
     return 0;
 }
 """
@@ -100,7 +119,8 @@ def test_integer_square_difference_matches_ieee_binary64():
         if r.returncode != 0:
             pytest.skip("no host C++ compiler: %s" % r.stderr[:200])
         out = subprocess.run([exe, "20000000"], capture_output=True, text=True, check=True).stdout.split()
-    total, fast, bad, ties = (int(v) for v in out)
+    total, fast, bad, ties, exact = (int(v) for v in out)
     assert bad == 0
     assert fast > total // 2  # the integer path serves most pairs
+    assert exact > total // 5  # close pairs take the exact-difference path
     assert ties > 10000
