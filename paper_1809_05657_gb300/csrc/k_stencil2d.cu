@@ -534,24 +534,6 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     }
 }
 
-int jacobi2d_tma_ctas_per_sm(int dtype, size_t smem)
-{
-    constexpr int NS = JACOBI2D_TMA_STAGES, M = JACOBI2D_TMA_ROWS;
-    const void *fn = dtype == DT_F64 ? (const void *)k_jacobi2d_tma<DT_F64, NS, M>
-                     : dtype == DT_F32 ? (const void *)k_jacobi2d_tma<DT_F32, NS, M>
-                                       : (const void *)k_jacobi2d_tma<DT_BF16, NS, M>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem) != cudaSuccess || n < 1) {
-        cudaGetLastError();
-        return 1;
-    }
-    return n;
-}
-
 cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
                                 const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
                                 unsigned spin_limit)

@@ -74,13 +74,12 @@ cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D
 // padded to 128 bytes; smem = the ring + 128 bytes of alignment slack, at most
 // JACOBI2D_TMA_SMEM_MAX).  tmaps holds one 128-byte CUtensorMap per part (its X buffer, box
 // rwb * 16 bytes x (ns * rows + 2)); err receives a set bit when a bounded wait gave up after
-// spin_limit polls.  jacobi2d_tma_ctas_per_sm: how many such CTAs one SM holds at once.
+// spin_limit polls.
 constexpr int JACOBI2D_TMA_STAGES = 4;
 constexpr int JACOBI2D_TMA_ROWS = 4;
 constexpr int JACOBI2D_TMA_THREADS = 256;
 constexpr int JACOBI2D_TMA_STAGE_MAX = 20 * 1024;  // largest stage the tile planner makes
 constexpr int JACOBI2D_TMA_SMEM_MAX = JACOBI2D_TMA_STAGES * (JACOBI2D_TMA_STAGE_MAX + 128) + 128;
-int jacobi2d_tma_ctas_per_sm(int dtype, size_t smem);
 cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
                                 const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
                                 unsigned spin_limit);

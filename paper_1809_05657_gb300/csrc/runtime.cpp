@@ -751,9 +751,9 @@ bool encode_row_map(const HDArray *X, const DevBuf &b, int box_w, int box_h, CUt
 // G row groups of JACOBI2D_TMA_ROWS rows per stage, so that G * nch <= 256 and a stage (its SR
 // rows and 2 halo rows) holds at most JACOBI2D_TMA_STAGE_MAX bytes.
 struct Tma2DGeom {
-    int64_t cb0, nb, nch, rw, G, SR, S;  // first band column, bands, chunks per band, staged row
-                                         // width, row groups, rows per stage, stages down a band
-    size_t stage;                        // bytes of a stage, padded to 128
+    int64_t cb0, nb, nch, rw, G, SR;  // first band column, bands, chunks per band, staged row width,
+                                      // row groups, rows per stage
+    size_t stage;                     // bytes of a stage, padded to 128
 };
 Tma2DGeom tma2d_geometry(const HDArray *X, const DevBuf &bx, const Box &W, int band_chunks)
 {
@@ -768,7 +768,6 @@ Tma2DGeom tma2d_geometry(const HDArray *X, const DevBuf &bx, const Box &W, int b
     q.G = std::max<int64_t>(1, std::min<int64_t>({JACOBI2D_TMA_THREADS / q.nch, (int64_t)(254 / M),
                                                   (JACOBI2D_TMA_STAGE_MAX / (16 * q.rw) - 2) / M}));
     q.SR = q.G * M;
-    q.S = (W.hi[0] - W.lo[0] + q.SR - 1) / q.SR;
     q.stage = ((size_t)(q.SR + 2) * (size_t)q.rw * 16 + 127) / 128 * 128;
     return q;
 }
