@@ -111,6 +111,14 @@ def stencil3d_variant():
         return 1
 
 
+def conv_variant():
+    """The convolution kernel this run used: variant 5 (rows staged by TMA) or 3 (packed streams)."""
+    for t in tune_report(os.environ.get("HDARRAY_TUNE_CACHE")) or []:
+        if t.get("kernel") == "conv2d" and t.get("dtype") == "f32":
+            return int(t["variant"])
+    return 5 if os.environ.get("HDARRAY_JACOBI_VARIANT") == "5" else 3
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle samples during the timed region."""
 
@@ -734,7 +742,9 @@ def workload_conv2d(H, torch, stream, args):
                         "%d iterations per step" % (N, iters),
             "metric": UNIT, "value": cells * iters / (ms * 1e-3) / 1e9, "unit": UNIT,
             "ms_per_step": ms, "us_per_iter": per * 1e3,
-            "roofline": _roofline_hbm("k_jacobi2d_cta<f32,8,OP_CONV> (packed row streams)", cells * 8, per)}
+            "roofline": _roofline_hbm("k_jacobi2d_tma<f32,4,4,OP_CONV> (rows staged by bulk tensor copies)"
+                                      if conv_variant() == 5 else "k_jacobi2d_cta<f32,8,OP_CONV> (packed row streams)",
+                                      cells * 8, per)}
 
 
 def workload_2mm(H, torch, stream, args):

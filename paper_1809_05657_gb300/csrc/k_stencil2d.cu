@@ -414,12 +414,12 @@ cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, con
 // up, the tile stops, thread 0 waits (with a fixed limit) for the copies it issued and the error
 // word is set.
 // ------------------------------------------------------------------------------------------
-template <int DT, int NS, int M>
+template <int DT, int NS, int M, int OP>
 __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__restrict__ parts,
                                                          const StenTile2D *__restrict__ tiles,
                                                          const Seg *__restrict__ segs,
-                                                         const uint8_t *__restrict__ tmaps, unsigned *err,
-                                                         unsigned spin_limit)
+                                                         const uint8_t *__restrict__ tmaps, const double *__restrict__ wts,
+                                                         unsigned *err, unsigned spin_limit)
 {
     static_assert((NS & (NS - 1)) == 0 && NS >= 2, "ring depth: a power of two");
     using EL = Elem<DT>;
@@ -432,6 +432,9 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     const int lane = threadIdx.x & 31;
     const StenTile2D t = tiles[blockIdx.x];
     const StenPart2D P = parts[t.part];
+    A w[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) w[k] = OP == OP_CONV ? (A)wts[k] : A(0);
     // the ring starts on a 128-byte boundary (the launch adds 128 bytes of slack)
     const uint32_t ring_s = (smem_addr(smem_dyn) + 127u) & ~127u;
     const char *ring = reinterpret_cast<const char *>(smem_dyn) + (ring_s - smem_addr(smem_dyn));
@@ -493,25 +496,55 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
         A rows[M + 2][VEC];
 #pragma unroll
         for (int q = 0; q < M + 2; q++) EL::unpack(*reinterpret_cast<const V *>(sp + q * rw), rows[q]);
+        // the elements left and right of the thread's chunk in staged row q: by shuffle, or from the
+        // staged neighbouring chunk (every box holds the halo chunks)
+        auto ends = [&](int q, A &left, A &right) {
+            left = __shfl_up_sync(0xffffffffu, rows[q][VEC - 1], 1);
+            right = __shfl_down_sync(0xffffffffu, rows[q][0], 1);
+            const E *crow = reinterpret_cast<const E *>(sp + q * rw);
+            if (!shflL) left = EL::load1(crow - 1);
+            if (!shflR) right = EL::load1(crow + VEC);
+        };
+        A lft[M + 2], rgt[M + 2];  // the convolution's: every staged row's, once
+        if constexpr (OP == OP_CONV) {
+#pragma unroll
+            for (int q = 0; q < M + 2; q++) ends(q, lft[q], rgt[q]);
+        }
 #pragma unroll
         for (int u = 0; u < M; u++) {
             const A(&up)[VEC] = rows[u];
             const A(&cv)[VEC] = rows[u + 1];
             const A(&dn)[VEC] = rows[u + 2];
-            A left = __shfl_up_sync(0xffffffffu, cv[VEC - 1], 1);
-            A right = __shfl_down_sync(0xffffffffu, cv[0], 1);
-            const E *crow = reinterpret_cast<const E *>(sp + (u + 1) * rw);
-            if (!shflL) left = EL::load1(crow - 1);
-            if (!shflR) right = EL::load1(crow + VEC);
             A out[VEC];
+            if constexpr (OP == OP_JACOBI) {
+                A left, right;
+                ends(u + 1, left, right);
 #pragma unroll
-            for (int k = 0; k < VEC; k++) {
-                const A wv = k > 0 ? cv[k - 1] : left;
-                const A ev = k < VEC - 1 ? cv[k + 1] : right;
-                A sum = wv + ev;
-                sum = sum + up[k];
-                sum = sum + dn[k];
-                out[k] = sum * A(0.25);
+                for (int k = 0; k < VEC; k++) {
+                    const A wv = k > 0 ? cv[k - 1] : left;
+                    const A ev = k < VEC - 1 ? cv[k + 1] : right;
+                    A sum = wv + ev;
+                    sum = sum + up[k];
+                    sum = sum + dn[k];
+                    out[k] = sum * A(0.25);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; k++) {
+                    const A r0[3] = {k > 0 ? up[k - 1] : lft[u], up[k], k < VEC - 1 ? up[k + 1] : rgt[u]};
+                    const A r1[3] = {k > 0 ? cv[k - 1] : lft[u + 1], cv[k], k < VEC - 1 ? cv[k + 1] : rgt[u + 1]};
+                    const A r2[3] = {k > 0 ? dn[k - 1] : lft[u + 2], dn[k], k < VEC - 1 ? dn[k + 1] : rgt[u + 2]};
+                    A sum = mul_rn(w[0], r0[0]);
+                    sum = add_rn(sum, mul_rn(w[1], r0[1]));
+                    sum = add_rn(sum, mul_rn(w[2], r0[2]));
+                    sum = add_rn(sum, mul_rn(w[3], r1[0]));
+                    sum = add_rn(sum, mul_rn(w[4], r1[1]));
+                    sum = add_rn(sum, mul_rn(w[5], r1[2]));
+                    sum = add_rn(sum, mul_rn(w[6], r2[0]));
+                    sum = add_rn(sum, mul_rn(w[7], r2[1]));
+                    sum = add_rn(sum, mul_rn(w[8], r2[2]));
+                    out[k] = sum;
+                }
             }
             if (act && rbase + u < t.r1) {
                 E *op = yp + (int64_t)(j * SR + u) * P.ys;
@@ -534,24 +567,29 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     }
 }
 
-cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
-                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
-                                unsigned spin_limit)
+cudaError_t launch_jacobi2d_tma(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, const double *weights,
+                                unsigned *err, unsigned spin_limit)
 {
     if (ntiles <= 0) return cudaSuccess;
     constexpr int NS = JACOBI2D_TMA_STAGES, M = JACOBI2D_TMA_ROWS;
     if (!tmaps || smem < 128 || smem > JACOBI2D_TMA_SMEM_MAX) return cudaErrorInvalidValue;
     const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
-    if (which < 0) return cudaErrorInvalidValue;
-    using KFn = void (*)(const StenPart2D *, const StenTile2D *, const Seg *, const uint8_t *, unsigned *, unsigned);
-    const KFn fns[3] = {k_jacobi2d_tma<DT_F64, NS, M>, k_jacobi2d_tma<DT_F32, NS, M>, k_jacobi2d_tma<DT_BF16, NS, M>};
-    static bool attr[3] = {};
-    if (!attr[which]) {
-        cudaError_t e = cudaFuncSetAttribute(fns[which], cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX);
+    if (which < 0 || (op != OP_JACOBI && op != OP_CONV) || (op == OP_CONV && !weights)) return cudaErrorInvalidValue;
+    using KFn = void (*)(const StenPart2D *, const StenTile2D *, const Seg *, const uint8_t *, const double *, unsigned *,
+                         unsigned);
+    const KFn fns[2][3] = {{k_jacobi2d_tma<DT_F64, NS, M, OP_JACOBI>, k_jacobi2d_tma<DT_F32, NS, M, OP_JACOBI>,
+                            k_jacobi2d_tma<DT_BF16, NS, M, OP_JACOBI>},
+                           {k_jacobi2d_tma<DT_F64, NS, M, OP_CONV>, k_jacobi2d_tma<DT_F32, NS, M, OP_CONV>,
+                            k_jacobi2d_tma<DT_BF16, NS, M, OP_CONV>}};
+    static bool attr[2][3] = {};
+    if (!attr[op][which]) {
+        cudaError_t e = cudaFuncSetAttribute(fns[op][which], cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX);
         if (e != cudaSuccess) return e;
-        attr[which] = true;
+        attr[op][which] = true;
     }
-    fns[which]<<<ntiles, 256, smem, s>>>(parts, tiles, segs, reinterpret_cast<const uint8_t *>(tmaps), err, spin_limit);
+    fns[op][which]<<<ntiles, 256, smem, s>>>(parts, tiles, segs, reinterpret_cast<const uint8_t *>(tmaps), weights, err,
+                                             spin_limit);
     return cudaGetLastError();
 }
 

@@ -80,9 +80,10 @@ constexpr int JACOBI2D_TMA_ROWS = 4;
 constexpr int JACOBI2D_TMA_THREADS = 256;
 constexpr int JACOBI2D_TMA_STAGE_MAX = 20 * 1024;  // largest stage the tile planner makes
 constexpr int JACOBI2D_TMA_SMEM_MAX = JACOBI2D_TMA_STAGES * (JACOBI2D_TMA_STAGE_MAX + 128) + 128;
-cudaError_t launch_jacobi2d_tma(int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
-                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, unsigned *err,
-                                unsigned spin_limit);
+// op 0: the Jacobi step; op 1: the 3 x 3 convolution of launch_stencil2d_cta with weights[9].
+cudaError_t launch_jacobi2d_tma(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
+                                const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, const double *weights,
+                                unsigned *err, unsigned spin_limit);
 // The packed-stream kernel with a chosen point operation: op 0 the Jacobi step, op 1 the 3 x 3
 // convolution with weights[9] (device memory, binary64, row-major over the offsets
 // (-1,-1) (-1,0) (-1,1) (0,-1) ... (1,1)).

@@ -1174,7 +1174,7 @@ int compile_plan(Plan &pl)
     };
 
     if (k.kind == K_JACOBI2D || k.kind == K_CONV2D) {
-        const bool conv = k.kind == K_CONV2D;  // always the packed-stream kernel
+        const bool conv = k.kind == K_CONV2D;  // the packed-stream kernel, or rows staged by TMA
         HDArray *X = pl.args[0], *Y = pl.args[1];
         const ArrStep *sx = nullptr;
         for (const ArrStep &st : pl.steps)
@@ -1213,7 +1213,7 @@ int compile_plan(Plan &pl)
                 int t0 = (int)h.tiles.size();
                 const bool flat = !conv && want == 2 && X->dtype != DT_BF16;
                 h.flat = flat;
-                h.variant = conv ? 3 : flat ? 2 : want == 2 ? 1 : want == 4 ? adaptive : want;
+                h.variant = conv ? (want == 5 ? 5 : 3) : flat ? 2 : want == 2 ? 1 : want == 4 ? adaptive : want;
                 h.warps = g->warps_per_cta;
                 bool ok = flat ? flat2d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, g->tile_rows * 256, h)
                                : jacobi_tiles(X, Y, p, pt.box[p], idx++, recv, fused, h, h.variant, g->band2, conv);
@@ -1252,6 +1252,7 @@ int compile_plan(Plan &pl)
         const CopyTask *dx = (const CopyTask *)addr[0];
         const int kind2d = conv ? L_CONV2D : h.flat ? L_FLAT2D : L_JACOBI2D;
         const char *p3 = h.variant == 5 ? addr[6] : addr[4];  // tensor maps, or the convolution's weights
+        const char *p4 = h.variant == 5 && conv ? addr[4] : nullptr;  // the weights beside the maps
         if (plain) {
             for (auto &gr : xfer_groups)
                 if (gr.second > gr.first) {
@@ -1260,7 +1261,7 @@ int compile_plan(Plan &pl)
                 }
             for (auto &r : dev_ranges) {
                 if (r.second <= r.first) continue;
-                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3;
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3; L.p4 = p4;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
                 L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
@@ -1271,7 +1272,7 @@ int compile_plan(Plan &pl)
                 pl.launches.push_back(L);
             }
             if (!h.tiles.empty()) {
-                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3;
+                LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3; L.p4 = p4;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3];
                 if (alternate) {
                     L.p1_alt = addr[5];
@@ -1870,12 +1871,17 @@ int compile_tuned(Plan &pl)
                         cands.push_back(Ctx::Shape{saved.variant, cells, saved.warps, tz, fu, 2, saved.band3, saved.cta3,
                                                    saved.band2});
             }
-    } else if (pl.k->kind == K_CONV2D) {  // the packed-stream kernel only
-        for (int fu : {1, 0})
+    } else if (pl.k->kind == K_CONV2D) {  // the packed-stream kernel, or rows staged by TMA
+        for (int fu : {1, 0}) {
             for (int band : {8, 16, 32})
                 for (int rows : {16, 32, 64})
-                    cands.push_back(Ctx::Shape{saved.variant, rows, saved.warps, saved.tile_z, fu, saved.variant3,
+                    cands.push_back(Ctx::Shape{3, rows, saved.warps, saved.tile_z, fu, saved.variant3,
                                                saved.band3, saved.cta3, band});
+            for (int band : {16, 32, 64})
+                for (int rows : {8, 16, 24})
+                    cands.push_back(Ctx::Shape{5, rows, saved.warps, saved.tile_z, fu, saved.variant3,
+                                               saved.band3, saved.cta3, band});
+        }
     } else {
         int64_t cells = 0;  // short tiles (more warps) are candidates for small grids only
         for (int p = 0; p < g->parts[pl.part].nparts; p++) cells += g->parts[pl.part].box[p].volume();
@@ -2846,8 +2852,8 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_COPY: return launch_copy((const CopyTask *)L.p0, (int)L.n0, s);
     case L_JACOBI2D:
         if (L.n2 == 5)
-            return launch_jacobi2d_tma(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
-                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, g->err_word, g->spin_limit);
+            return launch_jacobi2d_tma(0, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, nullptr, g->err_word, g->spin_limit);
         return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_STENCIL3D:
@@ -2878,6 +2884,10 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_CENTER: return launch_center(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, s);
     case L_SYMM: return launch_symmetrize(L.dtype, (const CovTask *)L.p0, (int)L.n0, (int)L.n1, (int)L.n2, s);
     case L_CONV2D:
+        if (L.n2 == 5)
+            return launch_jacobi2d_tma(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
+                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, (const double *)L.p4, g->err_word,
+                                       g->spin_limit);
         return launch_stencil2d_cta(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                     (const Seg *)L.p2, (const double *)L.p3, (size_t)L.n3, s);
     case L_FLAT2D:

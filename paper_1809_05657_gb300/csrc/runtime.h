@@ -76,6 +76,7 @@ struct LaunchRec {
     int kind = 0;
     int dtype = 0;
     const void *p0 = nullptr, *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+    const void *p4 = nullptr;      // a convolution's weights when p3 holds the tensor maps
     const void *p1_alt = nullptr;  // the same tiles in the reverse order (alternating launches)
     bool alt_calls = false;        // successive calls of the plan alternate p1 and p1_alt
     int64_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;

@@ -941,7 +941,12 @@ CONV_CASES = [((130, 301), 4, BLOCK, "float"), ((97, 131), 3, ROW, "double"), ((
 
 @pytest.mark.parametrize("dims,P,ptype,dtype", CONV_CASES)
 @pytest.mark.parametrize("mode", [H.HDARRAY_MODE_FUSED, H.HDARRAY_MODE_PLAIN])
-def test_conv2d_parity(gpu_lib, dims, P, ptype, dtype, mode):
+@pytest.mark.parametrize("variant", ["3", "5"])
+def test_conv2d_parity(gpu_lib, monkeypatch, dims, P, ptype, dtype, mode, variant):
+    """Every storage type and partition shape, fused and plain, with the packed-stream kernel and
+    with rows staged by bulk tensor copies."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", variant)
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", "5")
     x = synthetic.jacobi_field(dims, stream=94, dtype=dtype)
     w = synthetic.normal(9, stream=95) * 0.3
     lib, orc, *_ = run_program(conv_prog(dims, P, ptype, dtype, w), P, {"X": x, "Y": x}, gpu_lib, mode=mode)
@@ -951,7 +956,10 @@ def test_conv2d_parity(gpu_lib, dims, P, ptype, dtype, mode):
 
 @pytest.mark.parametrize("env", [{"HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "3"}, {"HDARRAY_BAND2": "3"},
                                  {"HDARRAY_FUSE_EXCHANGE": "0"}, {"HDARRAY_AUTOTUNE": "1"},
-                                 {"HDARRAY_BAND2": "32", "HDARRAY_TILE_ROWS": "64"}])
+                                 {"HDARRAY_BAND2": "32", "HDARRAY_TILE_ROWS": "64"},
+                                 {"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_BAND2": "1", "HDARRAY_TILE_ROWS": "1"},
+                                 {"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_BAND2": "64"},
+                                 {"HDARRAY_JACOBI_VARIANT": "5", "HDARRAY_FUSE_EXCHANGE": "0"}])
 def test_conv2d_execution_choices(gpu_lib, monkeypatch, env):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -963,13 +971,15 @@ def test_conv2d_execution_choices(gpu_lib, monkeypatch, env):
         assert np.array_equal(read_all(lib, name, dims, "float"), orc.arrays[name].G)
 
 
-@pytest.mark.parametrize("rows", [None, "16"])
-def test_conv2d_full_size_8192_block16(gpu_lib, rows, monkeypatch):
+@pytest.mark.parametrize("rows,variant", [(None, None), ("16", None), ("16", "5")])
+def test_conv2d_full_size_8192_block16(gpu_lib, rows, variant, monkeypatch):
     """The convolution workload at full size (8192^2 binary32, BLOCK 4 x 4) in a graph; outputs
     sampled at partition corners and edges and at random, each recomputed by the oracle from its
-    3 x 3 neighbourhood; default tile rows and the autotuned 16."""
+    3 x 3 neighbourhood; default tile rows, the autotuned 16, and rows staged by TMA."""
     if rows:
         monkeypatch.setenv("HDARRAY_TILE_ROWS", rows)
+    if variant:
+        monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", variant)
     N, P = 8192, 16
     x = synthetic.jacobi_field((N, N), stream=98, dtype="float")
     w = synthetic.normal(9, stream=99)
