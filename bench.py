@@ -60,21 +60,31 @@ def peaks():
         return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
+def code_hash(sources):
+    """First 16 hex digits of the SHA-256 of the kernel sources' code: each file with its `//`
+    comments, trailing blanks and empty lines removed, so that a comment edit does not make a
+    profile stale while any change to the code does."""
+    h = hashlib.sha256()
+    for src in sources:
+        for line in open(os.path.join(CSRC, src), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode("utf-8") + b"\n")
+    return h.hexdigest()[:16]
+
+
 def profiled(name, key, sources):
     """A figure from the committed ncu summary profiles/<name>: the value of `- key: value` in its
-    "Values read by bench.py" list, or None when any of the kernel sources changed since the capture
-    (the summary records their hash) or the key is absent."""
+    "Values read by bench.py" list, or None when the kernel sources' code changed since the capture
+    (the summary records code_hash(sources)) or the key is absent."""
     try:
         txt = open(os.path.join(PROFILES, name)).read()
-        h = hashlib.sha256()
-        for s in sources:
-            h.update(open(os.path.join(CSRC, s), "rb").read())
         vals = {}
         for line in txt.splitlines():
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+        if vals.get("kernel_code_sha256_16") != code_hash(sources):
             return None
         return float(vals[key])
     except Exception:

@@ -397,7 +397,8 @@ cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, con
 }
 
 // ------------------------------------------------------------------------------------------
-// The Jacobi step with its rows staged by the tensor memory accelerator.  A tile is a column band
+// The Jacobi step (OP_JACOBI) or the 3 x 3 convolution (OP_CONV, the order and rounding of the
+// packed-stream form above) with its rows staged by the tensor memory accelerator.  A tile is a column band
 // of nch 16-byte chunks by rows r0 .. r1 - 1 of one device, cut into stages of SR = ns * M output
 // rows.  Stage j is one box of the part's 2-D tensor map: the SR + 2 buffer rows
 // r0 - 1 + j * SR .. r0 + (j + 1) * SR (both halo rows included) by rwb chunks (the band with one
@@ -407,7 +408,8 @@ cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, con
 // stage: it reads its M + 2 staged rows from shared memory once each, the three-row window sliding
 // down in registers, and the copies cost the computing threads no instructions.  Horizontal
 // neighbours come by shuffle, or from the staged halo chunks, which every box holds (coordinates
-// outside the buffer read zeros, never used by an output).  Before its first copy the tile copies
+// outside the buffer read zeros, never used by an output); the convolution takes them for every
+// staged row once per stage, the Jacobi step for the centre row of each output row.  Before its first copy the tile copies
 // its receive segments -- the parts of the sections its device receives in this call (Eq. 1-2)
 // that only this tile reads -- from the senders' buffers into its own, and every thread fences
 // those generic stores to the async proxy.  Waits are bounded: after spin_limit polls a wait gives
