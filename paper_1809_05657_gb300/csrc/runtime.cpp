@@ -1295,31 +1295,41 @@ int compile_plan(Plan &pl)
             if (st.a == X) sx = &st;
         bool fused = !plain && g->fuse;
         Sten3DHost h;
-        h.dtype = X->dtype;
         std::vector<std::pair<int, int>> dev_ranges;
         int idx = 0;
         const int VEC = 16 / X->esize;
-        for (int p = 0; p < pt.nparts; p++) {
-            if (pt.box[p].empty()) continue;
-            if ((Y->buf[p].alloc.lo[2] - X->buf[p].alloc.lo[2]) % VEC != 0) return HDARRAY_ERR_STATE;
-            std::vector<Move> recv;
-            if (sx)
-                for (const Move &m : sx->moves)
-                    if (m.dst == p && local_move(m)) recv.push_back(m);
-            int t0 = (int)h.tiles.size();
-            const bool flat = g->variant3 == 2 && X->dtype != DT_BF16;
-            h.flat = flat;
-            if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, flat ? 2 : g->variant3, h,
-                                 flat ? g->tile_rows * 64 : 0, g->band3, g->cta3))
-                fused = false;
-            dev_ranges.push_back({t0, (int)h.tiles.size()});
+        // the TMA variant falls back to the cp.async tiles where a buffer admits no tensor map
+        const bool fuse0 = fused;
+        int v3 = g->variant3;
+        for (int attempt = 0; attempt < 2; attempt++) {
+            h = Sten3DHost{};
+            h.dtype = X->dtype;
+            dev_ranges.clear();
+            idx = 0;
+            fused = fuse0;
+            for (int p = 0; p < pt.nparts; p++) {
+                if (pt.box[p].empty()) continue;
+                if ((Y->buf[p].alloc.lo[2] - X->buf[p].alloc.lo[2]) % VEC != 0) return HDARRAY_ERR_STATE;
+                std::vector<Move> recv;
+                if (sx)
+                    for (const Move &m : sx->moves)
+                        if (m.dst == p && local_move(m)) recv.push_back(m);
+                int t0 = (int)h.tiles.size();
+                const bool flat = v3 == 2 && X->dtype != DT_BF16;
+                h.flat = flat;
+                if (!stencil3d_tiles(X, Y, p, pt.box[p], idx++, recv, fused, flat ? 2 : v3, h,
+                                     flat ? g->tile_rows * 64 : 0, g->band3, g->cta3))
+                    fused = false;
+                dev_ranges.push_back({t0, (int)h.tiles.size()});
+            }
+            if (!(v3 == 3 && h.map_error)) break;
+            v3 = 1;
         }
         if (!fused) {
             h.segs.clear();
             for (StenTile3D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
             if (sx) add_moves(*sx);
         }
-        if (h.map_error) return HDARRAY_ERR_CUDA;
         if (!plain && g->snake && X->uid > Y->uid) std::reverse(h.tiles.begin(), h.tiles.end());
         blobs.push_back({xfer.data(), xfer.size() * sizeof(CopyTask)});
         blobs.push_back({h.parts.data(), h.parts.size() * sizeof(StenPart3D)});
@@ -1344,7 +1354,7 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = (const StenTile3D *)addr[2] + r.first; L.p2 = addr[3]; L.p3 = addr[5];
-                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = v3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         } else {
@@ -1356,7 +1366,7 @@ int compile_plan(Plan &pl)
                 LaunchRec L; L.kind = h.flat ? L_FLAT3D : L_STENCIL3D; L.dtype = X->dtype;
                 L.p0 = addr[1]; L.p1 = addr[2]; L.p2 = addr[3]; L.p3 = addr[5];
                 if (alternate) L.p1_alt = addr[4];
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = g->variant3; L.n3 = (int64_t)h.smem;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : g->cta3 / 32; L.n2 = v3; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         }
