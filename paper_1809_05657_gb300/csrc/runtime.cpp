@@ -101,7 +101,8 @@ struct Ctx {
     int variant = 0;        // 2-D kernel variant (0 registers, 1 cp.async ring, 2 flat, 3 packed streams,
                             // 4 adaptive, 5 rows staged by bulk tensor copies)
     int tile_z = 64;        // 3-D tile depth (planes per tile)
-    int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat)
+    int variant3 = 1;       // 3-D kernel variant (0 warp per row, 1 CTA per tile with a plane ring, 2 flat,
+                            // 3 the CTA tiles with planes staged by bulk tensor copies)
     int band2 = 32;         // 2-D packed-stream variant: most 16-byte chunks per band
     unsigned spin_limit = GEMM_SPIN_LIMIT_DEFAULT;  // polls of a GEMM pipeline wait (HDARRAY_SPIN_LIMIT)
     int band3 = 32;         // 3-D CTA variant: most 16-byte chunks per band
