@@ -718,8 +718,8 @@ def workload_stencil3d(H, torch, stream, args):
             "metric": UNIT, "value": cells * iters / (ms * 1e-3) / 1e9, "unit": UNIT, "dtype": "f32",
             "steps": steps, "ms_per_step": ms, "us_per_iter": per * 1e3,
             "exchange_bytes_per_iteration": 2 * xbytes,
-            "roofline": _roofline_hbm({3: "k_stencil3d_tma<f32,8,256> (planes staged by bulk tensor copies)",
-                                       1: "k_stencil3d_cta<f32,8,256> (cp.async plane ring)"}.get(
+            "roofline": _roofline_hbm({3: "k_stencil3d_tma<f32,8> (planes staged by bulk tensor copies)",
+                                       1: "k_stencil3d_cta<f32,8> (cp.async plane ring)"}.get(
                                           stencil3d_variant(), "k_stencil3d") + ", fused exchange + stencil",
                                       algo, per, traffic),
             "parity": parity}
