@@ -96,11 +96,11 @@ KERNEL_NAMES_2D = {0: "k_jacobi2d<f32,6> (register ring)", 1: "k_jacobi2d_async<
                    5: "k_jacobi2d_tma<f32,4,4> (rows staged by bulk tensor copies)"}
 
 
-def jacobi_variant(tuned):
-    """The 2-D kernel variant the headline workload ran: the tuner's choice, else the
-    environment's or the library default."""
+def jacobi_variant(tuned, dtype="f32"):
+    """The 2-D kernel variant the headline workload ran: the tuner's choice for its storage type,
+    else the environment's or the library default."""
     for t in tuned or []:
-        if t.get("kernel") == "jacobi2d" and t.get("dtype") == "f32":
+        if t.get("kernel") == "jacobi2d" and t.get("dtype") == dtype:
             return int(t["variant"])
     try:
         v = int(os.environ.get("HDARRAY_JACOBI_VARIANT", "1"))
@@ -1291,7 +1291,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     if rank == 0:
-        variant = jacobi_variant(tuned)
+        variant = jacobi_variant(tuned, "f32" if args.storage == "float" else "bf16")
         traffic = profiled("jacobi2d_fp32_8192_block16.md", "dram_bytes_per_launch_v%d" % variant,
                            ["k_stencil2d.cu", "stencil_common.cuh"]) if N == 8192 and args.storage == "float" else None
         pk = r["peaks"]

@@ -409,19 +409,70 @@ cudaError_t launch_stencil2d_cta(int op, int dtype, const StenPart2D *parts, con
 // down in registers, and the copies cost the computing threads no instructions.  Horizontal
 // neighbours come by shuffle, or from the staged halo chunks, which every box holds (coordinates
 // outside the buffer read zeros, never used by an output); the convolution takes them for every
-// staged row once per stage, the Jacobi step for the centre row of each output row.  Before its first copy the tile copies
-// its receive segments -- the parts of the sections its device receives in this call (Eq. 1-2)
-// that only this tile reads -- from the senders' buffers into its own, and every thread fences
-// those generic stores to the async proxy.  Waits are bounded: after spin_limit polls a wait gives
-// up, the tile stops, thread 0 waits (with a fixed limit) for the copies it issued and the error
-// word is set.
+// staged row once per stage, the Jacobi step for the centre row of each output row.  The tile
+// copies its receive segments -- the parts of the sections its device receives in this call
+// (Eq. 1-2) that only this tile reads -- from the senders' buffers into its own, and every thread
+// fences those generic stores to the async proxy.  Without RX, or with more than rx_cap received
+// elements, it does so before its first copy.  With RX it issues the ring's first NS copies
+// first, so that they fly during the receive, and keeps each received value with its place in the
+// tile's staged window in shared memory.  When one of those stages has landed, the threads write
+// the values into it before anyone reads it.  Later stages are issued after the fence and read
+// the values from the buffer.  Waits are bounded: after spin_limit polls a wait gives up, the tile
+// stops, thread 0 waits (with a fixed limit) for the copies it issued and the error word is set.
 // ------------------------------------------------------------------------------------------
-template <int DT, int NS, int M, int OP>
+
+// The receive of a tile with RX: this thread's elements e = threadIdx.x + q * blockDim.x (q < 4)
+// of its segments, flattened in order, loaded together, then stored into the own buffer xb (row
+// stride xs elements) and kept at side_v[e] with side_p[e] = (row << 9) | column: the element's
+// place relative to the staged window's first row yc and the box's first column xc (buffer
+// coordinates), or -1 outside the window (never patched).
+template <typename E>
+__device__ __forceinline__ void receive_keep(const Seg *__restrict__ segs, int seg0, int nseg, const E *xb, int64_t xs,
+                                             int64_t yc, int64_t xc, E *side_v, int32_t *side_p)
+{
+    E v[4];
+    E *dp[4];
+    int32_t pp[4];
+    int u = 0, e = threadIdx.x, i0 = 0;
+    for (int s = 0; s < nseg && u < 4; s++) {
+        const Seg g = segs[seg0 + s];
+        const int total = g.n * g.m;
+        while (u < 4 && e < i0 + total) {
+            const int i = e - i0, o = i / g.n, k = i - o * g.n;
+            const E *sp = reinterpret_cast<const E *>(g.src) + (o * g.sso + k * g.ss);
+            E *dq = reinterpret_cast<E *>(g.dst) + (o * g.dso + k * g.ds);
+            const int64_t off = dq - xb;
+            const int64_t r = (off >= 0 && off < INT32_MAX && xs < INT32_MAX) ? (int64_t)((uint32_t)off / (uint32_t)xs)
+                                                                            : off / xs;
+            const int64_t tr = r - yc, tc = off - r * xs - xc;
+            const int32_t p = (tr >= 0 && tr < (1 << 21) && tc >= 0 && tc < 512) ? (int32_t)((tr << 9) | tc) : -1;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q == u) {
+                    v[q] = *sp;
+                    dp[q] = dq;
+                    pp[q] = p;
+                }
+            u++;
+            e += blockDim.x;
+        }
+        i0 += total;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (q < u) {
+            *dp[q] = v[q];
+            side_v[threadIdx.x + q * blockDim.x] = v[q];
+            side_p[threadIdx.x + q * blockDim.x] = pp[q];
+        }
+}
+
+template <int DT, int NS, int M, int OP, bool RX>
 __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__restrict__ parts,
                                                          const StenTile2D *__restrict__ tiles,
                                                          const Seg *__restrict__ segs,
                                                          const uint8_t *__restrict__ tmaps, const double *__restrict__ wts,
-                                                         unsigned *err, unsigned spin_limit)
+                                                         unsigned *err, unsigned spin_limit, int ring_bytes, int rx_cap)
 {
     static_assert((NS & (NS - 1)) == 0 && NS >= 2, "ring depth: a power of two");
     using EL = Elem<DT>;
@@ -441,7 +492,14 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     const uint32_t ring_s = (smem_addr(smem_dyn) + 127u) & ~127u;
     const char *ring = reinterpret_cast<const char *>(smem_dyn) + (ring_s - smem_addr(smem_dyn));
 
-    if (t.nseg > 0) receive_flat_vec<E>(segs, t.seg0, t.nseg, threadIdx.x, blockDim.x);
+    // RX: the received values and their places, after the ring
+    E *side_v = reinterpret_cast<E *>(reinterpret_cast<char *>(smem_dyn) + ring_bytes);
+    int32_t *side_p = reinterpret_cast<int32_t *>(side_v + rx_cap);
+    int ntot = 0;  // RX: received elements of the tile
+    if (RX)
+        for (int s = 0; s < t.nseg; s++) ntot += segs[t.seg0 + s].n * segs[t.seg0 + s].m;
+    const bool late = RX && t.nseg > 0 && ntot <= rx_cap;
+    if (t.nseg > 0 && !late) receive_flat_vec<E>(segs, t.seg0, t.nseg, threadIdx.x, blockDim.x);
     asm volatile("fence.proxy.async.global;" ::: "memory");  // the receive's stores, before bulk copies read them
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; s++)
@@ -471,6 +529,11 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
     };
     if (threadIdx.x == 0)
         for (int j = 0; j < NS; j++) issue(j);
+    if (late) {
+        // stages NS and later are issued after the first barrier of the loop, so after this fence
+        receive_keep<E>(segs, t.seg0, t.nseg, reinterpret_cast<const E *>(P.x), P.xs, yc, xc, side_v, side_p);
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
 
     // this thread: row group gi (output rows gi * M .. of every stage), chunk c
     const int gi = threadIdx.x / nch, c = threadIdx.x - gi * nch;
@@ -491,6 +554,19 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
+        }
+        if (late && j < NS) {
+            // this stage was copied before the receive's stores: the received values go in now,
+            // ordered before any later bulk copy into the same slot
+            char *st = const_cast<char *>(ring) + (size_t)(j & (NS - 1)) * stage_bytes;
+            for (int e = threadIdx.x; e < ntot; e += blockDim.x) {
+                const int32_t p = side_p[e];
+                const int ir = (p >> 9) - j * SR, ic = p & 511;
+                if (p >= 0 && ir >= 0 && ir < SR + 2 && ic < rw * VEC)
+                    *reinterpret_cast<E *>(st + (size_t)ir * rw * 16 + (size_t)ic * sizeof(E)) = side_v[e];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
         }
         if (threadIdx.x == 0 && j > 0) issue(j - 1 + NS);
         const uint4 *sp = reinterpret_cast<const uint4 *>(ring + (size_t)(j & (NS - 1)) * stage_bytes) + me;
@@ -571,27 +647,38 @@ __global__ void __launch_bounds__(256, 3) k_jacobi2d_tma(const StenPart2D *__res
 
 cudaError_t launch_jacobi2d_tma(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
                                 const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, const double *weights,
-                                unsigned *err, unsigned spin_limit)
+                                unsigned *err, unsigned spin_limit, int rx_cap)
 {
     if (ntiles <= 0) return cudaSuccess;
     constexpr int NS = JACOBI2D_TMA_STAGES, M = JACOBI2D_TMA_ROWS;
-    if (!tmaps || smem < 128 || smem > JACOBI2D_TMA_SMEM_MAX) return cudaErrorInvalidValue;
     const int which = dtype == DT_F64 ? 0 : dtype == DT_F32 ? 1 : dtype == DT_BF16 ? 2 : -1;
     if (which < 0 || (op != OP_JACOBI && op != OP_CONV) || (op == OP_CONV && !weights)) return cudaErrorInvalidValue;
+    if (rx_cap < 0 || rx_cap > JACOBI2D_TMA_RX_MAX || rx_cap % JACOBI2D_TMA_THREADS != 0) return cudaErrorInvalidValue;
+    const size_t esize = which == 0 ? 8 : which == 1 ? 4 : 2;
+    // the ring's bytes are a multiple of 16 so that the received values after it stay aligned
+    const size_t total = smem + (size_t)rx_cap * (esize + 4);
+    if (!tmaps || smem < 128 || smem % 16 != 0 || total > (size_t)JACOBI2D_TMA_SMEM_MAX) return cudaErrorInvalidValue;
     using KFn = void (*)(const StenPart2D *, const StenTile2D *, const Seg *, const uint8_t *, const double *, unsigned *,
-                         unsigned);
-    const KFn fns[2][3] = {{k_jacobi2d_tma<DT_F64, NS, M, OP_JACOBI>, k_jacobi2d_tma<DT_F32, NS, M, OP_JACOBI>,
-                            k_jacobi2d_tma<DT_BF16, NS, M, OP_JACOBI>},
-                           {k_jacobi2d_tma<DT_F64, NS, M, OP_CONV>, k_jacobi2d_tma<DT_F32, NS, M, OP_CONV>,
-                            k_jacobi2d_tma<DT_BF16, NS, M, OP_CONV>}};
-    static bool attr[2][3] = {};
-    if (!attr[op][which]) {
-        cudaError_t e = cudaFuncSetAttribute(fns[op][which], cudaFuncAttributeMaxDynamicSharedMemorySize, JACOBI2D_TMA_SMEM_MAX);
+                         unsigned, int, int);
+    const KFn fns[2][2][3] = {
+        {{k_jacobi2d_tma<DT_F64, NS, M, OP_JACOBI, false>, k_jacobi2d_tma<DT_F32, NS, M, OP_JACOBI, false>,
+          k_jacobi2d_tma<DT_BF16, NS, M, OP_JACOBI, false>},
+         {k_jacobi2d_tma<DT_F64, NS, M, OP_CONV, false>, k_jacobi2d_tma<DT_F32, NS, M, OP_CONV, false>,
+          k_jacobi2d_tma<DT_BF16, NS, M, OP_CONV, false>}},
+        {{k_jacobi2d_tma<DT_F64, NS, M, OP_JACOBI, true>, k_jacobi2d_tma<DT_F32, NS, M, OP_JACOBI, true>,
+          k_jacobi2d_tma<DT_BF16, NS, M, OP_JACOBI, true>},
+         {k_jacobi2d_tma<DT_F64, NS, M, OP_CONV, true>, k_jacobi2d_tma<DT_F32, NS, M, OP_CONV, true>,
+          k_jacobi2d_tma<DT_BF16, NS, M, OP_CONV, true>}}};
+    const int rx = rx_cap > 0 ? 1 : 0;
+    static bool attr[2][2][3] = {};
+    if (!attr[rx][op][which]) {
+        cudaError_t e = cudaFuncSetAttribute(fns[rx][op][which], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             JACOBI2D_TMA_SMEM_MAX);
         if (e != cudaSuccess) return e;
-        attr[op][which] = true;
+        attr[rx][op][which] = true;
     }
-    fns[op][which]<<<ntiles, 256, smem, s>>>(parts, tiles, segs, reinterpret_cast<const uint8_t *>(tmaps), weights, err,
-                                             spin_limit);
+    fns[rx][op][which]<<<ntiles, 256, total, s>>>(parts, tiles, segs, reinterpret_cast<const uint8_t *>(tmaps), weights,
+                                                  err, spin_limit, (int)smem, rx_cap);
     return cudaGetLastError();
 }
 

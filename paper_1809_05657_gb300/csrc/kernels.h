@@ -74,16 +74,21 @@ cudaError_t launch_jacobi2d(int dtype, const StenPart2D *parts, const StenTile2D
 // padded to 128 bytes; smem = the ring + 128 bytes of alignment slack, at most
 // JACOBI2D_TMA_SMEM_MAX).  tmaps holds one 128-byte CUtensorMap per part (its X buffer, box
 // rwb * 16 bytes x (ns * rows + 2)); err receives a set bit when a bounded wait gave up after
-// spin_limit polls.
+// spin_limit polls.  rx_cap > 0 (a multiple of 256, at most JACOBI2D_TMA_RX_MAX): a tile with at
+// most rx_cap received elements issues its first copies before its receive and patches the
+// received values into those stages; the launch adds rx_cap * (element size + 4) bytes of shared
+// memory after the ring for them.  Tiles with more, and every tile when rx_cap = 0, receive first.
 constexpr int JACOBI2D_TMA_STAGES = 4;
 constexpr int JACOBI2D_TMA_ROWS = 4;
 constexpr int JACOBI2D_TMA_THREADS = 256;
 constexpr int JACOBI2D_TMA_STAGE_MAX = 20 * 1024;  // largest stage the tile planner makes
-constexpr int JACOBI2D_TMA_SMEM_MAX = JACOBI2D_TMA_STAGES * (JACOBI2D_TMA_STAGE_MAX + 128) + 128;
+constexpr int JACOBI2D_TMA_RX_MAX = 4 * JACOBI2D_TMA_THREADS;
+constexpr int JACOBI2D_TMA_SMEM_MAX =
+    JACOBI2D_TMA_STAGES * (JACOBI2D_TMA_STAGE_MAX + 128) + 128 + JACOBI2D_TMA_RX_MAX * (8 + 4);
 // op 0: the Jacobi step; op 1: the 3 x 3 convolution of launch_stencil2d_cta with weights[9].
 cudaError_t launch_jacobi2d_tma(int op, int dtype, const StenPart2D *parts, const StenTile2D *tiles, int ntiles,
                                 const Seg *segs, size_t smem, cudaStream_t s, const void *tmaps, const double *weights,
-                                unsigned *err, unsigned spin_limit);
+                                unsigned *err, unsigned spin_limit, int rx_cap);
 // The packed-stream kernel with a chosen point operation: op 0 the Jacobi step, op 1 the 3 x 3
 // convolution with weights[9] (device memory, binary64, row-major over the offsets
 // (-1,-1) (-1,0) (-1,1) (0,-1) ... (1,1)).

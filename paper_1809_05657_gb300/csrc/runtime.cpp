@@ -109,6 +109,7 @@ struct Ctx {
     int cta3 = 256;         // 3-D CTA variant: threads per CTA (256 or 512)
     int fuse = 1;           // exchange inside the stencil launch (1) or as a copy launch before it (0)
     int snake = 1;          // alternate the tile order of X -> Y and Y -> X launches (L2 reuse)
+    int late = 1;           // 2-D TMA tiles issue their first copies before their receive (HDARRAY_LATE_RECEIVE)
     int gemm_parts = 2;     // binary32 GEMM on tensor cores: 2 bf16 parts (bf16x3) or 3 (bf16x6)
     int row_align = 16;     // bytes: device buffer rows start and end on this boundary (16 .. 1024)
     // autotuner: chosen tile shapes per (kernel, dtype, partition shape)
@@ -773,6 +774,22 @@ Tma2DGeom tma2d_geometry(const HDArray *X, const DevBuf &bx, const Box &W, int b
     return q;
 }
 
+// Received elements a TMA tile keeps for patching its first stages: the most any tile of h
+// receives, rounded up to whole passes of the CTA's threads and capped at JACOBI2D_TMA_RX_MAX (a
+// tile with more receives before its copies); 0 when no tile receives.
+int tma2d_rx_cap(const Sten2DHost &h)
+{
+    int64_t most = 0;
+    for (const StenTile2D &t : h.tiles) {
+        int64_t n = 0;
+        for (int s = 0; s < t.nseg; s++) n += (int64_t)h.segs[t.seg0 + s].n * h.segs[t.seg0 + s].m;
+        most = std::max(most, n);
+    }
+    if (most == 0) return 0;
+    const int64_t T = JACOBI2D_TMA_THREADS;
+    return (int)std::min<int64_t>(JACOBI2D_TMA_RX_MAX, (most + T - 1) / T * T);
+}
+
 // Tiles of the fused 2-D kernel for one device.  Warp variants (0, 1): column bands of 32 chunks
 // x tile_rows rows, a warp each.  Packed-stream variant (3): the box's chunks cut into bands of
 // equal width of at most band_chunks (<= 32); per band, tiles of ns streams x sl rows with
@@ -1228,6 +1245,7 @@ int compile_plan(Plan &pl)
             for (StenTile2D &t : h.tiles) { t.seg0 = 0; t.nseg = 0; }
             if (sx) add_moves(*sx);
         }
+        if (h.variant == 5 && g->late) h.rx_cap = tma2d_rx_cap(h);
         // one launch for every device: the tiles of the calls X -> Y and Y -> X run in opposite
         // orders, so an iteration starts on the rows the previous one wrote last, still in L2
         if (!plain && g->snake && X->uid > Y->uid) std::reverse(h.tiles.begin(), h.tiles.end());
@@ -1264,7 +1282,8 @@ int compile_plan(Plan &pl)
                 if (r.second <= r.first) continue;
                 LaunchRec L; L.kind = kind2d; L.dtype = X->dtype; L.p3 = p3; L.p4 = p4;
                 L.p0 = addr[1]; L.p1 = (const StenTile2D *)addr[2] + r.first; L.p2 = addr[3];
-                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
+                L.n0 = r.second - r.first; L.n1 = h.flat ? (int64_t)h.smem : h.variant == 5 ? h.rx_cap : h.warps;
+                L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         } else {
@@ -1279,7 +1298,8 @@ int compile_plan(Plan &pl)
                     L.p1_alt = addr[5];
                     L.alt_calls = conv;
                 }
-                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.warps; L.n2 = h.variant; L.n3 = (int64_t)h.smem;
+                L.n0 = (int64_t)h.tiles.size(); L.n1 = h.flat ? (int64_t)h.smem : h.variant == 5 ? h.rx_cap : h.warps;
+                L.n2 = h.variant; L.n3 = (int64_t)h.smem;
                 pl.launches.push_back(L);
             }
         }
@@ -2257,6 +2277,7 @@ int flush_batch()
                 h.variant = p->s2.variant;
                 h.warps = p->s2.warps;
                 h.smem = std::max(h.smem, p->s2.smem);
+                h.rx_cap = std::max(h.rx_cap, p->s2.rx_cap);
                 const int pbase = (int)h.parts.size(), sbase = (int)h.segs.size();
                 h.parts.insert(h.parts.end(), p->s2.parts.begin(), p->s2.parts.end());
                 h.maps.insert(h.maps.end(), p->s2.maps.begin(), p->s2.maps.end());  // TMA: one per part
@@ -2292,7 +2313,7 @@ int flush_batch()
             LaunchRec L; L.kind = kv.second.flat ? L_FLAT2D : L_JACOBI2D; L.dtype = kv.second.dtype;
             L.p0 = addr[ai]; L.p1 = addr[ai + 1]; L.p2 = addr[ai + 2]; L.p3 = addr[ai + 3];
             L.n0 = (int64_t)kv.second.tiles.size();
-            L.n1 = kv.second.flat ? (int64_t)kv.second.smem : kv.second.warps;
+            L.n1 = kv.second.flat ? (int64_t)kv.second.smem : kv.second.variant == 5 ? kv.second.rx_cap : kv.second.warps;
             L.n2 = kv.second.variant;
             L.n3 = (int64_t)kv.second.smem;
             ai += 4;
@@ -2782,6 +2803,8 @@ int init_impl(int ndev, unsigned flags)
         if (wc && atoi(wc) > 0 && atoi(wc) <= 8) g->warps_per_cta = atoi(wc);
         const char *vv = getenv("HDARRAY_JACOBI_VARIANT");
         if (vv && atoi(vv) >= 0 && atoi(vv) <= 5) g->variant = atoi(vv);
+        const char *lr = getenv("HDARRAY_LATE_RECEIVE");
+        if (lr && (atoi(lr) == 0 || atoi(lr) == 1)) g->late = atoi(lr);
         const char *sn = getenv("HDARRAY_SNAKE");
         if (sn && (atoi(sn) == 0 || atoi(sn) == 1)) g->snake = atoi(sn);
         const char *ra = getenv("HDARRAY_ROW_ALIGN");
@@ -2885,7 +2908,8 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
     case L_JACOBI2D:
         if (L.n2 == 5)
             return launch_jacobi2d_tma(0, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
-                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, nullptr, g->err_word, g->spin_limit);
+                                       (const Seg *)L.p2, (size_t)L.n3, s, L.p3, nullptr, g->err_word, g->spin_limit,
+                                       (int)L.n1);
         return launch_jacobi2d(L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                (const Seg *)L.p2, (int)L.n1, (int)L.n2, (size_t)L.n3, s);
     case L_STENCIL3D:
@@ -2919,7 +2943,7 @@ cudaError_t issue(const LaunchRec &L, cudaStream_t s)
         if (L.n2 == 5)
             return launch_jacobi2d_tma(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                        (const Seg *)L.p2, (size_t)L.n3, s, L.p3, (const double *)L.p4, g->err_word,
-                                       g->spin_limit);
+                                       g->spin_limit, (int)L.n1);
         return launch_stencil2d_cta(1, L.dtype, (const StenPart2D *)L.p0, (const StenTile2D *)L.p1, (int)L.n0,
                                     (const Seg *)L.p2, (const double *)L.p3, (size_t)L.n3, s);
     case L_FLAT2D:

@@ -107,6 +107,7 @@ struct Sten2DHost {
     std::vector<Seg> segs;
     std::vector<CUtensorMap> maps;  // TMA variant: one per part (its X buffer)
     bool map_error = false;
+    int rx_cap = 0;  // TMA variant: received elements a tile keeps to patch its first stages (0: none)
 };
 struct Sten3DHost {
     int dtype = 0;

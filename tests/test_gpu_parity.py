@@ -813,6 +813,26 @@ def test_jacobi2d_packed_narrow(gpu_lib, monkeypatch, dims, P, ptype, dtype, ban
     assert np.array_equal(read_all(lib, last, dims, dtype), orc.arrays[last].G)
 
 
+@pytest.mark.parametrize("dims,P,ptype,dtype,rows,band", [
+    ((700, 300), 5, COL, "float", "40", "16"),    # tiles longer than the ring: later stages read the buffer
+    ((2600, 200), 3, COL, "float", "80", "16"),   # middle parts receive 1280 elements a tile: receive first
+    ((300, 500), 6, ROW, "bf16", "8", "32"),      # row faces, patched into the first and the last stage
+    ((257, 263), 9, BLOCK, "double", "12", "16")])
+@pytest.mark.parametrize("late", ["0", "1"])
+def test_jacobi2d_tma_late_receive(gpu_lib, monkeypatch, dims, P, ptype, dtype, rows, band, late):
+    """Rows staged by bulk tensor copies with the receive before the tile's first copies (late 0) or
+    after them, the received values patched into the stages already copied (late 1): every held
+    element of every device buffer and the result are the oracle's."""
+    monkeypatch.setenv("HDARRAY_JACOBI_VARIANT", "5")
+    monkeypatch.setenv("HDARRAY_TILE_ROWS", rows)
+    monkeypatch.setenv("HDARRAY_BAND2", band)
+    monkeypatch.setenv("HDARRAY_LATE_RECEIVE", late)
+    x = synthetic.jacobi_field(dims, stream=89, dtype=dtype)
+    prog, last = jacobi_prog(dims, P, 5, ptype, dtype, True)
+    lib, orc, *_ = run_program(prog, P, {"B": x, "A": x}, gpu_lib)
+    assert np.array_equal(read_all(lib, last, dims, dtype), orc.arrays[last].G)
+
+
 @pytest.mark.parametrize("variant", ["0", "1", "3", "5"])
 @pytest.mark.parametrize("dtype", ["float", "bf16"])
 def test_jacobi2d_special_values(gpu_lib, monkeypatch, variant, dtype):
